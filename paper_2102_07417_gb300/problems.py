@@ -1,0 +1,234 @@
+"""Seeded synthetic problem generators (input synthesis only).
+
+This module builds the sparse SPD matrices and right-hand sides that the
+solver and its oracle are run on.  It holds none of the AMG method's
+arithmetic: strength, coarsening, interpolation, Galerkin products, smoothing
+and CG all live elsewhere.  Both the CUDA path and the CPU oracle take their
+inputs from here, and nothing else is shared between them.
+
+Workloads (all matrices CSR, int32 indices, float64 values, columns sorted
+ascending within each row, Dirichlet boundary rows eliminated):
+
+* ``poisson1d(n)``           tridiag(-1, 2, -1)
+* ``poisson2d(N)``           5-point stencil 4/-1 on an N x N interior grid
+* ``poisson3d(N)``           7-point stencil 6/-1 on an N^3 interior grid
+* ``diffusion3d(N, sigma, seed)``  cell-centred 7-point heterogeneous diffusion
+  whose face coefficient is the harmonic mean 2 k_i k_j / (k_i + k_j) of
+  k = exp(g), g ~ N(0, sigma^2) i.i.d. smoothed by three passes of a 3x3x3 box
+  mean truncated at the domain boundary; a domain-boundary face uses k_i, so
+  k == 1 reproduces ``poisson3d`` exactly.
+* ``graph_laplacian_spd(n, deg, shift, seed)``  random weighted graph
+  Laplacian plus ``shift * I`` (unstructured SPD test matrices).
+
+The paper's benchmark matrices (its Table 1) are not available; these
+synthetic operators stand in for its fluid-dynamics (Laplace-type) class.
+Grid ordering is lexicographic with x fastest: p = i + N*j + N*N*k.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class CSR:
+    """A square sparse matrix in compressed-sparse-row form."""
+
+    n: int
+    rowptr: np.ndarray  # int32 [n+1]
+    col: np.ndarray  # int32 [nnz]
+    val: np.ndarray  # float64 [nnz]
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def to_dense(self) -> np.ndarray:
+        d = np.zeros((self.n, self.n))
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        d[rows, self.col] = self.val
+        return d
+
+    def matvec(self, x: np.ndarray) -> np.ndarray:
+        """y = A x in float64 (used only to synthesise b = A x*)."""
+        prod = self.val * x[self.col]
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        return np.bincount(rows, weights=prod, minlength=self.n)
+
+
+def _finish(n: int, cols: np.ndarray, vals: np.ndarray, mask: np.ndarray, meta=None) -> CSR:
+    """Compress a dense (n, w) candidate table into CSR, keeping row-major order."""
+    counts = mask.sum(axis=1, dtype=np.int64)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    if rowptr[-1] >= 2**31:
+        raise ValueError("nnz does not fit int32")
+    col = cols[mask].astype(np.int32, copy=False)
+    val = vals[mask].astype(np.float64, copy=False)
+    return CSR(n, rowptr.astype(np.int32), np.ascontiguousarray(col), np.ascontiguousarray(val), meta or {})
+
+
+def poisson1d(n: int) -> CSR:
+    i = np.arange(n, dtype=np.int64)
+    cols = np.stack([i - 1, i, i + 1], axis=1)
+    vals = np.tile(np.array([-1.0, 2.0, -1.0]), (n, 1))
+    mask = (cols >= 0) & (cols < n)
+    return _finish(n, cols, vals, mask, {"kind": "poisson1d"})
+
+
+def poisson2d(N: int) -> CSR:
+    n = N * N
+    p = np.arange(n, dtype=np.int64)
+    ix, iy = p % N, p // N
+    cols = np.stack([p - N, p - 1, p, p + 1, p + N], axis=1)
+    vals = np.tile(np.array([-1.0, -1.0, 4.0, -1.0, -1.0]), (n, 1))
+    mask = np.stack([iy > 0, ix > 0, np.ones(n, bool), ix < N - 1, iy < N - 1], axis=1)
+    return _finish(n, cols, vals, mask, {"kind": "poisson2d", "N": N})
+
+
+def _box_mean_truncated(g: np.ndarray, passes: int) -> np.ndarray:
+    """Three-axis 3-point mean truncated at the boundary, applied ``passes`` times.
+
+    The truncated 3x3x3 box mean over in-bounds cells equals the composition
+    of the truncated 1-D means along each axis, because the in-bounds part of
+    the box is a product of intervals.
+    """
+    for _ in range(passes):
+        for ax in range(3):
+            s = g.copy()
+            cnt = np.ones(g.shape[ax])
+            lo = [slice(None)] * 3
+            hi = [slice(None)] * 3
+            lo[ax], hi[ax] = slice(1, None), slice(None, -1)
+            s[tuple(lo)] += g[tuple(hi)]
+            s[tuple(hi)] += g[tuple(lo)]
+            cnt[1:] += 1
+            cnt[:-1] += 1
+            shape = [1, 1, 1]
+            shape[ax] = -1
+            g = s / cnt.reshape(shape)
+    return g
+
+
+def _stencil7(N: int, kx_m, kx_p, ky_m, ky_p, kz_m, kz_p, diag, meta) -> CSR:
+    """Assemble a 7-point operator from per-cell face coefficients (arrays of n)."""
+    n = N ** 3
+    p = np.arange(n, dtype=np.int64)
+    ix, iy, iz = p % N, (p // N) % N, p // (N * N)
+    cols = np.stack([p - N * N, p - N, p - 1, p, p + 1, p + N, p + N * N], axis=1)
+    vals = np.stack([-kz_m, -ky_m, -kx_m, diag, -kx_p, -ky_p, -kz_p], axis=1)
+    mask = np.stack([iz > 0, iy > 0, ix > 0, np.ones(n, bool), ix < N - 1, iy < N - 1, iz < N - 1], axis=1)
+    return _finish(n, cols, vals, mask, meta)
+
+
+def poisson3d(N: int) -> CSR:
+    n = N ** 3
+    one = np.ones(n)
+    return _stencil7(N, one, one, one, one, one, one, 6.0 * one, {"kind": "poisson3d", "N": N})
+
+
+def diffusion_coefficients(N: int, sigma: float, rng: np.random.Generator) -> np.ndarray:
+    """k = exp(g), g ~ N(0, sigma^2) i.i.d. then three truncated 3x3x3 box means.
+
+    Returned as an (N, N, N) array indexed [z, y, x]."""
+    g = rng.normal(0.0, sigma, size=N ** 3).reshape(N, N, N)
+    g = _box_mean_truncated(g, passes=3)
+    return np.exp(g)
+
+
+def diffusion3d_from_k(k: np.ndarray, meta=None) -> CSR:
+    """Cell-centred 7-point operator with harmonic-mean face coefficients."""
+    N = k.shape[0]
+    n = N ** 3
+
+    def hm(a, b):
+        return 2.0 * a * b / (a + b)
+
+    kx_m = k.copy(); kx_m[:, :, 1:] = hm(k[:, :, 1:], k[:, :, :-1])
+    kx_p = k.copy(); kx_p[:, :, :-1] = hm(k[:, :, :-1], k[:, :, 1:])
+    ky_m = k.copy(); ky_m[:, 1:, :] = hm(k[:, 1:, :], k[:, :-1, :])
+    ky_p = k.copy(); ky_p[:, :-1, :] = hm(k[:, :-1, :], k[:, 1:, :])
+    kz_m = k.copy(); kz_m[1:, :, :] = hm(k[1:, :, :], k[:-1, :, :])
+    kz_p = k.copy(); kz_p[:-1, :, :] = hm(k[:-1, :, :], k[1:, :, :])
+    faces = [a.reshape(n) for a in (kx_m, kx_p, ky_m, ky_p, kz_m, kz_p)]
+    diag = ((((faces[4] + faces[2]) + faces[0]) + faces[1]) + faces[3]) + faces[5]
+    m = {"kind": "diffusion3d", "N": N, "k_min": float(k.min()), "k_max": float(k.max())}
+    m.update(meta or {})
+    return _stencil7(N, faces[0], faces[1], faces[2], faces[3], faces[4], faces[5], diag, m)
+
+
+def diffusion3d(N: int, sigma: float, seed: int) -> tuple[CSR, np.random.Generator]:
+    """Heterogeneous diffusion operator; returns (A, rng) with rng advanced past g."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = diffusion_coefficients(N, sigma, rng)
+    return diffusion3d_from_k(k, {"sigma": sigma, "seed": seed}), rng
+
+
+def graph_laplacian_spd(n: int, deg: int, shift: float, seed: int) -> CSR:
+    """Random weighted graph Laplacian (weights in [0.5, 1.5]) plus shift * I."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m = n * deg // 2
+    a = rng.integers(0, n, size=m)
+    b = rng.integers(0, n, size=m)
+    keep = a != b
+    a, b = a[keep], b[keep]
+    w = rng.uniform(0.5, 1.5, size=a.size)
+    d = np.zeros((n, n))
+    np.add.at(d, (a, b), -w)
+    np.add.at(d, (b, a), -w)
+    np.fill_diagonal(d, 0.0)
+    np.fill_diagonal(d, -d.sum(axis=1) + shift)
+    return dense_to_csr(d, {"kind": "graph_laplacian", "seed": seed})
+
+
+def dense_to_csr(d: np.ndarray, meta=None) -> CSR:
+    n = d.shape[0]
+    mask = d != 0.0
+    np.fill_diagonal(mask, True)
+    cols = np.broadcast_to(np.arange(n), (n, n))
+    return _finish(n, cols, d, mask, meta)
+
+
+def uniform(n: int, rng_or_seed) -> np.ndarray:
+    rng = rng_or_seed if isinstance(rng_or_seed, np.random.Generator) else np.random.Generator(np.random.PCG64(rng_or_seed))
+    return rng.uniform(-1.0, 1.0, size=n)
+
+
+@dataclass
+class Problem:
+    name: str
+    A: CSR
+    b: np.ndarray
+    xstar: np.ndarray | None
+
+
+def config1() -> Problem:
+    """2-D 5-point Poisson on 64 x 64, x* ~ U[-1,1] (seed 0), b = A x*."""
+    A = poisson2d(64)
+    xs = uniform(A.n, 0)
+    return Problem("poisson2d_64", A, A.matvec(xs), xs)
+
+
+def config2(N: int = 128) -> Problem:
+    """3-D 7-point Poisson on N^3 (128^3 by default), x* ~ U[-1,1] (seed 1), b = A x*."""
+    A = poisson3d(N)
+    xs = uniform(A.n, 1)
+    return Problem(f"poisson3d_{N}", A, A.matvec(xs), xs)
+
+
+def config3(N: int = 256, sigma: float = 2.0, seed: int = 2) -> Problem:
+    """Heterogeneous diffusion on N^3 (256^3 by default), b ~ U[-1,1] drawn after g."""
+    A, rng = diffusion3d(N, sigma, seed)
+    return Problem(f"diffusion3d_{N}", A, uniform(A.n, rng), None)
+
+
+def nnz_poisson2d(N: int) -> int:
+    """Closed form: 5n - 4N for the N x N interior 5-point stencil."""
+    return 5 * N * N - 4 * N
+
+
+def nnz_poisson3d(N: int) -> int:
+    """Closed form: 7n - 6N^2 for the N^3 interior 7-point stencil."""
+    return 7 * N ** 3 - 6 * N * N
