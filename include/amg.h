@@ -1,0 +1,196 @@
+/*
+ * amg.h -- C ABI of libamg: classical-AMG-preconditioned conjugate gradients
+ * on one GB300 GPU (method of Isotton, Frigo, Spiezia & Janna, "Chronos: a
+ * general purpose classical AMG solver for High Performance Computing",
+ * arXiv 2102.07417).
+ *
+ * Problem statement (Sec. 1, Eq. linSys): solve A x = b for a sparse
+ * symmetric positive definite A.  The preconditioner is one V-cycle
+ * (Algorithm 2) over a classical AMG hierarchy built by Algorithm 1; the
+ * Krylov solver is PCG with x0 given (zero in every benchmark) and the
+ * stopping rule ||r_k||_2 < rtol * ||b||_2 on the recursively updated
+ * residual (Sec. 4).  The solver interface mirrors the paper's LinSolver
+ * (Sec. 3.1): a preconditioner, the system, a right-hand side and an
+ * optional initial solution.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: AMG_OK (0) or a negative AMG_ERR_* code;
+ *     amg_status_string() names it and amg_last_error() gives detail.
+ *   - Streams are passed as `void *` holding a cudaStream_t (NULL = the
+ *     legacy default stream).  Work is enqueued on that stream.
+ *   - Indices are int32 (4-byte local numbering, Sec. 3.2); values FP64.
+ *   - The caller owns every buffer it passes; the library copies what it
+ *     keeps.  The hierarchy owns its device memory until amg_free().
+ *   - Device pointers must point to memory of the current CUDA device.
+ *   - A hierarchy is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef AMG_H
+#define AMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Status codes                                                         */
+/* ------------------------------------------------------------------ */
+#define AMG_OK 0
+#define AMG_ERR_INVALID_ARG (-1)    /* malformed CSR, bad parameter, NULL pointer */
+#define AMG_ERR_NOT_SPD (-2)        /* non-positive diagonal or Cholesky pivot */
+#define AMG_ERR_BREAKDOWN (-3)      /* CG breakdown: (p, A p) <= 0 or NaN */
+#define AMG_ERR_NO_CONVERGENCE (-4) /* maxit reached; x holds the last iterate */
+#define AMG_ERR_SETUP (-5)          /* coarsening stalled above the dense-solve limit */
+#define AMG_ERR_OOM (-6)            /* allocation failed (allocator returned NULL) */
+#define AMG_ERR_CUDA (-7)           /* a CUDA runtime call failed */
+#define AMG_ERR_TIMEOUT (-8)        /* a bounded device-side wait ran out */
+#define AMG_ERR_UNSUPPORTED (-9)    /* size beyond a documented limit */
+
+/* Precision modes of the solve phase (the set-up is always FP64). */
+#define AMG_PREC_FP64 0        /* hierarchy and V-cycle in FP64 */
+#define AMG_PREC_FP32 1        /* hierarchy stored and V-cycle run in FP32, outer PCG FP64, flexible beta */
+#define AMG_PREC_FP32_BF16PR 2 /* as FP32, with P and R stored in BF16 (FP32 accumulation) */
+
+/* Opaque hierarchy (Algorithm 1's levels A_k, P_k, R_k = P_k^T, D_k, L). */
+typedef struct amg_hierarchy amg_hierarchy;
+
+/* Optional device allocator (e.g. a PyTorch caching allocator).
+ * alloc(bytes, stream, ctx) returns device memory usable in stream order on
+ * `stream`, or NULL on failure; free(ptr, bytes, stream, ctx) releases it.
+ * A NULL allocator pointer, or NULL alloc/free members, selects
+ * cudaMallocAsync / cudaFreeAsync on the call's stream. */
+typedef void *(*amg_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*amg_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+typedef struct {
+  amg_alloc_fn alloc;
+  amg_free_fn free;
+  void *ctx;
+} amg_allocator;
+
+/* Square sparse matrix in CSR (Sec. 3.2 CSRMAT).  rowptr[n+1] starting at
+ * 0; colidx[nnz] strictly ascending within each row and in [0, n); val[nnz].
+ * The pattern must be structurally symmetric and every row must hold a
+ * positive diagonal entry.  on_device = 1: the three arrays are device
+ * pointers; 0: host pointers. */
+typedef struct {
+  int32_t n;
+  int32_t nnz;
+  const int32_t *rowptr;
+  const int32_t *colidx;
+  const double *val;
+  int32_t on_device;
+} amg_csr;
+
+/* Set-up and cycle parameters (Sec. 2; Algorithm 1 and 2). */
+typedef struct {
+  double theta;       /* strength threshold of the classical measure (Eq. cla filter), (0, 1]; 0.25 */
+  uint64_t seed;      /* seed of the counter-based SplitMix64 stream of the PMIS measures; 0 */
+  int32_t max_coarse; /* a level with at most this many rows is factorised densely; 64 */
+  int32_t max_levels; /* hard cap on the number of levels, 1..40; 25 */
+  double omega;       /* Jacobi damping of the smoother S = I - omega D^-1 A (Eq. smoother); 2/3 */
+  int32_t nu1, nu2;   /* pre- and post-smoothing steps (Eq. twoGridOp), 0..8 each; 1, 1 */
+  int32_t precision;  /* AMG_PREC_*; AMG_PREC_FP64 */
+  int32_t block_size; /* unknowns per node for nodal strength; 1 (only 1 is supported) */
+} amg_params;
+
+/* Fills *p with the defaults above.  Returns AMG_ERR_INVALID_ARG if p is NULL. */
+int amg_params_default(amg_params *p);
+
+/* Algorithm 1 (AMG_SetUp), recursively on the GPU: strength of connection
+ * (Eq. cla, read as Ruge-Stueben), PMIS C/F splitting (Sec. 2.2), direct
+ * interpolation P = [W; I] (Eq. prolOperator), R = P^T and the Galerkin
+ * product A_{k+1} = R (A_k P) (Eq. AcDef) as a GPU SpGEMM whose summation
+ * order is canonical (the hierarchy is reproducible bit for bit), until a
+ * level has at most max_coarse rows, coarsening stalls (n_{k+1} = 0 or
+ * n_{k+1} > 0.9 n_k), or max_levels is reached; the last level is factorised
+ * by a dense Cholesky A_L = L L^T (at most 4096 rows, else AMG_ERR_SETUP).
+ * A is copied; the caller may free it on return.  `alloc` may be NULL.
+ * Synchronises `stream` (coarse sizes are needed on the host).
+ * On error *out is NULL and nothing is leaked. */
+int amg_setup(const amg_csr *A, const amg_params *params, const amg_allocator *alloc, void *stream,
+              amg_hierarchy **out);
+
+/* PCG preconditioned by one V-cycle (Algorithm 2) per iteration.
+ * b, x: device arrays of n doubles; x holds x0 on entry and the solution
+ * (or the last iterate) on return.  Stops when ||r_k||_2 < rtol ||b||_2
+ * (recursive residual, Sec. 4) or after maxit iterations.  In the FP32
+ * precision modes the flexible (Polak-Ribiere) beta is used.
+ * iters (may be NULL) receives the iteration count; res_hist (host, may be
+ * NULL) receives ||r_k||_2 for k = 0..min(iters, hist_cap-1).
+ * Returns when the solve has finished (the stream is synchronised).
+ * AMG_ERR_NO_CONVERGENCE / AMG_ERR_BREAKDOWN leave the last iterate in x. */
+int amg_pcg_solve(amg_hierarchy *h, const double *b, double *x, double rtol, int32_t maxit, void *stream,
+                  int32_t *iters, double *res_hist, int32_t hist_cap);
+
+/* One application of the preconditioner z = B y (Algorithm 2 on level 0):
+ * y, z device arrays of n doubles (FP64 in and out in every precision mode). */
+int amg_vcycle_apply(amg_hierarchy *h, const double *y, double *z, void *stream);
+
+/* y = A_k x with the FP64 copy of level k's operator; x, y device arrays of n_k doubles. */
+int amg_spmv(amg_hierarchy *h, int32_t level, const double *x, double *y, void *stream);
+
+/* Result of a one-call solve. */
+typedef struct {
+  int32_t iters;
+  int32_t nlevels;
+  double final_residual; /* ||r||_2 of the recursive residual at exit */
+  double setup_ms;       /* T_p: amg_setup wall time (ms), host-measured */
+  double solve_ms;       /* T_s: amg_pcg_solve wall time (ms), host-measured */
+} amg_result;
+
+/* Set-up + solve + free in one call (T_t = T_p + T_s, Sec. 4).  A, b, x are
+ * host or device according to A->on_device (b and x follow A).  x holds x0 on
+ * entry.  Host buffers are copied to and from the device inside the call. */
+int amg_solve(const amg_csr *A, const double *b, double *x, const amg_params *params, double rtol,
+              int32_t maxit, const amg_allocator *alloc, void *stream, amg_result *res);
+
+/* Hierarchy sizes.  cap = capacity of the per-level arrays (any may be NULL):
+ * n_k[k] rows of A_k, nnz_k[k] nonzeros of A_k, nnzP_k[k] nonzeros of P_k
+ * (0 on the last level).  cgd = sum n_k / n_0 and cop = sum nnz_k / nnz_0
+ * (grid and operator complexities, Sec. 4). */
+int amg_hierarchy_info(const amg_hierarchy *h, int32_t *nlevels, int32_t cap, int64_t *n_k, int64_t *nnz_k,
+                       int64_t *nnzP_k, double *cgd, double *cop);
+
+/* Copies level k of the FP64 hierarchy to host arrays (any may be NULL):
+ * cf[n_k] (1 = C, 0 = F; all zero on the last level), A_k as CSR
+ * (A_rowptr[n_k+1], A_col[nnz_k], A_val[nnz_k]) and P_k as CSR
+ * (P_rowptr[n_k+1], P_col[nnzP_k], P_val[nnzP_k]; ignored on the last level).
+ * Synchronises the hierarchy's stream. */
+int amg_hierarchy_export(const amg_hierarchy *h, int32_t level, int8_t *cf, int32_t *A_rowptr, int32_t *A_col,
+                         double *A_val, int32_t *P_rowptr, int32_t *P_col, double *P_val);
+
+/* Device bytes held by the hierarchy (for admission by free HBM). */
+size_t amg_hierarchy_bytes(const amg_hierarchy *h);
+
+/* Releases the hierarchy (stream-ordered on the stream given to amg_setup). NULL is a no-op. */
+void amg_free(amg_hierarchy *h);
+
+/* Per-kernel timing of the solve phase with CUDA events on the launch stream.
+ * amg_profile_enable(h, 1) starts recording (and clears the totals); 0 stops.
+ * amg_profile_read(h, kernel, &launches, &ms, &bytes) returns, for kernel class
+ * `kernel` (AMG_K_*), the number of launches, their summed event-timed
+ * duration and the algorithmic bytes they move (same accounting as the
+ * roofline).  Totals are complete once the solve call has returned. */
+#define AMG_K_SPMV_DOT 0      /* q = A p and (p, q) */
+#define AMG_K_PCG_UPDATE 1    /* x += alpha p, r -= alpha q, ||r||, smoother input */
+#define AMG_K_SMOOTH_RESID 2  /* r_k = y_k - A_k s_k (pre-smoothed residual) */
+#define AMG_K_RESTRICT 3      /* y_{k+1} = R_k r_k */
+#define AMG_K_PROLONG 4       /* t_k = s_k + P_k z_{k+1} */
+#define AMG_K_SMOOTH_POST 5   /* z_k = t_k + omega D^-1 (y_k - A_k t_k) */
+#define AMG_K_COARSE 6        /* z_L = L^-T L^-1 y_L */
+#define AMG_K_DIRECTION 7     /* p = z + beta p */
+#define AMG_K_OTHER 8         /* initial residual, extra sweeps, copies */
+#define AMG_K_COUNT 9
+int amg_profile_enable(amg_hierarchy *h, int32_t on);
+int amg_profile_read(const amg_hierarchy *h, int32_t kernel, int64_t *launches, double *ms, double *bytes);
+
+/* Static strings; never NULL. */
+const char *amg_status_string(int status);
+const char *amg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMG_H */

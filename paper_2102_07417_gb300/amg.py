@@ -1,0 +1,313 @@
+"""Python binding of libamg's C ABI (include/amg.h): argument marshalling only.
+
+Every step of the set-up and the solve runs in libamg's CUDA kernels; this
+module converts numpy arrays / torch tensors to pointers, passes the current
+torch CUDA stream, and optionally routes libamg's device allocations through
+PyTorch's caching allocator.  There is no CPU fallback: if libamg.so cannot
+be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AMG_OK = 0
+AMG_ERR_INVALID_ARG = -1
+AMG_ERR_NOT_SPD = -2
+AMG_ERR_BREAKDOWN = -3
+AMG_ERR_NO_CONVERGENCE = -4
+AMG_ERR_SETUP = -5
+AMG_ERR_OOM = -6
+AMG_ERR_CUDA = -7
+AMG_ERR_TIMEOUT = -8
+AMG_ERR_UNSUPPORTED = -9
+
+PREC_FP64, PREC_FP32, PREC_FP32_BF16PR = 0, 1, 2
+
+K_SPMV_DOT, K_PCG_UPDATE, K_SMOOTH_RESID, K_RESTRICT, K_PROLONG, K_SMOOTH_POST, K_COARSE, K_DIRECTION, K_OTHER = range(9)
+KERNEL_NAMES = ["spmv_dot", "pcg_update", "smooth_resid", "restrict", "prolong", "smooth_post", "coarse",
+                "direction", "other"]
+
+# Names exported by the C ABI (each declared in include/amg.h).
+EXPORTS = ["amg_params_default", "amg_setup", "amg_pcg_solve", "amg_vcycle_apply", "amg_spmv", "amg_solve",
+           "amg_hierarchy_info", "amg_hierarchy_export", "amg_hierarchy_bytes", "amg_free", "amg_profile_enable",
+           "amg_profile_read", "amg_status_string", "amg_last_error"]
+
+
+class AmgError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {detail} (status {code})")
+        self.code = code
+
+
+class Csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("rowptr", C.c_void_p), ("colidx", C.c_void_p),
+                ("val", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("theta", C.c_double), ("seed", C.c_uint64), ("max_coarse", C.c_int32), ("max_levels", C.c_int32),
+                ("omega", C.c_double), ("nu1", C.c_int32), ("nu2", C.c_int32), ("precision", C.c_int32),
+                ("block_size", C.c_int32)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("nlevels", C.c_int32), ("final_residual", C.c_double),
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libamg.so (building it first if asked); raises if it is not there."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not os.path.exists(path):
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libamg.so not found at {path}; run paper_2102_07417_gb300.build.build()")
+    L = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    L.amg_params_default.argtypes = [C.POINTER(Params)]
+    L.amg_setup.argtypes = [C.POINTER(Csr), C.POINTER(Params), C.POINTER(Allocator), vp, C.POINTER(vp)]
+    L.amg_pcg_solve.argtypes = [vp, vp, vp, dbl, i32, vp, C.POINTER(i32), vp, i32]
+    L.amg_vcycle_apply.argtypes = [vp, vp, vp, vp]
+    L.amg_spmv.argtypes = [vp, i32, vp, vp, vp]
+    L.amg_solve.argtypes = [C.POINTER(Csr), vp, vp, C.POINTER(Params), dbl, i32, C.POINTER(Allocator), vp,
+                            C.POINTER(Result)]
+    L.amg_hierarchy_info.argtypes = [vp, C.POINTER(i32), i32, vp, vp, vp, C.POINTER(dbl), C.POINTER(dbl)]
+    L.amg_hierarchy_export.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.amg_hierarchy_bytes.argtypes = [vp]
+    L.amg_hierarchy_bytes.restype = C.c_size_t
+    L.amg_free.argtypes = [vp]
+    L.amg_free.restype = None
+    L.amg_profile_enable.argtypes = [vp, i32]
+    L.amg_profile_read.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]
+    L.amg_status_string.argtypes = [C.c_int]
+    L.amg_status_string.restype = C.c_char_p
+    L.amg_last_error.argtypes = []
+    L.amg_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def check(code: int, where: str):
+    if code != AMG_OK:
+        L = load()
+        raise AmgError(code, where, f"{L.amg_status_string(code).decode()}: {L.amg_last_error().decode()}")
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    check(load().amg_params_default(C.byref(p)), "amg_params_default")
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class TorchAllocator:
+    """Routes libamg allocations through torch's caching allocator."""
+
+    def __init__(self):
+        import torch
+
+        self._torch = torch
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
+            except Exception:  # out of memory: libamg turns NULL into AMG_ERR_OOM
+                return None
+
+        def _free(ptr, nbytes, stream, ctx):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._a = ALLOC_FN(_alloc)
+        self._f = FREE_FN(_free)
+        self.struct = Allocator(self._a, self._f, None)
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+class Hierarchy:
+    """An AMG hierarchy resident on the GPU (Algorithm 1), with PCG / V-cycle entry points.
+
+    ``A`` is a CSR object with numpy (host) arrays ``rowptr``, ``col``, ``val``
+    and ``n``, or the same fields as CUDA torch tensors (int32 / float64).
+    """
+
+    def __init__(self, A, params: Params | None = None, stream=None, torch_allocator: bool = True, **kw):
+        import torch
+
+        L = load()
+        self.params = params if params is not None else default_params(**kw)
+        self._alloc = TorchAllocator() if torch_allocator else None
+        on_dev = isinstance(A.rowptr, torch.Tensor) and A.rowptr.is_cuda
+        if on_dev:
+            rp, ci, v = A.rowptr, A.col, A.val
+            ptrs = (_ptr(rp), _ptr(ci), _ptr(v))
+        else:
+            rp = np.ascontiguousarray(A.rowptr, np.int32)
+            ci = np.ascontiguousarray(A.col, np.int32)
+            v = np.ascontiguousarray(A.val, np.float64)
+            ptrs = (rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+        self.n = int(A.n)
+        self.nnz = int(rp[-1]) if not on_dev else int(rp[-1].item())
+        csr = Csr(self.n, self.nnz, *ptrs, 1 if on_dev else 0)
+        self.stream = _stream_handle(stream)
+        h = C.c_void_p()
+        check(L.amg_setup(C.byref(csr), C.byref(self.params), C.byref(self._alloc.struct) if self._alloc else None,
+                          self.stream, C.byref(h)), "amg_setup")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().amg_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- solve phase ---------------------------------------------------------
+    def solve(self, b, x=None, rtol: float = 1e-8, maxit: int = 500, hist: bool = False, stream=None):
+        """PCG to ||r|| < rtol ||b||.  b, x: CUDA float64 tensors (x holds x0; default zeros).
+        Returns (x, iters, status, history or None); raises on errors other than non-convergence."""
+        import torch
+
+        if x is None:
+            x = torch.zeros_like(b)
+        hbuf = np.zeros(maxit + 1) if hist else None
+        it = C.c_int32(0)
+        st = load().amg_pcg_solve(self.h, _ptr(b), _ptr(x), rtol, maxit, _stream_handle(stream) if stream else self.stream,
+                                  C.byref(it), hbuf.ctypes.data if hist else None, maxit + 1 if hist else 0)
+        if st not in (AMG_OK, AMG_ERR_NO_CONVERGENCE):
+            check(st, "amg_pcg_solve")
+        return x, it.value, st, (hbuf[: it.value + 1].copy() if hist else None)
+
+    def vcycle(self, y, z=None, stream=None):
+        import torch
+
+        if z is None:
+            z = torch.empty_like(y)
+        check(load().amg_vcycle_apply(self.h, _ptr(y), _ptr(z), _stream_handle(stream) if stream else self.stream),
+              "amg_vcycle_apply")
+        return z
+
+    def spmv(self, level: int, x, y=None, stream=None):
+        import torch
+
+        if y is None:
+            y = torch.empty(self.info()["n"][level], dtype=torch.float64, device=x.device)
+        check(load().amg_spmv(self.h, level, _ptr(x), _ptr(y), _stream_handle(stream) if stream else self.stream),
+              "amg_spmv")
+        return y
+
+    # -- inspection ----------------------------------------------------------
+    def info(self) -> dict:
+        L = load()
+        nl = C.c_int32()
+        cap = 64
+        n = np.zeros(cap, np.int64)
+        nz = np.zeros(cap, np.int64)
+        npz = np.zeros(cap, np.int64)
+        cgd, cop = C.c_double(), C.c_double()
+        check(L.amg_hierarchy_info(self.h, C.byref(nl), cap, n.ctypes.data, nz.ctypes.data, npz.ctypes.data,
+                                   C.byref(cgd), C.byref(cop)), "amg_hierarchy_info")
+        k = nl.value
+        return {"nlevels": k, "n": n[:k].tolist(), "nnz": nz[:k].tolist(), "nnzP": npz[:k].tolist(),
+                "cgd": cgd.value, "cop": cop.value}
+
+    def export(self, level: int) -> dict:
+        inf = self.info()
+        n, nnz, nnzp = inf["n"][level], inf["nnz"][level], inf["nnzP"][level]
+        cf = np.zeros(n, np.int8)
+        arp, aci, av = np.zeros(n + 1, np.int32), np.zeros(max(nnz, 1), np.int32), np.zeros(max(nnz, 1))
+        prp, pci, pv = np.zeros(n + 1, np.int32), np.zeros(max(nnzp, 1), np.int32), np.zeros(max(nnzp, 1))
+        check(load().amg_hierarchy_export(self.h, level, cf.ctypes.data, arp.ctypes.data, aci.ctypes.data,
+                                          av.ctypes.data, prp.ctypes.data, pci.ctypes.data, pv.ctypes.data),
+              "amg_hierarchy_export")
+        return {"cf": cf, "A": (arp, aci[:nnz], av[:nnz]), "P": (prp, pci[:nnzp], pv[:nnzp])}
+
+    def nbytes(self) -> int:
+        return int(load().amg_hierarchy_bytes(self.h))
+
+    def profile(self, on: bool):
+        check(load().amg_profile_enable(self.h, 1 if on else 0), "amg_profile_enable")
+
+    def profile_read(self) -> dict:
+        out = {}
+        for k, name in enumerate(KERNEL_NAMES):
+            n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+            check(load().amg_profile_read(self.h, k, C.byref(n), C.byref(ms), C.byref(by)), "amg_profile_read")
+            out[name] = {"launches": n.value, "ms": ms.value, "bytes": by.value}
+        return out
+
+
+def solve(A, b, x0=None, params: Params | None = None, rtol: float = 1e-8, maxit: int = 500, stream=None,
+          torch_allocator: bool = True, **kw):
+    """One-call set-up + solve (amg_solve).  Host (numpy) or device (torch CUDA) inputs.
+    Returns (x, Result)."""
+    import torch
+
+    L = load()
+    prm = params if params is not None else default_params(**kw)
+    on_dev = isinstance(A.rowptr, torch.Tensor) and A.rowptr.is_cuda
+    keep = []
+    if on_dev:
+        ptrs = (_ptr(A.rowptr), _ptr(A.col), _ptr(A.val))
+        nnz = int(A.rowptr[-1].item())
+        x = torch.zeros_like(b) if x0 is None else x0
+        bp, xp = _ptr(b), _ptr(x)
+    else:
+        rp = np.ascontiguousarray(A.rowptr, np.int32)
+        ci = np.ascontiguousarray(A.col, np.int32)
+        v = np.ascontiguousarray(A.val, np.float64)
+        keep += [rp, ci, v]
+        ptrs = (rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+        nnz = int(rp[-1])
+        bb = np.ascontiguousarray(b, np.float64)
+        x = np.zeros(A.n) if x0 is None else np.ascontiguousarray(x0, np.float64).copy()
+        keep.append(bb)
+        bp, xp = bb.ctypes.data, x.ctypes.data
+    csr = Csr(int(A.n), nnz, *ptrs, 1 if on_dev else 0)
+    alloc = TorchAllocator() if torch_allocator else None
+    res = Result()
+    st = L.amg_solve(C.byref(csr), bp, xp, C.byref(prm), rtol, maxit, C.byref(alloc.struct) if alloc else None,
+                     _stream_handle(stream), C.byref(res))
+    if st not in (AMG_OK, AMG_ERR_NO_CONVERGENCE):
+        check(st, "amg_solve")
+    return x, res

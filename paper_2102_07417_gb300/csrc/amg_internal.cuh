@@ -1,0 +1,171 @@
+// Internal declarations of libamg (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "amg.h"
+
+namespace amg {
+
+constexpr int kMaxLevels = 40;
+constexpr int kMaxDense = 4096;  // largest last level factorised densely
+constexpr int kNumSMs = 152;     // GB300; grids below are multiples of this
+
+void set_error(const char *fmt, ...);
+
+// Thrown internally, converted to a status code at the C boundary.
+struct Status {
+  int code;
+};
+
+#define AMG_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      ::amg::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      throw ::amg::Status{AMG_ERR_CUDA};                                                     \
+    }                                                                                        \
+  } while (0)
+
+#define AMG_CHECK_LAUNCH() AMG_CUDA(cudaGetLastError())
+
+// Device memory through the caller's allocator (or cudaMallocAsync).
+struct Mem {
+  amg_allocator alloc{};
+  bool callbacks = false;
+  cudaStream_t stream = nullptr;
+  size_t live_bytes = 0;
+  std::unordered_map<void *, size_t> live;  // every allocation not yet returned
+
+  void *get(size_t bytes);   // throws Status{AMG_ERR_OOM} on failure
+  void put(void *p, size_t bytes);
+  void free_all();
+  template <typename T>
+  T *get_n(size_t n) {
+    return static_cast<T *>(get(n * sizeof(T)));
+  }
+};
+
+// A device buffer owned by a Mem, freed on destruction (used for temporaries).
+template <typename T>
+struct Buf {
+  Mem *m = nullptr;
+  T *p = nullptr;
+  size_t n = 0;
+  Buf() = default;
+  Buf(Mem &mem, size_t count) : m(&mem), p(mem.get_n<T>(count)), n(count) {}
+  Buf(const Buf &) = delete;
+  Buf &operator=(const Buf &) = delete;
+  Buf(Buf &&o) noexcept : m(o.m), p(o.p), n(o.n) { o.p = nullptr; }
+  Buf &operator=(Buf &&o) noexcept {
+    reset();
+    m = o.m; p = o.p; n = o.n; o.p = nullptr;
+    return *this;
+  }
+  ~Buf() { reset(); }
+  void reset() {
+    if (p && m) m->put(p, n * sizeof(T));
+    p = nullptr;
+    n = 0;
+  }
+  T *release() {
+    T *q = p;
+    p = nullptr;
+    return q;
+  }
+};
+
+// CSR matrix on the device (int32 indices).  Value arrays for each storage type.
+struct DCsr {
+  int n = 0, ncols = 0;
+  int64_t nnz = 0;
+  int *rp = nullptr, *ci = nullptr;
+  double *v = nullptr;           // FP64 master copy
+  float *v32 = nullptr;          // FP32 copy (FP32 modes)
+  __nv_bfloat16 *v16 = nullptr;  // BF16 copy (P and R in the BF16 ablation)
+};
+
+// Scalars of one PCG solve, resident on the device.
+struct PcgScalars {
+  double rho;     // (r_k, z_k)
+  double alpha;   // rho / (p, q)
+  double beta;
+  double rr;      // (r, r)
+  double bb;      // (b, b)
+  double tol;     // rtol * ||b||
+  double pq, rz, zq;
+  int iters;
+  int done;       // 1: converged or failed; every kernel of later iterations returns at once
+  int status;     // AMG_OK, AMG_ERR_BREAKDOWN
+  int maxit;
+};
+
+struct Level {
+  DCsr A, P, R;   // P, R empty on the last level
+  int8_t *cf = nullptr;    // C/F of this level (export), nullptr on the last level
+  double *wd = nullptr;    // omega / a_ii (FP64)
+  float *wd32 = nullptr;   // omega / a_ii (FP32)
+  // V-cycle work vectors (type per precision mode; only one set is allocated)
+  void *y = nullptr, *s = nullptr, *r = nullptr, *z = nullptr, *w = nullptr;
+};
+
+struct Profile {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // pool of events, two per recorded launch
+  std::vector<int> kind;        // kernel class of each recorded pair
+  std::vector<double> bytes;    // algorithmic bytes of each recorded pair
+  size_t used = 0;
+  int64_t launches[AMG_K_COUNT] = {};
+  double ms[AMG_K_COUNT] = {};
+  double total_bytes[AMG_K_COUNT] = {};
+};
+
+}  // namespace amg
+
+struct amg_hierarchy {
+  amg::Mem mem;
+  amg_params prm{};
+  int nlevels = 0;
+  amg::Level lev[amg::kMaxLevels];
+  double *L = nullptr;  // dense Cholesky factor of the last level (row-major, lower)
+  int nL = 0;
+  // PCG vectors (level 0, FP64)
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  amg::PcgScalars *sc = nullptr;   // device scalars
+  double *hist = nullptr;          // device residual history
+  int hist_cap = 0;
+  double *partials = nullptr;      // per-block reduction partials (3 per block)
+  unsigned int *counter = nullptr; // last-block tickets
+  int *d_zero = nullptr;           // a device int that stays 0 ("never done")
+  int *h_done = nullptr;           // mapped pinned host flag (written by the device)
+  int *d_done = nullptr;           // its device alias
+  cudaEvent_t iter_ev[2] = {nullptr, nullptr};
+  amg::Profile prof;
+  size_t bytes = 0;
+};
+
+namespace amg {
+
+// set-up (setup.cu)
+void build_hierarchy(amg_hierarchy *h, const amg_csr &A);
+// solve (solve.cu)
+void prepare_solve(amg_hierarchy *h);
+int pcg_solve(amg_hierarchy *h, const double *b, double *x, double rtol, int maxit, int *iters, double *hist,
+              int hist_cap);
+void vcycle_apply(amg_hierarchy *h, const double *y, double *z);
+void spmv_level(amg_hierarchy *h, int level, const double *x, double *y);
+void release_solve(amg_hierarchy *h);
+
+// device-wide exclusive scan of n int32 counts into out[0..n] (out[n] = total); returns total
+int64_t scan_counts(Mem &mem, const int *in, int *out, int n);
+
+inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+
+}  // namespace amg

@@ -1,0 +1,869 @@
+// setup.cu -- Algorithm 1 (AMG_SetUp) on the GPU.
+//
+// Per level k, all on the device:
+//   strength of connection   (Sec. 2.2, Eq. cla read as Ruge-Stueben, threshold filter)
+//   PMIS C/F splitting       (Sec. 2.2; synchronous rounds, SplitMix64 measures)
+//   direct interpolation     P = [W; I] in the original ordering (Eq. prolOperator)
+//   R = P^T                  (CSR transpose, rows sorted)
+//   A_{k+1} = R (A P)        (Eq. AcDef) by a hash-based SpGEMM with a canonical summation order
+// and a dense Cholesky of the last level (Algorithm 1, direct factorisation).
+//
+// This translation unit is compiled with --fmad=false and uses explicit
+// round-to-nearest intrinsics for every floating-point operation that
+// decides the hierarchy, so that the hierarchy is reproducible bit for bit:
+//   (A P)_{iJ} = sum over j ascending of a_ij * P_jJ, each product rounded,
+//   then added left to right from 0; (A_c)_{IJ} likewise over i ascending in
+//   row I of R.  A one-ulp difference at an exact strength tie would change
+//   the next level's strong graph, so this order is part of the method here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "amg_internal.cuh"
+
+namespace amg {
+
+namespace {
+
+constexpr int TPB = 256;
+
+// ------------------------------------------------------------------ scan --
+constexpr int SCAN_T = 256, SCAN_ITEMS = 8, SCAN_TILE = SCAN_T * SCAN_ITEMS;
+
+__device__ __forceinline__ long long warp_incl_scan(long long v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan of one value per thread across the block; returns the block total in *total.
+__device__ long long block_excl_scan(long long v, long long *total) {
+  __shared__ long long warp_tot[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long inc = warp_incl_scan(v);
+  if (lane == 31) warp_tot[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    long long t = lane < nw ? warp_tot[lane] : 0;
+    long long ti = warp_incl_scan(t);
+    if (lane < nw) warp_tot[lane] = ti - t;
+    if (lane == nw - 1) warp_tot[31] = ti;
+  }
+  __syncthreads();
+  long long res = warp_tot[w] + inc - v;
+  *total = warp_tot[31];
+  __syncthreads();
+  return res;
+}
+
+__global__ void k_scan_reduce(const int *__restrict__ in, int n, long long *__restrict__ bsum) {
+  long long s = 0;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  for (int t = threadIdx.x; t < SCAN_TILE; t += SCAN_T) {
+    int64_t i = base + t;
+    if (i < n) s += in[i];
+  }
+  long long tot;
+  block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_blocks(long long *bsum, int nb) {
+  long long carry = 0;
+  for (int c = 0; c < nb; c += SCAN_T) {
+    int i = c + threadIdx.x;
+    long long v = i < nb ? bsum[i] : 0, tot;
+    long long ex = block_excl_scan(v, &tot);
+    if (i < nb) bsum[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void k_scan_apply(const int *__restrict__ in, int n, const long long *__restrict__ boff,
+                             int *__restrict__ out) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  long long v[SCAN_ITEMS], s = 0;
+#pragma unroll
+  for (int t = 0; t < SCAN_ITEMS; ++t) {
+    int64_t i = base + t;
+    v[t] = i < n ? in[i] : 0;
+    s += v[t];
+  }
+  long long tot;
+  long long ex = block_excl_scan(s, &tot) + boff[blockIdx.x];
+#pragma unroll
+  for (int t = 0; t < SCAN_ITEMS; ++t) {
+    int64_t i = base + t;
+    if (i < n) out[i] = static_cast<int>(ex);
+    ex += v[t];
+  }
+}
+
+__global__ void k_set_last(int *out, int n, const long long *total) { out[n] = static_cast<int>(*total); }
+
+// ------------------------------------------------------- validation --
+// flags[0]: malformed CSR, flags[1]: non-positive or missing diagonal,
+// flags[2]: pattern not structurally symmetric, flags[3]: hash table overflow,
+// flags[4]: Cholesky pivot <= 0
+__global__ void k_validate(int n, int64_t nnz, const int *__restrict__ rp, const int *__restrict__ ci,
+                           const double *__restrict__ a, int *flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = rp[i], e = rp[i + 1];
+  if (b < 0 || e < b || e > nnz || (i == 0 && b != 0) || (i == n - 1 && e != nnz)) {
+    flags[0] = 1;
+    return;
+  }
+  bool diag = false;
+  for (int p = b; p < e; ++p) {
+    const int j = ci[p];
+    if (j < 0 || j >= n || (p > b && j <= ci[p - 1])) {
+      flags[0] = 1;
+      return;
+    }
+    if (j == i) {
+      diag = true;
+      if (!(a[p] > 0.0)) flags[1] = 1;
+    }
+  }
+  if (!diag) flags[1] = 1;
+}
+
+// ----------------------------------------------------------- strength --
+// S[p] = 1 iff ci[p] != i, m_i = max_{k != i} (-a_ik) > 0 and -a[p] >= theta * m_i.
+__global__ void k_strength(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                           const double *__restrict__ a, double theta, uint8_t *__restrict__ S) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = rp[i], e = rp[i + 1];
+  double m = 0.0;
+  bool have = false;
+  for (int p = b; p < e; ++p) {
+    if (ci[p] == i) continue;
+    const double t = -a[p];
+    if (!have || t > m) m = t;
+    have = true;
+  }
+  const double thr = __dmul_rn(theta, m);
+  for (int p = b; p < e; ++p) {
+    uint8_t s = 0;
+    if (have && m > 0.0 && ci[p] != i && -a[p] >= thr) s = 1;
+    S[p] = s;
+  }
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) evaluated at counter c: the c-th output
+// of the generator seeded with `seed`.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t c) {
+  uint64_t z = seed + c * 0x9E3779B97F4A7C15ull;
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+
+enum : int8_t { ST_U = 0, ST_C = 1, ST_F = 2, ST_NEWC = 3 };
+
+__device__ __forceinline__ int find_col(const int *__restrict__ ci, int b, int e, int key) {
+  int lo = b, hi = e - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int c = ci[mid];
+    if (c == key) return mid;
+    if (c < key) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+// ST[p] = S at the mirrored position (j, i): 1 iff i strongly influences j.
+// lambda_i = |S_i^T| + u_i, u_i from the counter-based stream; points that
+// influence nobody start as F.
+__global__ void k_pmis_init(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                            const uint8_t *__restrict__ S, uint8_t *__restrict__ ST, double *__restrict__ lam,
+                            int8_t *__restrict__ st, uint64_t seed, int level, int *flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int cnt = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const int j = ci[p];
+    uint8_t t = 0;
+    if (j != i) {
+      const int q = find_col(ci, rp[j], rp[j + 1], i);
+      if (q < 0) flags[2] = 1;
+      else t = S[q];
+    }
+    ST[p] = t;
+    cnt += t;
+  }
+  const uint64_t c = ((uint64_t)(uint32_t)level << 32) + (uint64_t)(uint32_t)i + 1ull;
+  const double u = (double)(splitmix64_at(seed, c) >> 11) * 0x1.0p-53;
+  lam[i] = __dadd_rn((double)cnt, u);
+  st[i] = cnt == 0 ? ST_F : ST_U;
+}
+
+// Selection step of a round: an undecided point beating every undecided
+// strong neighbour (either direction) becomes a new C point.
+__global__ void k_pmis_select(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                              const uint8_t *__restrict__ S, const uint8_t *__restrict__ ST,
+                              const double *__restrict__ lam, const int8_t *__restrict__ st_old,
+                              int8_t *__restrict__ st_new) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int8_t s = st_old[i];
+  if (s != ST_U) {
+    st_new[i] = s;
+    return;
+  }
+  const double li = lam[i];
+  bool is_max = true;
+  for (int p = rp[i]; p < rp[i + 1] && is_max; ++p) {
+    if (!(S[p] | ST[p])) continue;
+    const int j = ci[p];
+    if (st_old[j] != ST_U) continue;
+    const double lj = lam[j];
+    if (lj > li || (lj == li && j > i)) is_max = false;
+  }
+  st_new[i] = is_max ? ST_NEWC : ST_U;
+}
+
+// Update step: undecided points that depend strongly on a new C point become
+// F; new C points become C.  Counts the points still undecided.
+__global__ void k_pmis_update(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                              const uint8_t *__restrict__ S, const int8_t *__restrict__ st_new,
+                              int8_t *__restrict__ st_next, int *undecided) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool und = false;
+  if (i < n) {
+    const int8_t s = st_new[i];
+    int8_t o = s;
+    if (s == ST_NEWC) {
+      o = ST_C;
+    } else if (s == ST_U) {
+      bool f = false;
+      for (int p = rp[i]; p < rp[i + 1] && !f; ++p)
+        if (S[p] && st_new[ci[p]] == ST_NEWC) f = true;
+      o = f ? ST_F : ST_U;
+      und = !f;
+    }
+    st_next[i] = o;
+  }
+  const unsigned b = __ballot_sync(0xffffffffu, und);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(undecided, __popc(b));
+}
+
+__global__ void k_cf_out(int n, const int8_t *__restrict__ st, int8_t *__restrict__ cf, int *__restrict__ isC) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = st[i] == ST_C;
+  cf[i] = (int8_t)c;
+  isC[i] = c;
+}
+
+// ------------------------------------------------------ interpolation --
+__global__ void k_interp_count(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                               const uint8_t *__restrict__ S, const int8_t *__restrict__ cf,
+                               int *__restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (cf[i]) {
+    cnt[i] = 1;
+    return;
+  }
+  int c = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const int j = ci[p];
+    if (j != i && S[p] && cf[j]) ++c;
+  }
+  cnt[i] = c;
+}
+
+// Direct interpolation with every sum over the row in ascending column order:
+//   alpha = sum_{N_i} a^- / sum_{P_i} a^-,  beta = sum_{N_i} a^+ / sum_{P_i} a^+,
+//   at = a_ii + sum_{N_i} a^+ when P_i holds no positive entry, else a_ii,
+//   w_ij = -(alpha a_ij) / at for a_ij < 0, -(beta a_ij) / at for a_ij > 0.
+__global__ void k_interp_fill(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                              const double *__restrict__ a, const uint8_t *__restrict__ S,
+                              const int8_t *__restrict__ cf, const int *__restrict__ cidx,
+                              const int *__restrict__ prp, int *__restrict__ pci, double *__restrict__ pv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int pos = prp[i];
+  if (cf[i]) {
+    pci[pos] = cidx[i];
+    pv[pos] = 1.0;
+    return;
+  }
+  double aii = 0.0, sn_neg = 0.0, sn_pos = 0.0, sp_neg = 0.0, sp_pos = 0.0;
+  int np = 0;
+  const int b = rp[i], e = rp[i + 1];
+  for (int p = b; p < e; ++p) {
+    const int j = ci[p];
+    const double v = a[p];
+    if (j == i) {
+      aii = v;
+      continue;
+    }
+    if (v < 0.0) sn_neg = __dadd_rn(sn_neg, v);
+    if (v > 0.0) sn_pos = __dadd_rn(sn_pos, v);
+    if (S[p] && cf[j]) {
+      ++np;
+      if (v < 0.0) sp_neg = __dadd_rn(sp_neg, v);
+      if (v > 0.0) sp_pos = __dadd_rn(sp_pos, v);
+    }
+  }
+  if (np == 0) return;
+  const double alpha = sp_neg != 0.0 ? __ddiv_rn(sn_neg, sp_neg) : 0.0;
+  const double beta = sp_pos != 0.0 ? __ddiv_rn(sn_pos, sp_pos) : 0.0;
+  const double at = sp_pos != 0.0 ? aii : __dadd_rn(aii, sn_pos);
+  for (int p = b; p < e; ++p) {
+    const int j = ci[p];
+    if (j == i || !S[p] || !cf[j]) continue;
+    const double v = a[p];
+    double w = 0.0;
+    if (v < 0.0) w = __ddiv_rn(-__dmul_rn(alpha, v), at);
+    if (v > 0.0) w = __ddiv_rn(-__dmul_rn(beta, v), at);
+    pci[pos] = cidx[j];
+    pv[pos] = w;
+    ++pos;
+  }
+}
+
+// ---------------------------------------------------------- transpose --
+__global__ void k_col_count(int64_t nnz, const int *__restrict__ ci, int *__restrict__ cnt) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nnz) atomicAdd(&cnt[ci[p]], 1);
+}
+
+__global__ void k_transpose_scatter(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                    const double *__restrict__ v, int *__restrict__ fill, int *__restrict__ tci,
+                                    double *__restrict__ tv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const int q = atomicAdd(&fill[ci[p]], 1);
+    tci[q] = i;
+    tv[q] = v[p];
+  }
+}
+
+// Rows of (src_ci, src_v) sorted by column into (dst_ci, dst_v); a warp per
+// row, rank of each entry = number of smaller keys in its row (keys distinct).
+__global__ void k_sort_rows(int m, const int *__restrict__ rp, const int *__restrict__ src_ci,
+                            const double *__restrict__ src_v, int *__restrict__ dst_ci, double *__restrict__ dst_v) {
+  const int lane = threadIdx.x & 31;
+  const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (row >= m) return;
+  const int b = rp[row], e = rp[row + 1];
+  for (int p = b + lane; p < e; p += 32) {
+    const int key = src_ci[p];
+    int rank = 0;
+    for (int q = b; q < e; ++q) rank += src_ci[q] < key;
+    dst_ci[b + rank] = key;
+    dst_v[b + rank] = src_v[p];
+  }
+}
+
+// ------------------------------------------------------------- SpGEMM --
+// C = X Y.  Row classes by the upper bound ub_i = sum_{p in X_i} nnz(Y_{x_p}):
+//   W: ub <= 1024, a warp per row, hash table of 2048 slots in shared memory;
+//   B: ub <= 8192, a block per row, 16384-slot table in shared memory;
+//   G: larger, a block per row, table in a global scratch slice per block.
+constexpr int W_UB = 1024, W_TAB = 2048, W_WARPS = 4;
+constexpr int B_UB = 8192, B_TAB = 16384, B_T = 256;
+
+__global__ void k_spgemm_ub(int m, const int *__restrict__ xrp, const int *__restrict__ xci,
+                            const int *__restrict__ yrp, int *__restrict__ lists, int *__restrict__ list_cnt,
+                            int *__restrict__ max_ub, int *flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  int64_t ub = 0;
+  for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
+    const int k = xci[p];
+    ub += yrp[k + 1] - yrp[k];
+  }
+  if (ub > (1 << 30)) {
+    flags[3] = 1;
+    ub = 1 << 30;
+  }
+  const int cls = ub <= W_UB ? 0 : (ub <= B_UB ? 1 : 2);
+  const int slot = atomicAdd(&list_cnt[cls], 1);
+  lists[(int64_t)cls * m + slot] = i;
+  if (cls == 2) atomicMax(max_ub, (int)ub);
+}
+
+__device__ __forceinline__ bool hash_insert(int *table, unsigned mask, int key, int *flags) {
+  unsigned h = ((unsigned)key * 2654435761u) & mask;
+  for (unsigned probe = 0; probe <= mask; ++probe) {
+    const int prev = atomicCAS(&table[h], -1, key);
+    if (prev == -1) return true;
+    if (prev == key) return false;
+    h = (h + 1) & mask;
+  }
+  flags[3] = 1;  // table full: cannot happen while ub <= capacity / 2
+  return false;
+}
+
+__device__ __forceinline__ int bsearch_sorted(const int *a, int len, int key) {
+  int lo = 0, hi = len - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Warp per row.  FILL = false: count distinct columns into cnt[i].
+// FILL = true: write the sorted columns and the canonically summed values.
+template <bool FILL>
+__global__ void __launch_bounds__(W_WARPS * 32) k_spgemm_warp(
+    const int *__restrict__ rows, int nrows, const int *__restrict__ xrp, const int *__restrict__ xci,
+    const double *__restrict__ xv, const int *__restrict__ yrp, const int *__restrict__ yci,
+    const double *__restrict__ yv, const int *__restrict__ crp, int *__restrict__ cci, double *__restrict__ cv,
+    int *__restrict__ cnt, int *flags) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int *table = reinterpret_cast<int *>(smem) + warp * W_TAB;
+  int *sorted = reinterpret_cast<int *>(smem) + W_WARPS * W_TAB + warp * W_UB;
+  double *acc = reinterpret_cast<double *>(smem + 4 * W_WARPS * (W_TAB + W_UB)) + warp * W_UB;
+  int *tmp = reinterpret_cast<int *>(acc);  // unsorted keys, reused as accumulator afterwards
+  for (int r = blockIdx.x * W_WARPS + warp; r < nrows; r += gridDim.x * W_WARPS) {
+    const int i = rows[r];
+    for (int t = lane; t < W_TAB; t += 32) table[t] = -1;
+    __syncwarp();
+    int mine = 0;
+    const int xb = xrp[i], xe = xrp[i + 1];
+    for (int p = xb; p < xe; ++p) {
+      const int k = xci[p];
+      for (int q = yrp[k] + lane; q < yrp[k + 1]; q += 32) mine += hash_insert(table, W_TAB - 1, yci[q], flags);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    const int count = mine;
+    if (!FILL) {
+      if (lane == 0) cnt[i] = count;
+      __syncwarp();
+      continue;
+    }
+    __syncwarp();
+    int base = 0;
+    for (int t0 = 0; t0 < W_TAB; t0 += 32) {
+      const int key = table[t0 + lane];
+      const unsigned bal = __ballot_sync(0xffffffffu, key >= 0);
+      if (key >= 0) tmp[base + __popc(bal & ((1u << lane) - 1u))] = key;
+      base += __popc(bal);
+    }
+    __syncwarp();
+    for (int e = lane; e < count; e += 32) {
+      const int key = tmp[e];
+      int rank = 0;
+      for (int f = 0; f < count; ++f) rank += tmp[f] < key;
+      sorted[rank] = key;
+    }
+    __syncwarp();
+    const int cb = crp[i];
+    for (int e = lane; e < count; e += 32) {
+      cci[cb + e] = sorted[e];
+      acc[e] = 0.0;
+    }
+    __syncwarp();
+    for (int p = xb; p < xe; ++p) {
+      const int k = xci[p];
+      const double x = xv[p];
+      for (int q = yrp[k] + lane; q < yrp[k + 1]; q += 32) {
+        const int pos = bsearch_sorted(sorted, count, yci[q]);
+        acc[pos] = __dadd_rn(acc[pos], __dmul_rn(x, yv[q]));
+      }
+      __syncwarp();
+    }
+    for (int e = lane; e < count; e += 32) cv[cb + e] = acc[e];
+    __syncwarp();
+  }
+}
+
+// Block per row; table / lists in shared memory (GLOBAL = false) or in a
+// per-block slice of global scratch of `cap` table slots (GLOBAL = true).
+template <bool FILL, bool GLOBAL>
+__global__ void __launch_bounds__(B_T) k_spgemm_block(
+    const int *__restrict__ rows, int nrows, const int *__restrict__ xrp, const int *__restrict__ xci,
+    const double *__restrict__ xv, const int *__restrict__ yrp, const int *__restrict__ yci,
+    const double *__restrict__ yv, const int *__restrict__ crp, int *__restrict__ cci, double *__restrict__ cv,
+    int *__restrict__ cnt, int *flags, unsigned char *gscratch, int cap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_count;
+  unsigned char *base_ptr = GLOBAL ? gscratch + (size_t)blockIdx.x * ((size_t)cap * 4 + (size_t)cap / 2 * 16) : smem;
+  const int tcap = GLOBAL ? cap : B_TAB;
+  int *table = reinterpret_cast<int *>(base_ptr);
+  int *tmp = table + tcap;
+  int *sorted = tmp + tcap / 2;
+  double *acc = reinterpret_cast<double *>(sorted + tcap / 2);
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int i = rows[r];
+    for (int t = threadIdx.x; t < tcap; t += blockDim.x) table[t] = -1;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    const int xb = xrp[i], xe = xrp[i + 1];
+    int mine = 0;
+    for (int p = xb; p < xe; ++p) {
+      const int k = xci[p];
+      for (int q = yrp[k] + threadIdx.x; q < yrp[k + 1]; q += blockDim.x)
+        mine += hash_insert(table, tcap - 1, yci[q], flags);
+    }
+    if (mine) atomicAdd(&s_count, mine);
+    __syncthreads();
+    const int count = s_count;
+    if (!FILL) {
+      if (threadIdx.x == 0) cnt[i] = count;
+      __syncthreads();
+      continue;
+    }
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < tcap; t += blockDim.x) {
+      const int key = table[t];
+      if (key >= 0) tmp[atomicAdd(&s_count, 1)] = key;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < count; e += blockDim.x) {
+      const int key = tmp[e];
+      int rank = 0;
+      for (int f = 0; f < count; ++f) rank += tmp[f] < key;
+      sorted[rank] = key;
+    }
+    __syncthreads();
+    const int cb = crp[i];
+    for (int e = threadIdx.x; e < count; e += blockDim.x) {
+      cci[cb + e] = sorted[e];
+      acc[e] = 0.0;
+    }
+    __syncthreads();
+    for (int p = xb; p < xe; ++p) {
+      const int k = xci[p];
+      const double x = xv[p];
+      for (int q = yrp[k] + threadIdx.x; q < yrp[k + 1]; q += blockDim.x) {
+        const int pos = bsearch_sorted(sorted, count, yci[q]);
+        acc[pos] = __dadd_rn(acc[pos], __dmul_rn(x, yv[q]));
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < count; e += blockDim.x) cv[cb + e] = acc[e];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ dense LL^T --
+__global__ void k_to_dense(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                           const double *__restrict__ v, double *__restrict__ M) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) M[(size_t)i * n + ci[p]] = v[p];
+}
+
+// Right-looking dense Cholesky in one block; lower factor in place, upper
+// triangle zeroed.  A pivot <= 0 sets flags[4] and stops.
+__global__ void k_cholesky(int n, double *M, int *flags) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = M[(size_t)j * n + j];
+      if (!(d > 0.0)) {
+        bad = 1;
+        flags[4] = 1;
+      } else {
+        M[(size_t)j * n + j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (bad) return;
+    const double ljj = M[(size_t)j * n + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) M[(size_t)i * n + j] = __ddiv_rn(M[(size_t)i * n + j], ljj);
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int64_t t = threadIdx.x; t < (int64_t)m * m; t += blockDim.x) {
+      const int i = j + 1 + (int)(t / m), k = j + 1 + (int)(t % m);
+      if (k <= i) M[(size_t)i * n + k] = __dadd_rn(M[(size_t)i * n + k], -__dmul_rn(M[(size_t)i * n + j], M[(size_t)k * n + j]));
+    }
+    __syncthreads();
+  }
+  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
+    const int i = (int)(t / n), k = (int)(t % n);
+    if (k > i) M[t] = 0.0;
+  }
+}
+
+// ------------------------------------------------------------ host side --
+struct Flags {
+  int *d = nullptr;
+  int h[8] = {};
+};
+
+void read_flags(Mem &m, Flags &f) {
+  AMG_CUDA(cudaMemcpyAsync(f.h, f.d, sizeof(f.h), cudaMemcpyDeviceToHost, m.stream));
+  AMG_CUDA(cudaStreamSynchronize(m.stream));
+}
+
+int read_int(Mem &m, const int *d) {
+  int v = 0;
+  AMG_CUDA(cudaMemcpyAsync(&v, d, sizeof(int), cudaMemcpyDeviceToHost, m.stream));
+  AMG_CUDA(cudaStreamSynchronize(m.stream));
+  return v;
+}
+
+void fail(int code, const char *msg) {
+  set_error("%s", msg);
+  throw Status{code};
+}
+
+// R = P^T (ncols rows), each row listing fine indices in ascending order.
+void transpose(Mem &m, const DCsr &P, int ncols, DCsr &R) {
+  cudaStream_t s = m.stream;
+  Buf<int> cnt(m, (size_t)ncols + 1);
+  AMG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * ((size_t)ncols + 1), s));
+  if (P.nnz) k_col_count<<<ceil_div(P.nnz, TPB), TPB, 0, s>>>(P.nnz, P.ci, cnt.p);
+  AMG_CHECK_LAUNCH();
+  R.n = ncols;
+  R.ncols = P.n;
+  R.nnz = P.nnz;
+  R.rp = m.get_n<int>((size_t)ncols + 1);
+  scan_counts(m, cnt.p, R.rp, ncols);
+  R.ci = m.get_n<int>(std::max<int64_t>(R.nnz, 1));
+  R.v = m.get_n<double>(std::max<int64_t>(R.nnz, 1));
+  Buf<int> fill(m, (size_t)ncols + 1);
+  AMG_CUDA(cudaMemcpyAsync(fill.p, R.rp, sizeof(int) * ((size_t)ncols + 1), cudaMemcpyDeviceToDevice, s));
+  Buf<int> tci(m, std::max<int64_t>(R.nnz, 1));
+  Buf<double> tv(m, std::max<int64_t>(R.nnz, 1));
+  k_transpose_scatter<<<ceil_div(P.n, TPB), TPB, 0, s>>>(P.n, P.rp, P.ci, P.v, fill.p, tci.p, tv.p);
+  AMG_CHECK_LAUNCH();
+  k_sort_rows<<<ceil_div((int64_t)ncols * 32, TPB), TPB, 0, s>>>(ncols, R.rp, tci.p, tv.p, R.ci, R.v);
+  AMG_CHECK_LAUNCH();
+}
+
+size_t warp_smem() { return (size_t)W_WARPS * (W_TAB * 4 + W_UB * 4 + W_UB * 8); }
+size_t block_smem() { return (size_t)B_TAB * 4 + (size_t)B_TAB / 2 * 4 * 2 + (size_t)B_TAB / 2 * 8; }
+
+// C = X Y with the canonical order (see file header).
+void spgemm(Mem &m, Flags &fl, const DCsr &X, const DCsr &Y, int ncols, DCsr &C) {
+  cudaStream_t s = m.stream;
+  const int rows = X.n;
+  Buf<int> lists(m, (size_t)rows * 3);
+  Buf<int> meta(m, 4);  // list counts [3], max ub
+  AMG_CUDA(cudaMemsetAsync(meta.p, 0, sizeof(int) * 4, s));
+  k_spgemm_ub<<<ceil_div(rows, TPB), TPB, 0, s>>>(rows, X.rp, X.ci, Y.rp, lists.p, meta.p, meta.p + 3, fl.d);
+  AMG_CHECK_LAUNCH();
+  int hm[4];
+  AMG_CUDA(cudaMemcpyAsync(hm, meta.p, sizeof(hm), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  if (hm[3] > (1 << 22)) fail(AMG_ERR_UNSUPPORTED, "SpGEMM row product bound above 2^22 entries");
+  int gcap = 2;
+  while (gcap < 2 * std::max(hm[3], 1)) gcap <<= 1;
+  const int gblocks = std::min(hm[2], kNumSMs);
+  Buf<unsigned char> gscr;
+  if (hm[2] > 0) gscr = Buf<unsigned char>(m, (size_t)gblocks * ((size_t)gcap * 4 + (size_t)gcap / 2 * 16));
+
+  static bool attr_done = false;
+  if (!attr_done) {
+    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem()));
+    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem()));
+    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_block<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem()));
+    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_block<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem()));
+    attr_done = true;
+  }
+  const int *lw = lists.p, *lb = lists.p + rows, *lg = lists.p + 2 * (size_t)rows;
+  auto grid_w = [&](int nr) { return std::max(1, std::min(ceil_div(nr, W_WARPS), kNumSMs * 16)); };
+  auto grid_b = [&](int nr) { return std::max(1, std::min(nr, kNumSMs * 2)); };
+
+  Buf<int> cnt(m, (size_t)rows + 1);
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fillp = pass == 1;
+    if (fillp) {
+      C.n = rows;
+      C.ncols = ncols;
+      C.rp = m.get_n<int>((size_t)rows + 1);
+      C.nnz = scan_counts(m, cnt.p, C.rp, rows);
+      C.ci = m.get_n<int>(std::max<int64_t>(C.nnz, 1));
+      C.v = m.get_n<double>(std::max<int64_t>(C.nnz, 1));
+    }
+    if (hm[0] > 0) {
+      if (fillp)
+        k_spgemm_warp<true><<<grid_w(hm[0]), W_WARPS * 32, warp_smem(), s>>>(lw, hm[0], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, C.rp, C.ci, C.v, cnt.p, fl.d);
+      else
+        k_spgemm_warp<false><<<grid_w(hm[0]), W_WARPS * 32, warp_smem(), s>>>(lw, hm[0], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, nullptr, nullptr, nullptr, cnt.p, fl.d);
+      AMG_CHECK_LAUNCH();
+    }
+    if (hm[1] > 0) {
+      if (fillp)
+        k_spgemm_block<true, false><<<grid_b(hm[1]), B_T, block_smem(), s>>>(lb, hm[1], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, C.rp, C.ci, C.v, cnt.p, fl.d, nullptr, 0);
+      else
+        k_spgemm_block<false, false><<<grid_b(hm[1]), B_T, block_smem(), s>>>(lb, hm[1], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, nullptr, nullptr, nullptr, cnt.p, fl.d, nullptr, 0);
+      AMG_CHECK_LAUNCH();
+    }
+    if (hm[2] > 0) {
+      if (fillp)
+        k_spgemm_block<true, true><<<gblocks, B_T, 0, s>>>(lg, hm[2], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, C.rp, C.ci, C.v, cnt.p, fl.d, gscr.p, gcap);
+      else
+        k_spgemm_block<false, true><<<gblocks, B_T, 0, s>>>(lg, hm[2], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, nullptr, nullptr, nullptr, cnt.p, fl.d, gscr.p, gcap);
+      AMG_CHECK_LAUNCH();
+    }
+  }
+}
+
+void free_csr(Mem &m, DCsr &c) {
+  if (c.rp) m.put(c.rp, sizeof(int) * ((size_t)c.n + 1));
+  if (c.ci) m.put(c.ci, sizeof(int) * (size_t)std::max<int64_t>(c.nnz, 1));
+  if (c.v) m.put(c.v, sizeof(double) * (size_t)std::max<int64_t>(c.nnz, 1));
+  c.rp = c.ci = nullptr;
+  c.v = nullptr;
+}
+
+}  // namespace
+
+int64_t scan_counts(Mem &m, const int *in, int *out, int n) {
+  cudaStream_t s = m.stream;
+  const int nb = std::max(1, ceil_div(n, SCAN_TILE));
+  Buf<long long> bsum(m, (size_t)nb + 1);
+  k_scan_reduce<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p);
+  AMG_CHECK_LAUNCH();
+  k_scan_blocks<<<1, SCAN_T, 0, s>>>(bsum.p, nb);
+  AMG_CHECK_LAUNCH();
+  long long total = 0;
+  AMG_CUDA(cudaMemcpyAsync(&total, bsum.p + nb, sizeof(total), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  if (total >= (1LL << 31) - 1) fail(AMG_ERR_UNSUPPORTED, "more than 2^31-1 nonzeros in one matrix");
+  k_scan_apply<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p, out);
+  AMG_CHECK_LAUNCH();
+  k_set_last<<<1, 1, 0, s>>>(out, n, bsum.p + nb);
+  AMG_CHECK_LAUNCH();
+  return total;
+}
+
+void free_level_csr(Mem &m, DCsr &c) { free_csr(m, c); }
+
+void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
+  Mem &m = h->mem;
+  cudaStream_t s = m.stream;
+  const amg_params &prm = h->prm;
+  const int n0 = Ain.n;
+  const int64_t nnz0 = Ain.nnz;
+
+  Flags fl;
+  Buf<int> flags_buf(m, 8);
+  fl.d = flags_buf.p;
+  AMG_CUDA(cudaMemsetAsync(fl.d, 0, sizeof(int) * 8, s));
+
+  // level 0: copy A
+  DCsr &A0 = h->lev[0].A;
+  A0.n = A0.ncols = n0;
+  A0.nnz = nnz0;
+  A0.rp = m.get_n<int>((size_t)n0 + 1);
+  A0.ci = m.get_n<int>(std::max<int64_t>(nnz0, 1));
+  A0.v = m.get_n<double>(std::max<int64_t>(nnz0, 1));
+  const cudaMemcpyKind kind = Ain.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  AMG_CUDA(cudaMemcpyAsync(A0.rp, Ain.rowptr, sizeof(int) * ((size_t)n0 + 1), kind, s));
+  AMG_CUDA(cudaMemcpyAsync(A0.ci, Ain.colidx, sizeof(int) * (size_t)nnz0, kind, s));
+  AMG_CUDA(cudaMemcpyAsync(A0.v, Ain.val, sizeof(double) * (size_t)nnz0, kind, s));
+  k_validate<<<ceil_div(n0, TPB), TPB, 0, s>>>(n0, nnz0, A0.rp, A0.ci, A0.v, fl.d);
+  AMG_CHECK_LAUNCH();
+  read_flags(m, fl);
+  if (fl.h[0]) fail(AMG_ERR_INVALID_ARG, "malformed CSR (row pointers, column range or unsorted columns)");
+  if (fl.h[1]) fail(AMG_ERR_NOT_SPD, "a diagonal entry is missing or not positive");
+
+  int k = 0;
+  for (;;) {
+    Level &L = h->lev[k];
+    const DCsr &A = L.A;
+    const int n = A.n;
+    bool last = n <= prm.max_coarse || k == prm.max_levels - 1;
+    Buf<uint8_t> S, ST;
+    Buf<int> cidx;
+    int nc = 0;
+    if (!last) {
+      S = Buf<uint8_t>(m, std::max<int64_t>(A.nnz, 1));
+      ST = Buf<uint8_t>(m, std::max<int64_t>(A.nnz, 1));
+      Buf<double> lam(m, n);
+      Buf<int8_t> st0(m, n), st1(m, n);
+      Buf<int> und(m, 1);
+      const int g = ceil_div(n, TPB);
+      k_strength<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
+      AMG_CHECK_LAUNCH();
+      k_pmis_init<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
+      AMG_CHECK_LAUNCH();
+      read_flags(m, fl);
+      if (fl.h[2]) fail(AMG_ERR_INVALID_ARG, "matrix pattern is not structurally symmetric");
+      for (int round = 0;; ++round) {
+        if (round > n + 1) fail(AMG_ERR_SETUP, "PMIS did not terminate");
+        AMG_CUDA(cudaMemsetAsync(und.p, 0, sizeof(int), s));
+        k_pmis_select<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, st1.p);
+        AMG_CHECK_LAUNCH();
+        k_pmis_update<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, st1.p, st0.p, und.p);
+        AMG_CHECK_LAUNCH();
+        if (read_int(m, und.p) == 0) break;
+      }
+      L.cf = m.get_n<int8_t>(n);
+      Buf<int> isC(m, n);
+      k_cf_out<<<g, TPB, 0, s>>>(n, st0.p, L.cf, isC.p);
+      AMG_CHECK_LAUNCH();
+      cidx = Buf<int>(m, (size_t)n + 1);
+      nc = (int)scan_counts(m, isC.p, cidx.p, n);
+      if (nc == 0 || (double)nc > 0.9 * (double)n) {
+        last = true;  // stalled coarsening
+        m.put(L.cf, n);
+        L.cf = nullptr;
+      }
+    }
+    if (last) {
+      if (n > kMaxDense) fail(AMG_ERR_SETUP, "coarsening stalled on a level too large for the dense factor");
+      h->nL = n;
+      h->L = m.get_n<double>((size_t)n * n);
+      AMG_CUDA(cudaMemsetAsync(h->L, 0, sizeof(double) * (size_t)n * n, s));
+      k_to_dense<<<ceil_div(n, TPB), TPB, 0, s>>>(n, A.rp, A.ci, A.v, h->L);
+      AMG_CHECK_LAUNCH();
+      k_cholesky<<<1, 256, 0, s>>>(n, h->L, fl.d);
+      AMG_CHECK_LAUNCH();
+      read_flags(m, fl);
+      if (fl.h[4]) fail(AMG_ERR_NOT_SPD, "dense Cholesky of the last level met a non-positive pivot");
+      h->nlevels = k + 1;
+      break;
+    }
+    // interpolation
+    const int g = ceil_div(n, TPB);
+    DCsr &P = L.P;
+    {
+      Buf<int> pcnt(m, n);
+      k_interp_count<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, L.cf, pcnt.p);
+      AMG_CHECK_LAUNCH();
+      P.n = n;
+      P.ncols = nc;
+      P.rp = m.get_n<int>((size_t)n + 1);
+      P.nnz = scan_counts(m, pcnt.p, P.rp, n);
+      P.ci = m.get_n<int>(std::max<int64_t>(P.nnz, 1));
+      P.v = m.get_n<double>(std::max<int64_t>(P.nnz, 1));
+      k_interp_fill<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, P.rp, P.ci, P.v);
+      AMG_CHECK_LAUNCH();
+    }
+    S.reset();
+    ST.reset();
+    cidx.reset();
+    transpose(m, P, nc, L.R);
+    DCsr AP;
+    spgemm(m, fl, A, P, nc, AP);
+    spgemm(m, fl, L.R, AP, nc, h->lev[k + 1].A);
+    free_csr(m, AP);
+    read_flags(m, fl);
+    if (fl.h[3]) fail(AMG_ERR_UNSUPPORTED, "SpGEMM hash table overflow");
+    ++k;
+  }
+}
+
+}  // namespace amg

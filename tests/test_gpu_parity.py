@@ -1,0 +1,292 @@
+"""GPU parity: libamg (through its C ABI) against the CPU oracle on the same seeded inputs.
+
+Bars (stated per test):
+  * C/F splittings and the patterns of P and A_c: bit-exact.
+  * P and A_c values: the set-up fixes its summation order and forbids FMA
+    contraction, so the values are expected bitwise equal; the test allows
+    1e-12 relative to the row's largest entry.
+  * Solve (FP64 mode): same iteration count as the oracle; x within 1e-9 of
+    the oracle's x relative; |x - x*| / |x*| <= 1e-6 at rtol 1e-8.
+  * V-cycle (FP64): z within 1e-12 relative (rounding-order differences only).
+  * V-cycle (FP32): within 1e-5 relative; FP32 / BF16 solves reach rtol 1e-8
+    and agree with the oracle's x to 1e-6.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from oracle import oracle as O  # noqa: E402
+from paper_2102_07417_gb300 import amg  # noqa: E402
+from paper_2102_07417_gb300 import problems as pr  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.asarray(a), dtype=dtype, device=DEV)
+
+
+def to_dev_csr(A):
+    return pr.CSR(A.n, dev(A.rowptr, torch.int32), dev(A.col, torch.int32), dev(A.val))
+
+
+def assert_same_hierarchy(h_gpu, h_or, rel=1e-12):
+    inf = h_gpu.info()
+    assert inf["nlevels"] == h_or.nlevels
+    for k in range(h_or.nlevels):
+        ex = h_gpu.export(k)
+        arp, aci, av = h_or.A(k)
+        grp, gci, gv = ex["A"]
+        assert np.array_equal(grp, arp), f"A_{k} row pointers"
+        assert np.array_equal(gci, aci), f"A_{k} columns"
+        scale = np.maximum.reduceat(np.abs(av), arp[:-1]) if len(av) else np.zeros(0)
+        rows = np.repeat(np.arange(len(arp) - 1), np.diff(arp))
+        assert np.all(np.abs(gv - av) <= rel * scale[rows]), f"A_{k} values"
+        if k < h_or.nlevels - 1:
+            assert np.array_equal(ex["cf"], h_or.cf(k)), f"C/F of level {k}"
+            prp, pci, pv = h_or.P(k)
+            g2, g3, g4 = ex["P"]
+            assert np.array_equal(g2, prp) and np.array_equal(g3, pci), f"P_{k} pattern"
+            assert np.all(np.abs(g4 - pv) <= rel * np.abs(pv) + 1e-300), f"P_{k} values"
+
+
+def bitwise_equal_hierarchy(h_gpu, h_or):
+    for k in range(h_or.nlevels):
+        ex = h_gpu.export(k)
+        if not np.array_equal(ex["A"][2], h_or.A(k)[2]):
+            return False
+        if k < h_or.nlevels - 1 and not np.array_equal(ex["P"][2], h_or.P(k)[2]):
+            return False
+    return True
+
+
+CASES = {
+    "poisson2d_64": lambda: pr.poisson2d(64),
+    "poisson3d_24": lambda: pr.poisson3d(24),
+    "diffusion3d_20": lambda: pr.diffusion3d(20, 2.0, 2)[0],
+    "graph_laplacian_700": lambda: pr.graph_laplacian_spd(700, 7, 0.05, 3),
+    "poisson1d_301": lambda: pr.poisson1d(301),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("seed", [0, 17])
+def test_hierarchy_bit_exact(name, seed):
+    A = CASES[name]()
+    ho = O.Hierarchy(A, seed=seed)
+    hg = amg.Hierarchy(A, seed=seed)
+    assert_same_hierarchy(hg, ho)
+    assert bitwise_equal_hierarchy(hg, ho)
+    cgd, cop = ho.complexities()
+    inf = hg.info()
+    assert inf["cgd"] == pytest.approx(cgd, rel=1e-15) and inf["cop"] == pytest.approx(cop, rel=1e-15)
+
+
+def test_hierarchy_from_device_input_matches_host_input():
+    A = pr.poisson3d(16)
+    h1 = amg.Hierarchy(A, seed=3)
+    h2 = amg.Hierarchy(to_dev_csr(A), seed=3)
+    for k in range(h1.info()["nlevels"]):
+        e1, e2 = h1.export(k), h2.export(k)
+        assert all(np.array_equal(a, b) for a, b in zip(e1["A"], e2["A"]))
+
+
+def test_hierarchy_config2_full_size():
+    """128^3 Poisson, the benchmark workload: every level bit-exact against the oracle."""
+    p = pr.config2()
+    ho = O.Hierarchy(p.A, seed=0)
+    hg = amg.Hierarchy(p.A, seed=0)
+    assert_same_hierarchy(hg, ho)
+
+
+@pytest.mark.parametrize("name", ["poisson2d_64", "diffusion3d_20", "graph_laplacian_700"])
+@pytest.mark.parametrize("nu", [(1, 1), (2, 1), (0, 2), (1, 0)])
+def test_vcycle_fp64_parity(name, nu):
+    A = CASES[name]()
+    ho = O.Hierarchy(A, seed=1, nu1=nu[0], nu2=nu[1])
+    hg = amg.Hierarchy(A, seed=1, nu1=nu[0], nu2=nu[1])
+    rng = np.random.default_rng(5)
+    for _ in range(2):
+        y = rng.standard_normal(A.n)
+        zo = ho.vcycle(y)
+        zg = hg.vcycle(dev(y)).cpu().numpy()
+        assert np.abs(zg - zo).max() <= 1e-12 * np.abs(zo).max()
+
+
+@pytest.mark.parametrize("prec,tol", [(amg.PREC_FP32, 1e-5), (amg.PREC_FP32_BF16PR, 2e-2)])
+def test_vcycle_reduced_precision(prec, tol):
+    A = CASES["diffusion3d_20"]()
+    ho = O.Hierarchy(A, seed=1)
+    hg = amg.Hierarchy(A, seed=1, precision=prec)
+    y = np.random.default_rng(2).standard_normal(A.n)
+    zo = ho.vcycle(y)
+    zg = hg.vcycle(dev(y)).cpu().numpy()
+    assert np.abs(zg - zo).max() <= tol * np.abs(zo).max()
+
+
+def test_spmv_parity_all_levels():
+    A = CASES["diffusion3d_20"]()
+    ho = O.Hierarchy(A, seed=4)
+    hg = amg.Hierarchy(A, seed=4)
+    rng = np.random.default_rng(1)
+    for k in range(ho.nlevels):
+        rp, ci, v = ho.A(k)
+        Ak = pr.CSR(len(rp) - 1, rp, ci, v)
+        x = rng.standard_normal(Ak.n)
+        yo = O.spmv(Ak, x)
+        yg = hg.spmv(k, dev(x)).cpu().numpy()
+        assert np.abs(yg - yo).max() <= 1e-13 * np.abs(yo).max()
+
+
+def _solve_both(A, b, seed=0, rtol=1e-8, **kw):
+    ho = O.Hierarchy(A, seed=seed)
+    st, xo, ito, hist_o, _ = ho.pcg(b, rtol=rtol, maxit=500)
+    assert st == 0
+    hg = amg.Hierarchy(A, seed=seed, **kw)
+    xg, itg, stg, hist_g = hg.solve(dev(b), rtol=rtol, maxit=500, hist=True)
+    assert stg == amg.AMG_OK
+    return xo, ito, hist_o, xg.cpu().numpy(), itg, hist_g
+
+
+@pytest.mark.parametrize("name", ["poisson2d_64", "poisson3d_24", "diffusion3d_20", "graph_laplacian_700"])
+def test_pcg_fp64_parity(name):
+    A = CASES[name]()
+    b = pr.uniform(A.n, 11)
+    xo, ito, ho_, xg, itg, hg_ = _solve_both(A, b)
+    assert itg == ito
+    assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+    assert np.allclose(hg_, ho_, rtol=1e-6, atol=0)
+    assert hg_[-1] < 1e-8 * np.linalg.norm(b)
+
+
+def test_pcg_config1_against_xstar():
+    p = pr.config1()
+    xo, ito, _, xg, itg, _ = _solve_both(p.A, p.b)
+    assert itg == ito
+    assert np.linalg.norm(xg - p.xstar) <= 1e-6 * np.linalg.norm(p.xstar)
+    assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+def test_pcg_config2_full_size():
+    """128^3 Poisson at rtol 1e-8, FP64: same iterations as the oracle and |x - x*| / |x*| <= 1e-6."""
+    p = pr.config2()
+    xo, ito, _, xg, itg, _ = _solve_both(p.A, p.b)
+    assert itg == ito
+    assert np.linalg.norm(xg - p.xstar) <= 1e-6 * np.linalg.norm(p.xstar)
+    assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("prec", [amg.PREC_FP32, amg.PREC_FP32_BF16PR])
+def test_pcg_mixed_precision(prec):
+    A, rng = pr.diffusion3d(32, 2.0, 2)
+    b = pr.uniform(A.n, rng)
+    xo, ito, _, xg, itg, hist = _solve_both(A, b, precision=prec)
+    assert hist[-1] < 1e-8 * np.linalg.norm(b)
+    assert abs(itg - ito) <= max(3, ito // 5)
+    assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+def test_host_one_call_solve_matches_device_path():
+    p = pr.config1()
+    xh, res = amg.solve(p.A, p.b, rtol=1e-8)
+    hg = amg.Hierarchy(p.A)
+    xd, it, st, _ = hg.solve(dev(p.b), rtol=1e-8)
+    assert res.iters == it and res.nlevels == hg.info()["nlevels"]
+    assert np.array_equal(xh, xd.cpu().numpy())
+    assert res.setup_ms > 0 and res.solve_ms > 0
+
+
+def test_solve_is_deterministic():
+    A = CASES["diffusion3d_20"]()
+    b = dev(pr.uniform(A.n, 1))
+    h = amg.Hierarchy(A, seed=2)
+    x1, i1, _, h1 = h.solve(b, hist=True)
+    x2, i2, _, h2 = h.solve(b, hist=True)
+    assert i1 == i2 and torch.equal(x1, x2) and np.array_equal(h1, h2)
+
+
+def test_nonzero_initial_guess():
+    A = CASES["poisson2d_64"]()
+    b = pr.uniform(A.n, 3)
+    x0 = pr.uniform(A.n, 4)
+    ho = O.Hierarchy(A)
+    st, xo, ito, _, _ = ho.pcg(b, x0=x0, rtol=1e-8)
+    hg = amg.Hierarchy(A)
+    xg, itg, _, _ = hg.solve(dev(b), x=dev(x0), rtol=1e-8)
+    assert itg == ito and np.linalg.norm(xg.cpu().numpy() - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+# ------------------------------------------------------------ edge cases --
+
+def test_single_row_and_direct_levels():
+    A = pr.dense_to_csr(np.array([[4.0]]))
+    h = amg.Hierarchy(A)
+    x, it, st, _ = h.solve(dev([2.0]))
+    assert st == 0 and it == 1 and x.item() == pytest.approx(0.5, rel=1e-15)
+    A = pr.poisson2d(6)
+    h = amg.Hierarchy(A, max_levels=1)
+    assert h.info()["nlevels"] == 1
+    b = pr.uniform(A.n, 1)
+    x, it, st, _ = h.solve(dev(b), rtol=1e-10)
+    assert it == 1 and np.allclose(x.cpu().numpy(), np.linalg.solve(A.to_dense(), b), rtol=1e-12, atol=1e-14)
+
+
+def test_zero_rhs_returns_immediately():
+    h = amg.Hierarchy(pr.poisson2d(10))
+    x, it, st, hist = h.solve(torch.zeros(100, dtype=torch.float64, device=DEV), hist=True)
+    assert st == 0 and it == 0 and torch.count_nonzero(x) == 0
+
+
+def test_maxit_reports_no_convergence():
+    h = amg.Hierarchy(pr.poisson3d(16))
+    x, it, st, _ = h.solve(dev(pr.uniform(16 ** 3, 1)), rtol=1e-14, maxit=2)
+    assert st == amg.AMG_ERR_NO_CONVERGENCE and it == 2
+
+
+def test_isolated_points_and_empty_interpolation_rows():
+    # a diagonal block (no strong connections) next to a Poisson block
+    D = np.zeros((130, 130))
+    D[:100, :100] = pr.poisson2d(10).to_dense()
+    D[100:, 100:] = np.diag(np.linspace(1.0, 3.0, 30))
+    A = pr.dense_to_csr(D)
+    ho = O.Hierarchy(A, seed=9, max_coarse=8)
+    hg = amg.Hierarchy(A, seed=9, max_coarse=8)
+    assert_same_hierarchy(hg, ho)
+    b = pr.uniform(130, 2)
+    x, it, st, _ = hg.solve(dev(b), rtol=1e-10)
+    assert st == 0 and np.allclose(x.cpu().numpy(), np.linalg.solve(D, b), rtol=1e-8, atol=1e-10)
+
+
+@pytest.mark.parametrize("mutate,code", [
+    ("unsorted", amg.AMG_ERR_INVALID_ARG),
+    ("neg_diag", amg.AMG_ERR_NOT_SPD),
+    ("col_range", amg.AMG_ERR_INVALID_ARG),
+    ("nonsym_pattern", amg.AMG_ERR_INVALID_ARG),
+    ("indefinite", amg.AMG_ERR_NOT_SPD),
+])
+def test_setup_rejects_bad_input(mutate, code):
+    A = pr.poisson2d(10)
+    rp, ci, v = A.rowptr.copy(), A.col.copy(), A.val.copy()
+    if mutate == "unsorted":
+        ci[1], ci[2] = ci[2], ci[1]
+    elif mutate == "neg_diag":
+        v[0] = -v[0]
+    elif mutate == "col_range":
+        ci[-1] = A.n
+    elif mutate == "nonsym_pattern":
+        D = A.to_dense()
+        D[0, 99] = -0.5
+        B = pr.dense_to_csr(D)
+        rp, ci, v = B.rowptr, B.col, B.val
+    elif mutate == "indefinite":
+        B = pr.dense_to_csr(np.array([[1.0, 2.0], [2.0, 1.0]]))
+        rp, ci, v = B.rowptr, B.col, B.val
+    bad = pr.CSR(len(rp) - 1, rp, ci, v)
+    with pytest.raises(amg.AmgError) as e:
+        amg.Hierarchy(bad, max_levels=1 if mutate == "indefinite" else 25)
+    assert e.value.code == code
