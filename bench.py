@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark: classical-AMG-preconditioned CG, time to rtol 1e-8, on one GB300 per rank.
+
+One step = one pass of the whole hot path on one system: the AMG set-up
+(strength, PMIS, direct interpolation, R = P^T, Galerkin SpGEMM, dense
+Cholesky, cast) followed by PCG with one V-cycle per iteration until
+||r|| < 1e-8 ||b||.  The matrix and right-hand side are resident in HBM
+when the timed region starts.  The default workload is the 3-D 7-point
+Poisson problem on a 128^3 interior grid (n = 2,097,152, 14,581,760
+nonzeros, FP64 CSR; x* ~ U[-1,1] seed 1, b = A x*), solved in FP64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun (N > 1) every rank solves its own copy of the system on its
+own GPU (independent replicas: the method has no data-parallel exchange at
+one system per GPU); the reported time is the maximum over ranks.
+``--impl reference`` times the CPU oracle (plain single-threaded FP64 C) on
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AMG-PCG time to rtol 1e-8 & V-cycle HBM GB/s vs peak; served p50/p99 latency"
+FALLBACK_HBM_GBS = 6800.0
+VCYCLE = ("smooth_resid", "restrict", "prolong", "smooth_post", "coarse")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", default="poisson3d_128",
+                    help="poisson3d_<N> | poisson2d_<N> | diffusion3d_<N>")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16pr"], default=None)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def make_problem(name: str):
+    from paper_2102_07417_gb300 import problems as pr
+
+    kind, N = name.rsplit("_", 1)
+    N = int(N)
+    if kind == "poisson3d":
+        return pr.config2(N), f"3-D 7-point Poisson {N}^3 (x* ~ U[-1,1] seed 1, b = A x*)"
+    if kind == "poisson2d":
+        A = pr.poisson2d(N)
+        xs = pr.uniform(A.n, 0)
+        return pr.Problem(name, A, A.matvec(xs), xs), f"2-D 5-point Poisson {N}^2 (x* ~ U[-1,1] seed 0)"
+    if kind == "diffusion3d":
+        return pr.config3(N), f"3-D 7-point heterogeneous diffusion {N}^3 (sigma 2, seed 2, b ~ U[-1,1])"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_for(kernel_class: str):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary, if
+    it was captured on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_2102_07417_gb300", "csrc", "solve.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        m = re.match(r"^\|\s*`?(\w+)`?\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]{16})\s*\|", line)
+        if m and m.group(1) == kernel_class and m.group(3) == sha:
+            return float(m.group(2))
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_id: str | None, enabled: bool):
+        self.proc = None
+        self.path = None
+        if not enabled:
+            return
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if gpu_id is not None:
+                cmd += ["-i", gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]", "") else 0.0,
+                             parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        load = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def gpu_uuid(dev: int):
+    try:
+        import torch
+
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ oracle arm --
+def oracle_solve(p, rtol):
+    from oracle import oracle as O
+
+    t0 = time.perf_counter()
+    h = O.Hierarchy(p.A, seed=0)
+    t1 = time.perf_counter()
+    st, x, it, _, _ = h.pcg(p.b, rtol=rtol, maxit=1000)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, it, st
+
+
+def run_reference(args, rank, world):
+    import numpy as np  # noqa: F401
+
+    if rank != 0:
+        return
+    p, desc = make_problem(args.workload)
+    # one full oracle set-up + solve per step; if that would not fit in a few
+    # minutes, the set-up is timed once and each step times the PCG phase only
+    tp, ts, it, st = oracle_solve(p, args.rtol)
+    full = (args.steps + args.warmup) * (tp + ts) <= 240.0
+    times = []
+    for k in range(args.warmup + args.steps):
+        if k == 0:
+            t = tp + ts
+        elif full:
+            a, b, it, st = oracle_solve(p, args.rtol)
+            t = a + b
+        else:
+            from oracle import oracle as O
+
+            if k == 1:
+                h = O.Hierarchy(p.A, seed=0)
+            t0 = time.perf_counter()
+            h.pcg(p.b, rtol=args.rtol, maxit=1000)
+            t = tp + (time.perf_counter() - t0)
+        if k >= args.warmup:
+            times.append(t)
+    v = sum(times) / len(times)
+    sample = ("each step: a full oracle set-up + PCG solve of the workload" if full else
+              "each step: the oracle PCG solve of the workload plus the set-up time measured once")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": desc, "n": p.A.n, "nnz": p.A.nnz, "rtol": args.rtol, "precision": "fp64"},
+           "iters": it, "status": st,
+           "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------- GPU arm --
+def run_gpu(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    from paper_2102_07417_gb300 import amg
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    amg.load()
+    p, desc = make_problem(args.workload)
+    prec = args.precision or ("fp64" if p.A.n <= 4_200_000 else "fp32")
+    prec_id = {"fp64": amg.PREC_FP64, "fp32": amg.PREC_FP32, "bf16pr": amg.PREC_FP32_BF16PR}[prec]
+    params = amg.default_params(precision=prec_id)
+    from paper_2102_07417_gb300.problems import CSR
+
+    A_dev = CSR(p.A.n, torch.as_tensor(p.A.rowptr, device=dev), torch.as_tensor(p.A.col, device=dev),
+                torch.as_tensor(p.A.val, device=dev))
+    b_dev = torch.as_tensor(p.b, device=dev)
+    x_dev = torch.zeros_like(b_dev)
+    stream = torch.cuda.current_stream(dev)
+    rec = {}
+
+    def step():
+        t0 = time.perf_counter()
+        h = amg.Hierarchy(A_dev, params, stream=stream)
+        t1 = time.perf_counter()
+        x_dev.zero_()
+        _, it, st, _ = h.solve(b_dev, x_dev, rtol=args.rtol, maxit=1000)
+        t2 = time.perf_counter()
+        rec.update(tp=t1 - t0, ts=t2 - t1, iters=it, status=st, info=h.info(), bytes=h.nbytes())
+        h.close()
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    tps, tss = [], []
+    clk = Clocks(gpu_uuid(local), not args.no_clocks)
+    amg.profile(True)
+    launches0 = amg.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+        tps.append(rec["tp"])
+        tss.append(rec["ts"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = amg.launch_count() - launches0
+    amg.profile(False)
+    clocks = clk.stop()
+    prof = amg.profile_read()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    x_err = None
+    if p.xstar is not None:
+        x_err = float(np.linalg.norm(x_dev.cpu().numpy() - p.xstar) / np.linalg.norm(p.xstar))
+
+    # roofline of the dominant kernel class (largest summed event time in the timed region)
+    peak, peak_src = peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    tr = traffic_for(dom)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
+            "avg_launch_us": d["ms"] * 1e3 / max(d["launches"], 1),
+            "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
+            "traffic": tr}
+    vb = sum(prof[k]["bytes"] for k in VCYCLE)
+    vt = sum(prof[k]["ms"] for k in VCYCLE)
+    kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                   "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+               for k, v in prof.items() if v["launches"]}
+
+    # end to end through the public one-call API with host buffers (H2D / D2H inside)
+    e2e = None
+    if not args.no_e2e:
+        A_h = p.A
+        bh = np.ascontiguousarray(p.b)
+        amg.solve(A_h, bh, params=params, rtol=args.rtol, maxit=1000, stream=stream)  # warm
+        reps = max(1, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            xh, res = amg.solve(A_h, bh, params=params, rtol=args.rtol, maxit=1000, stream=stream)
+        te = (time.perf_counter() - t0) / reps
+        if dist:
+            t = torch.tensor([te], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        n, nnz = p.A.n, p.A.nnz
+        e2e = {"value": te, "unit": "s", "h2d_bytes_per_step": 4 * (n + 1) + 12 * nnz + 16 * n,
+               "d2h_bytes_per_step": 8 * n + 8 + 8 * 10}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and p.A.n <= 4_200_000:
+        tp_o, ts_o, it_o, st_o = oracle_solve(p, args.rtol)
+        cpu = {"value": tp_o + ts_o, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"one full oracle set-up ({tp_o:.2f} s) + PCG solve ({ts_o:.2f} s, {it_o} it) of the workload",
+               "iters": it_o}
+
+    if rank != 0:
+        return
+    info = rec["info"]
+    out = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": desc, "n": p.A.n, "nnz": p.A.nnz, "precision": prec, "rtol": args.rtol,
+                   "theta": 0.25, "coarsening": "PMIS (seed 0)", "interpolation": "direct",
+                   "smoother": "Jacobi omega=2/3, V(1,1)", "max_coarse": 64,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": f"inputs larger than L2 (A is {(12 * p.A.nnz + 4 * p.A.n) / 1e6:.0f} MB of FP64 CSR)"},
+        "t_setup_ms": 1e3 * statistics.median(tps), "t_solve_ms": 1e3 * statistics.median(tss),
+        "iters": rec["iters"], "status": rec["status"], "nlevels": info["nlevels"], "cgd": info["cgd"],
+        "cop": info["cop"], "hierarchy_bytes": rec["bytes"], "x_rel_err": x_err,
+        "solves_per_s_all_ranks": world * 1e3 / ms,
+        "roofline": roof,
+        "vcycle_hbm": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s", "peak": peak,
+                       "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None},
+        "kernels": kernels,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = world > 1
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if dist:
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world, dist)
+    finally:
+        if dist:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -167,24 +167,35 @@ size_t amg_hierarchy_bytes(const amg_hierarchy *h);
 /* Releases the hierarchy (stream-ordered on the stream given to amg_setup). NULL is a no-op. */
 void amg_free(amg_hierarchy *h);
 
-/* Per-kernel timing of the solve phase with CUDA events on the launch stream.
- * amg_profile_enable(h, 1) starts recording (and clears the totals); 0 stops.
- * amg_profile_read(h, kernel, &launches, &ms, &bytes) returns, for kernel class
+/* Per-kernel timing with CUDA events on each launch's stream (process-wide,
+ * not thread-safe).  amg_profile_enable(1) clears the totals and starts
+ * recording every libamg kernel launch; amg_profile_enable(0) stops.
+ * amg_profile_read(kernel, &launches, &ms, &bytes) returns, for kernel class
  * `kernel` (AMG_K_*), the number of launches, their summed event-timed
- * duration and the algorithmic bytes they move (same accounting as the
- * roofline).  Totals are complete once the solve call has returned. */
-#define AMG_K_SPMV_DOT 0      /* q = A p and (p, q) */
-#define AMG_K_PCG_UPDATE 1    /* x += alpha p, r -= alpha q, ||r||, smoother input */
-#define AMG_K_SMOOTH_RESID 2  /* r_k = y_k - A_k s_k (pre-smoothed residual) */
-#define AMG_K_RESTRICT 3      /* y_{k+1} = R_k r_k */
-#define AMG_K_PROLONG 4       /* t_k = s_k + P_k z_{k+1} */
-#define AMG_K_SMOOTH_POST 5   /* z_k = t_k + omega D^-1 (y_k - A_k t_k) */
-#define AMG_K_COARSE 6        /* z_L = L^-T L^-1 y_L */
-#define AMG_K_DIRECTION 7     /* p = z + beta p */
-#define AMG_K_OTHER 8         /* initial residual, extra sweeps, copies */
-#define AMG_K_COUNT 9
-int amg_profile_enable(amg_hierarchy *h, int32_t on);
-int amg_profile_read(const amg_hierarchy *h, int32_t kernel, int64_t *launches, double *ms, double *bytes);
+ * duration and the algorithmic bytes they move (int32 indices, values and
+ * vectors counted once per launch; the accounting behind the roofline).
+ * Totals include every call that has returned. */
+#define AMG_K_SPMV_DOT 0      /* PCG: q = A p and (p, q) */
+#define AMG_K_PCG_UPDATE 1    /* PCG: x += alpha p, r -= alpha q, ||r||, smoother input */
+#define AMG_K_SMOOTH_RESID 2  /* V-cycle: r_k = y_k - A_k s_k (pre-smoothed residual) */
+#define AMG_K_RESTRICT 3      /* V-cycle: y_{k+1} = R_k r_k */
+#define AMG_K_PROLONG 4       /* V-cycle: t_k = s_k + P_k z_{k+1} */
+#define AMG_K_SMOOTH_POST 5   /* V-cycle: z_k = t_k + omega D^-1 (y_k - A_k t_k) */
+#define AMG_K_COARSE 6        /* V-cycle: z_L = L^-T L^-1 y_L */
+#define AMG_K_DIRECTION 7     /* PCG: p = z + beta p */
+#define AMG_K_SOLVE_OTHER 8   /* initial residual, extra sweeps, copies, level SpMV */
+#define AMG_K_STRENGTH 9      /* set-up: validation, strength, PMIS measures */
+#define AMG_K_PMIS 10         /* set-up: PMIS rounds and C/F output */
+#define AMG_K_INTERP 11       /* set-up: direct interpolation */
+#define AMG_K_TRANSPOSE 12    /* set-up: R = P^T */
+#define AMG_K_SPGEMM 13       /* set-up: Galerkin SpGEMM (A P, then R (A P)) */
+#define AMG_K_SETUP_OTHER 14  /* set-up: scans, dense factor, casts, diagonal */
+#define AMG_K_COUNT 15
+int amg_profile_enable(int32_t on);
+int amg_profile_read(int32_t kernel, int64_t *launches, double *ms, double *bytes);
+
+/* Number of libamg kernel launches in this process so far. */
+int64_t amg_launch_count(void);
 
 /* Static strings; never NULL. */
 const char *amg_status_string(int status);

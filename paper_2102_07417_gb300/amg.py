@@ -28,14 +28,15 @@ AMG_ERR_UNSUPPORTED = -9
 
 PREC_FP64, PREC_FP32, PREC_FP32_BF16PR = 0, 1, 2
 
-K_SPMV_DOT, K_PCG_UPDATE, K_SMOOTH_RESID, K_RESTRICT, K_PROLONG, K_SMOOTH_POST, K_COARSE, K_DIRECTION, K_OTHER = range(9)
 KERNEL_NAMES = ["spmv_dot", "pcg_update", "smooth_resid", "restrict", "prolong", "smooth_post", "coarse",
-                "direction", "other"]
+                "direction", "solve_other", "strength", "pmis", "interp", "transpose", "spgemm", "setup_other"]
+SOLVE_KERNELS = KERNEL_NAMES[:9]
+SETUP_KERNELS = KERNEL_NAMES[9:]
 
 # Names exported by the C ABI (each declared in include/amg.h).
 EXPORTS = ["amg_params_default", "amg_setup", "amg_pcg_solve", "amg_vcycle_apply", "amg_spmv", "amg_solve",
            "amg_hierarchy_info", "amg_hierarchy_export", "amg_hierarchy_bytes", "amg_free", "amg_profile_enable",
-           "amg_profile_read", "amg_status_string", "amg_last_error"]
+           "amg_profile_read", "amg_launch_count", "amg_status_string", "amg_last_error"]
 
 
 class AmgError(RuntimeError):
@@ -100,8 +101,10 @@ def load(build_if_missing: bool = True):
     L.amg_hierarchy_bytes.restype = C.c_size_t
     L.amg_free.argtypes = [vp]
     L.amg_free.restype = None
-    L.amg_profile_enable.argtypes = [vp, i32]
-    L.amg_profile_read.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]
+    L.amg_profile_enable.argtypes = [i32]
+    L.amg_profile_read.argtypes = [i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]
+    L.amg_launch_count.argtypes = []
+    L.amg_launch_count.restype = C.c_int64
     L.amg_status_string.argtypes = [C.c_int]
     L.amg_status_string.restype = C.c_char_p
     L.amg_last_error.argtypes = []
@@ -265,16 +268,26 @@ class Hierarchy:
     def nbytes(self) -> int:
         return int(load().amg_hierarchy_bytes(self.h))
 
-    def profile(self, on: bool):
-        check(load().amg_profile_enable(self.h, 1 if on else 0), "amg_profile_enable")
 
-    def profile_read(self) -> dict:
-        out = {}
-        for k, name in enumerate(KERNEL_NAMES):
-            n, ms, by = C.c_int64(), C.c_double(), C.c_double()
-            check(load().amg_profile_read(self.h, k, C.byref(n), C.byref(ms), C.byref(by)), "amg_profile_read")
-            out[name] = {"launches": n.value, "ms": ms.value, "bytes": by.value}
-        return out
+
+def profile(on: bool):
+    """Start (clearing totals) or stop process-wide per-launch CUDA-event timing."""
+    check(load().amg_profile_enable(1 if on else 0), "amg_profile_enable")
+
+
+def profile_read() -> dict:
+    """Per kernel class: launches, summed event time (ms) and algorithmic bytes."""
+    out = {}
+    for k, name in enumerate(KERNEL_NAMES):
+        n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+        check(load().amg_profile_read(k, C.byref(n), C.byref(ms), C.byref(by)), "amg_profile_read")
+        out[name] = {"launches": n.value, "ms": ms.value, "bytes": by.value}
+    return out
+
+
+def launch_count() -> int:
+    """libamg kernel launches in this process so far."""
+    return int(load().amg_launch_count())
 
 
 def solve(A, b, x0=None, params: Params | None = None, rtol: float = 1e-8, maxit: int = 500, stream=None,

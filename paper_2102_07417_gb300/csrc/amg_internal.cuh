@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -34,7 +35,12 @@ struct Status {
     }                                                                                        \
   } while (0)
 
-#define AMG_CHECK_LAUNCH() AMG_CUDA(cudaGetLastError())
+extern std::atomic<long long> g_launches;
+#define AMG_CHECK_LAUNCH()                                    \
+  do {                                                        \
+    ::amg::g_launches.fetch_add(1, std::memory_order_relaxed); \
+    AMG_CUDA(cudaGetLastError());                             \
+  } while (0)
 
 // Device memory through the caller's allocator (or cudaMallocAsync).
 struct Mem {
@@ -116,6 +122,7 @@ struct Level {
   void *y = nullptr, *s = nullptr, *r = nullptr, *z = nullptr, *w = nullptr;
 };
 
+// Process-wide per-launch event timing (amg_profile_enable).
 struct Profile {
   bool on = false;
   std::vector<cudaEvent_t> ev;  // pool of events, two per recorded launch
@@ -126,6 +133,17 @@ struct Profile {
   double ms[AMG_K_COUNT] = {};
   double total_bytes[AMG_K_COUNT] = {};
 };
+extern Profile g_prof;
+
+// Brackets one kernel launch with two events when profiling is on.
+struct ProfScope {
+  size_t slot = (size_t)-1;
+  cudaStream_t stream;
+  ProfScope(cudaStream_t s, int kind, double bytes);
+  ~ProfScope();
+};
+// Folds recorded event pairs into the totals; synchronises `s` first.
+void prof_collect(cudaStream_t s);
 
 }  // namespace amg
 
@@ -147,7 +165,6 @@ struct amg_hierarchy {
   int *h_done = nullptr;           // mapped pinned host flag (written by the device)
   int *d_done = nullptr;           // its device alias
   cudaEvent_t iter_ev[2] = {nullptr, nullptr};
-  amg::Profile prof;
   size_t bytes = 0;
 };
 
@@ -162,6 +179,9 @@ int pcg_solve(amg_hierarchy *h, const double *b, double *x, double rtol, int max
 void vcycle_apply(amg_hierarchy *h, const double *y, double *z);
 void spmv_level(amg_hierarchy *h, int level, const double *x, double *y);
 void release_solve(amg_hierarchy *h);
+
+// C = X Y with the canonical summation order (spgemm.cu); flags: device error flags
+void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C);
 
 // device-wide exclusive scan of n int32 counts into out[0..n] (out[n] = total); returns total
 int64_t scan_counts(Mem &mem, const int *in, int *out, int n);

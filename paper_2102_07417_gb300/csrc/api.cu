@@ -2,7 +2,9 @@
 // checks, allocation, error translation; the work is in setup.cu / solve.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstring>
 
@@ -11,6 +13,48 @@
 namespace amg {
 
 static thread_local char g_err[512] = "";
+std::atomic<long long> g_launches{0};
+Profile g_prof;
+
+ProfScope::ProfScope(cudaStream_t s, int kind, double bytes) : stream(s) {
+  Profile &pr = g_prof;
+  if (!pr.on) return;
+  if (pr.used * 2 + 2 > pr.ev.size()) {
+    const size_t add = std::max<size_t>(2048, pr.ev.size());
+    for (size_t t = 0; t < add; ++t) {
+      cudaEvent_t e;
+      AMG_CUDA(cudaEventCreate(&e));
+      pr.ev.push_back(e);
+    }
+  }
+  slot = pr.used++;
+  if (pr.kind.size() < pr.used) {
+    pr.kind.resize(pr.used);
+    pr.bytes.resize(pr.used);
+  }
+  pr.kind[slot] = kind;
+  pr.bytes[slot] = bytes;
+  AMG_CUDA(cudaEventRecord(pr.ev[2 * slot], s));
+}
+
+ProfScope::~ProfScope() {
+  if (slot != (size_t)-1) cudaEventRecord(g_prof.ev[2 * slot + 1], stream);
+}
+
+void prof_collect(cudaStream_t s) {
+  Profile &pr = g_prof;
+  if (!pr.used) return;
+  AMG_CUDA(cudaStreamSynchronize(s));
+  for (size_t k = 0; k < pr.used; ++k) {
+    float ms = 0.f;
+    AMG_CUDA(cudaEventSynchronize(pr.ev[2 * k + 1]));
+    AMG_CUDA(cudaEventElapsedTime(&ms, pr.ev[2 * k], pr.ev[2 * k + 1]));
+    pr.launches[pr.kind[k]] += 1;
+    pr.ms[pr.kind[k]] += ms;
+    pr.total_bytes[pr.kind[k]] += pr.bytes[k];
+  }
+  pr.used = 0;
+}
 
 void set_error(const char *fmt, ...) {
   va_list ap;
@@ -139,6 +183,7 @@ int amg_setup(const amg_csr *A, const amg_params *params, const amg_allocator *a
     amg::build_hierarchy(h, *A);
     amg::prepare_solve(h);
     AMG_CUDA(cudaStreamSynchronize(h->mem.stream));
+    amg::prof_collect(h->mem.stream);
   } catch (const Status &e) {
     cudaStreamSynchronize(h->mem.stream);
     amg_free(h);
@@ -182,6 +227,7 @@ int amg_spmv(amg_hierarchy *h, int32_t level, const double *x, double *y, void *
   AMG_GUARD_BEGIN
   h->mem.stream = static_cast<cudaStream_t>(stream);
   amg::spmv_level(h, level, x, y);
+  amg::prof_collect(h->mem.stream);
   return AMG_OK;
   AMG_GUARD_END
 }
@@ -286,28 +332,30 @@ int amg_hierarchy_export(const amg_hierarchy *h, int32_t level, int8_t *cf, int3
 
 size_t amg_hierarchy_bytes(const amg_hierarchy *h) { return h ? h->mem.live_bytes : 0; }
 
-int amg_profile_enable(amg_hierarchy *h, int32_t on) {
-  if (!h) return bad("NULL hierarchy");
-  h->prof.on = on != 0;
+int amg_profile_enable(int32_t on) {
+  amg::Profile &pr = amg::g_prof;
+  pr.on = on != 0;
   if (on) {
     for (int k = 0; k < AMG_K_COUNT; ++k) {
-      h->prof.launches[k] = 0;
-      h->prof.ms[k] = 0.0;
-      h->prof.total_bytes[k] = 0.0;
+      pr.launches[k] = 0;
+      pr.ms[k] = 0.0;
+      pr.total_bytes[k] = 0.0;
     }
-    h->prof.used = 0;
+    pr.used = 0;
   }
   return AMG_OK;
 }
 
-int amg_profile_read(const amg_hierarchy *h, int32_t kernel, int64_t *launches, double *ms, double *bytes) {
-  if (!h) return bad("NULL hierarchy");
+int amg_profile_read(int32_t kernel, int64_t *launches, double *ms, double *bytes) {
   if (kernel < 0 || kernel >= AMG_K_COUNT) return bad("kernel class out of range");
-  if (launches) *launches = h->prof.launches[kernel];
-  if (ms) *ms = h->prof.ms[kernel];
-  if (bytes) *bytes = h->prof.total_bytes[kernel];
+  const amg::Profile &pr = amg::g_prof;
+  if (launches) *launches = pr.launches[kernel];
+  if (ms) *ms = pr.ms[kernel];
+  if (bytes) *bytes = pr.total_bytes[kernel];
   return AMG_OK;
 }
+
+int64_t amg_launch_count(void) { return amg::g_launches.load(); }
 
 const char *amg_status_string(int status) {
   switch (status) {

@@ -373,194 +373,6 @@ __global__ void k_sort_rows(int m, const int *__restrict__ rp, const int *__rest
   }
 }
 
-// ------------------------------------------------------------- SpGEMM --
-// C = X Y.  Row classes by the upper bound ub_i = sum_{p in X_i} nnz(Y_{x_p}):
-//   W: ub <= 1024, a warp per row, hash table of 2048 slots in shared memory;
-//   B: ub <= 8192, a block per row, 16384-slot table in shared memory;
-//   G: larger, a block per row, table in a global scratch slice per block.
-constexpr int W_UB = 1024, W_TAB = 2048, W_WARPS = 4;
-constexpr int B_UB = 8192, B_TAB = 16384, B_T = 256;
-
-__global__ void k_spgemm_ub(int m, const int *__restrict__ xrp, const int *__restrict__ xci,
-                            const int *__restrict__ yrp, int *__restrict__ lists, int *__restrict__ list_cnt,
-                            int *__restrict__ max_ub, int *flags) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  int64_t ub = 0;
-  for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
-    const int k = xci[p];
-    ub += yrp[k + 1] - yrp[k];
-  }
-  if (ub > (1 << 30)) {
-    flags[3] = 1;
-    ub = 1 << 30;
-  }
-  const int cls = ub <= W_UB ? 0 : (ub <= B_UB ? 1 : 2);
-  const int slot = atomicAdd(&list_cnt[cls], 1);
-  lists[(int64_t)cls * m + slot] = i;
-  if (cls == 2) atomicMax(max_ub, (int)ub);
-}
-
-__device__ __forceinline__ bool hash_insert(int *table, unsigned mask, int key, int *flags) {
-  unsigned h = ((unsigned)key * 2654435761u) & mask;
-  for (unsigned probe = 0; probe <= mask; ++probe) {
-    const int prev = atomicCAS(&table[h], -1, key);
-    if (prev == -1) return true;
-    if (prev == key) return false;
-    h = (h + 1) & mask;
-  }
-  flags[3] = 1;  // table full: cannot happen while ub <= capacity / 2
-  return false;
-}
-
-__device__ __forceinline__ int bsearch_sorted(const int *a, int len, int key) {
-  int lo = 0, hi = len - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (a[mid] < key) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
-// Warp per row.  FILL = false: count distinct columns into cnt[i].
-// FILL = true: write the sorted columns and the canonically summed values.
-template <bool FILL>
-__global__ void __launch_bounds__(W_WARPS * 32) k_spgemm_warp(
-    const int *__restrict__ rows, int nrows, const int *__restrict__ xrp, const int *__restrict__ xci,
-    const double *__restrict__ xv, const int *__restrict__ yrp, const int *__restrict__ yci,
-    const double *__restrict__ yv, const int *__restrict__ crp, int *__restrict__ cci, double *__restrict__ cv,
-    int *__restrict__ cnt, int *flags) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int *table = reinterpret_cast<int *>(smem) + warp * W_TAB;
-  int *sorted = reinterpret_cast<int *>(smem) + W_WARPS * W_TAB + warp * W_UB;
-  double *acc = reinterpret_cast<double *>(smem + 4 * W_WARPS * (W_TAB + W_UB)) + warp * W_UB;
-  int *tmp = reinterpret_cast<int *>(acc);  // unsorted keys, reused as accumulator afterwards
-  for (int r = blockIdx.x * W_WARPS + warp; r < nrows; r += gridDim.x * W_WARPS) {
-    const int i = rows[r];
-    for (int t = lane; t < W_TAB; t += 32) table[t] = -1;
-    __syncwarp();
-    int mine = 0;
-    const int xb = xrp[i], xe = xrp[i + 1];
-    for (int p = xb; p < xe; ++p) {
-      const int k = xci[p];
-      for (int q = yrp[k] + lane; q < yrp[k + 1]; q += 32) mine += hash_insert(table, W_TAB - 1, yci[q], flags);
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-    const int count = mine;
-    if (!FILL) {
-      if (lane == 0) cnt[i] = count;
-      __syncwarp();
-      continue;
-    }
-    __syncwarp();
-    int base = 0;
-    for (int t0 = 0; t0 < W_TAB; t0 += 32) {
-      const int key = table[t0 + lane];
-      const unsigned bal = __ballot_sync(0xffffffffu, key >= 0);
-      if (key >= 0) tmp[base + __popc(bal & ((1u << lane) - 1u))] = key;
-      base += __popc(bal);
-    }
-    __syncwarp();
-    for (int e = lane; e < count; e += 32) {
-      const int key = tmp[e];
-      int rank = 0;
-      for (int f = 0; f < count; ++f) rank += tmp[f] < key;
-      sorted[rank] = key;
-    }
-    __syncwarp();
-    const int cb = crp[i];
-    for (int e = lane; e < count; e += 32) {
-      cci[cb + e] = sorted[e];
-      acc[e] = 0.0;
-    }
-    __syncwarp();
-    for (int p = xb; p < xe; ++p) {
-      const int k = xci[p];
-      const double x = xv[p];
-      for (int q = yrp[k] + lane; q < yrp[k + 1]; q += 32) {
-        const int pos = bsearch_sorted(sorted, count, yci[q]);
-        acc[pos] = __dadd_rn(acc[pos], __dmul_rn(x, yv[q]));
-      }
-      __syncwarp();
-    }
-    for (int e = lane; e < count; e += 32) cv[cb + e] = acc[e];
-    __syncwarp();
-  }
-}
-
-// Block per row; table / lists in shared memory (GLOBAL = false) or in a
-// per-block slice of global scratch of `cap` table slots (GLOBAL = true).
-template <bool FILL, bool GLOBAL>
-__global__ void __launch_bounds__(B_T) k_spgemm_block(
-    const int *__restrict__ rows, int nrows, const int *__restrict__ xrp, const int *__restrict__ xci,
-    const double *__restrict__ xv, const int *__restrict__ yrp, const int *__restrict__ yci,
-    const double *__restrict__ yv, const int *__restrict__ crp, int *__restrict__ cci, double *__restrict__ cv,
-    int *__restrict__ cnt, int *flags, unsigned char *gscratch, int cap) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_count;
-  unsigned char *base_ptr = GLOBAL ? gscratch + (size_t)blockIdx.x * ((size_t)cap * 4 + (size_t)cap / 2 * 16) : smem;
-  const int tcap = GLOBAL ? cap : B_TAB;
-  int *table = reinterpret_cast<int *>(base_ptr);
-  int *tmp = table + tcap;
-  int *sorted = tmp + tcap / 2;
-  double *acc = reinterpret_cast<double *>(sorted + tcap / 2);
-  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
-    const int i = rows[r];
-    for (int t = threadIdx.x; t < tcap; t += blockDim.x) table[t] = -1;
-    if (threadIdx.x == 0) s_count = 0;
-    __syncthreads();
-    const int xb = xrp[i], xe = xrp[i + 1];
-    int mine = 0;
-    for (int p = xb; p < xe; ++p) {
-      const int k = xci[p];
-      for (int q = yrp[k] + threadIdx.x; q < yrp[k + 1]; q += blockDim.x)
-        mine += hash_insert(table, tcap - 1, yci[q], flags);
-    }
-    if (mine) atomicAdd(&s_count, mine);
-    __syncthreads();
-    const int count = s_count;
-    if (!FILL) {
-      if (threadIdx.x == 0) cnt[i] = count;
-      __syncthreads();
-      continue;
-    }
-    if (threadIdx.x == 0) s_count = 0;
-    __syncthreads();
-    for (int t = threadIdx.x; t < tcap; t += blockDim.x) {
-      const int key = table[t];
-      if (key >= 0) tmp[atomicAdd(&s_count, 1)] = key;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < count; e += blockDim.x) {
-      const int key = tmp[e];
-      int rank = 0;
-      for (int f = 0; f < count; ++f) rank += tmp[f] < key;
-      sorted[rank] = key;
-    }
-    __syncthreads();
-    const int cb = crp[i];
-    for (int e = threadIdx.x; e < count; e += blockDim.x) {
-      cci[cb + e] = sorted[e];
-      acc[e] = 0.0;
-    }
-    __syncthreads();
-    for (int p = xb; p < xe; ++p) {
-      const int k = xci[p];
-      const double x = xv[p];
-      for (int q = yrp[k] + threadIdx.x; q < yrp[k + 1]; q += blockDim.x) {
-        const int pos = bsearch_sorted(sorted, count, yci[q]);
-        acc[pos] = __dadd_rn(acc[pos], __dmul_rn(x, yv[q]));
-      }
-      __syncthreads();
-    }
-    for (int e = threadIdx.x; e < count; e += blockDim.x) cv[cb + e] = acc[e];
-    __syncthreads();
-  }
-}
-
 // ------------------------------------------------------------ dense LL^T --
 __global__ void k_to_dense(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                            const double *__restrict__ v, double *__restrict__ M) {
@@ -631,8 +443,11 @@ void transpose(Mem &m, const DCsr &P, int ncols, DCsr &R) {
   cudaStream_t s = m.stream;
   Buf<int> cnt(m, (size_t)ncols + 1);
   AMG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * ((size_t)ncols + 1), s));
-  if (P.nnz) k_col_count<<<ceil_div(P.nnz, TPB), TPB, 0, s>>>(P.nnz, P.ci, cnt.p);
-  AMG_CHECK_LAUNCH();
+  if (P.nnz) {
+    ProfScope ps(s, AMG_K_TRANSPOSE, 4.0 * P.nnz + 4.0 * ncols);
+    k_col_count<<<ceil_div(P.nnz, TPB), TPB, 0, s>>>(P.nnz, P.ci, cnt.p);
+    AMG_CHECK_LAUNCH();
+  }
   R.n = ncols;
   R.ncols = P.n;
   R.nnz = P.nnz;
@@ -644,78 +459,15 @@ void transpose(Mem &m, const DCsr &P, int ncols, DCsr &R) {
   AMG_CUDA(cudaMemcpyAsync(fill.p, R.rp, sizeof(int) * ((size_t)ncols + 1), cudaMemcpyDeviceToDevice, s));
   Buf<int> tci(m, std::max<int64_t>(R.nnz, 1));
   Buf<double> tv(m, std::max<int64_t>(R.nnz, 1));
-  k_transpose_scatter<<<ceil_div(P.n, TPB), TPB, 0, s>>>(P.n, P.rp, P.ci, P.v, fill.p, tci.p, tv.p);
-  AMG_CHECK_LAUNCH();
-  k_sort_rows<<<ceil_div((int64_t)ncols * 32, TPB), TPB, 0, s>>>(ncols, R.rp, tci.p, tv.p, R.ci, R.v);
-  AMG_CHECK_LAUNCH();
-}
-
-size_t warp_smem() { return (size_t)W_WARPS * (W_TAB * 4 + W_UB * 4 + W_UB * 8); }
-size_t block_smem() { return (size_t)B_TAB * 4 + (size_t)B_TAB / 2 * 4 * 2 + (size_t)B_TAB / 2 * 8; }
-
-// C = X Y with the canonical order (see file header).
-void spgemm(Mem &m, Flags &fl, const DCsr &X, const DCsr &Y, int ncols, DCsr &C) {
-  cudaStream_t s = m.stream;
-  const int rows = X.n;
-  Buf<int> lists(m, (size_t)rows * 3);
-  Buf<int> meta(m, 4);  // list counts [3], max ub
-  AMG_CUDA(cudaMemsetAsync(meta.p, 0, sizeof(int) * 4, s));
-  k_spgemm_ub<<<ceil_div(rows, TPB), TPB, 0, s>>>(rows, X.rp, X.ci, Y.rp, lists.p, meta.p, meta.p + 3, fl.d);
-  AMG_CHECK_LAUNCH();
-  int hm[4];
-  AMG_CUDA(cudaMemcpyAsync(hm, meta.p, sizeof(hm), cudaMemcpyDeviceToHost, s));
-  AMG_CUDA(cudaStreamSynchronize(s));
-  if (hm[3] > (1 << 22)) fail(AMG_ERR_UNSUPPORTED, "SpGEMM row product bound above 2^22 entries");
-  int gcap = 2;
-  while (gcap < 2 * std::max(hm[3], 1)) gcap <<= 1;
-  const int gblocks = std::min(hm[2], kNumSMs);
-  Buf<unsigned char> gscr;
-  if (hm[2] > 0) gscr = Buf<unsigned char>(m, (size_t)gblocks * ((size_t)gcap * 4 + (size_t)gcap / 2 * 16));
-
-  static bool attr_done = false;
-  if (!attr_done) {
-    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem()));
-    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem()));
-    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_block<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem()));
-    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_block<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem()));
-    attr_done = true;
+  {
+    ProfScope ps(s, AMG_K_TRANSPOSE, 4.0 * (P.n + 1) + 24.0 * P.nnz + 4.0 * ncols);
+    k_transpose_scatter<<<ceil_div(P.n, TPB), TPB, 0, s>>>(P.n, P.rp, P.ci, P.v, fill.p, tci.p, tv.p);
+    AMG_CHECK_LAUNCH();
   }
-  const int *lw = lists.p, *lb = lists.p + rows, *lg = lists.p + 2 * (size_t)rows;
-  auto grid_w = [&](int nr) { return std::max(1, std::min(ceil_div(nr, W_WARPS), kNumSMs * 16)); };
-  auto grid_b = [&](int nr) { return std::max(1, std::min(nr, kNumSMs * 2)); };
-
-  Buf<int> cnt(m, (size_t)rows + 1);
-  for (int pass = 0; pass < 2; ++pass) {
-    const bool fillp = pass == 1;
-    if (fillp) {
-      C.n = rows;
-      C.ncols = ncols;
-      C.rp = m.get_n<int>((size_t)rows + 1);
-      C.nnz = scan_counts(m, cnt.p, C.rp, rows);
-      C.ci = m.get_n<int>(std::max<int64_t>(C.nnz, 1));
-      C.v = m.get_n<double>(std::max<int64_t>(C.nnz, 1));
-    }
-    if (hm[0] > 0) {
-      if (fillp)
-        k_spgemm_warp<true><<<grid_w(hm[0]), W_WARPS * 32, warp_smem(), s>>>(lw, hm[0], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, C.rp, C.ci, C.v, cnt.p, fl.d);
-      else
-        k_spgemm_warp<false><<<grid_w(hm[0]), W_WARPS * 32, warp_smem(), s>>>(lw, hm[0], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, nullptr, nullptr, nullptr, cnt.p, fl.d);
-      AMG_CHECK_LAUNCH();
-    }
-    if (hm[1] > 0) {
-      if (fillp)
-        k_spgemm_block<true, false><<<grid_b(hm[1]), B_T, block_smem(), s>>>(lb, hm[1], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, C.rp, C.ci, C.v, cnt.p, fl.d, nullptr, 0);
-      else
-        k_spgemm_block<false, false><<<grid_b(hm[1]), B_T, block_smem(), s>>>(lb, hm[1], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, nullptr, nullptr, nullptr, cnt.p, fl.d, nullptr, 0);
-      AMG_CHECK_LAUNCH();
-    }
-    if (hm[2] > 0) {
-      if (fillp)
-        k_spgemm_block<true, true><<<gblocks, B_T, 0, s>>>(lg, hm[2], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, C.rp, C.ci, C.v, cnt.p, fl.d, gscr.p, gcap);
-      else
-        k_spgemm_block<false, true><<<gblocks, B_T, 0, s>>>(lg, hm[2], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, nullptr, nullptr, nullptr, cnt.p, fl.d, gscr.p, gcap);
-      AMG_CHECK_LAUNCH();
-    }
+  {
+    ProfScope ps(s, AMG_K_TRANSPOSE, 4.0 * (ncols + 1) + 24.0 * P.nnz);
+    k_sort_rows<<<ceil_div((int64_t)ncols * 32, TPB), TPB, 0, s>>>(ncols, R.rp, tci.p, tv.p, R.ci, R.v);
+    AMG_CHECK_LAUNCH();
   }
 }
 
@@ -733,6 +485,7 @@ int64_t scan_counts(Mem &m, const int *in, int *out, int n) {
   cudaStream_t s = m.stream;
   const int nb = std::max(1, ceil_div(n, SCAN_TILE));
   Buf<long long> bsum(m, (size_t)nb + 1);
+  ProfScope ps(s, AMG_K_SETUP_OTHER, 8.0 * n + 8.0 * nb);
   k_scan_reduce<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p);
   AMG_CHECK_LAUNCH();
   k_scan_blocks<<<1, SCAN_T, 0, s>>>(bsum.p, nb);
@@ -773,8 +526,11 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
   AMG_CUDA(cudaMemcpyAsync(A0.rp, Ain.rowptr, sizeof(int) * ((size_t)n0 + 1), kind, s));
   AMG_CUDA(cudaMemcpyAsync(A0.ci, Ain.colidx, sizeof(int) * (size_t)nnz0, kind, s));
   AMG_CUDA(cudaMemcpyAsync(A0.v, Ain.val, sizeof(double) * (size_t)nnz0, kind, s));
-  k_validate<<<ceil_div(n0, TPB), TPB, 0, s>>>(n0, nnz0, A0.rp, A0.ci, A0.v, fl.d);
-  AMG_CHECK_LAUNCH();
+  {
+    ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n0 + 1) + 12.0 * nnz0);
+    k_validate<<<ceil_div(n0, TPB), TPB, 0, s>>>(n0, nnz0, A0.rp, A0.ci, A0.v, fl.d);
+    AMG_CHECK_LAUNCH();
+  }
   read_flags(m, fl);
   if (fl.h[0]) fail(AMG_ERR_INVALID_ARG, "malformed CSR (row pointers, column range or unsorted columns)");
   if (fl.h[1]) fail(AMG_ERR_NOT_SPD, "a diagonal entry is missing or not positive");
@@ -795,25 +551,41 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       Buf<int8_t> st0(m, n), st1(m, n);
       Buf<int> und(m, 1);
       const int g = ceil_div(n, TPB);
-      k_strength<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
-      AMG_CHECK_LAUNCH();
-      k_pmis_init<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
-      AMG_CHECK_LAUNCH();
+      const double nz = (double)A.nnz, rows = 4.0 * (n + 1);
+      {
+        ProfScope ps(s, AMG_K_STRENGTH, rows + 13.0 * nz);
+        k_strength<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
+        AMG_CHECK_LAUNCH();
+      }
+      {
+        ProfScope ps(s, AMG_K_STRENGTH, rows + 6.0 * nz + 9.0 * n);
+        k_pmis_init<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
+        AMG_CHECK_LAUNCH();
+      }
       read_flags(m, fl);
       if (fl.h[2]) fail(AMG_ERR_INVALID_ARG, "matrix pattern is not structurally symmetric");
       for (int round = 0;; ++round) {
         if (round > n + 1) fail(AMG_ERR_SETUP, "PMIS did not terminate");
         AMG_CUDA(cudaMemsetAsync(und.p, 0, sizeof(int), s));
-        k_pmis_select<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, st1.p);
-        AMG_CHECK_LAUNCH();
-        k_pmis_update<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, st1.p, st0.p, und.p);
-        AMG_CHECK_LAUNCH();
+        {
+          ProfScope ps(s, AMG_K_PMIS, rows + 6.0 * nz + 10.0 * n);
+          k_pmis_select<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, st1.p);
+          AMG_CHECK_LAUNCH();
+        }
+        {
+          ProfScope ps(s, AMG_K_PMIS, rows + 5.0 * nz + 2.0 * n);
+          k_pmis_update<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, st1.p, st0.p, und.p);
+          AMG_CHECK_LAUNCH();
+        }
         if (read_int(m, und.p) == 0) break;
       }
       L.cf = m.get_n<int8_t>(n);
       Buf<int> isC(m, n);
-      k_cf_out<<<g, TPB, 0, s>>>(n, st0.p, L.cf, isC.p);
-      AMG_CHECK_LAUNCH();
+      {
+        ProfScope ps(s, AMG_K_PMIS, 6.0 * n);
+        k_cf_out<<<g, TPB, 0, s>>>(n, st0.p, L.cf, isC.p);
+        AMG_CHECK_LAUNCH();
+      }
       cidx = Buf<int>(m, (size_t)n + 1);
       nc = (int)scan_counts(m, isC.p, cidx.p, n);
       if (nc == 0 || (double)nc > 0.9 * (double)n) {
@@ -827,10 +599,13 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       h->nL = n;
       h->L = m.get_n<double>((size_t)n * n);
       AMG_CUDA(cudaMemsetAsync(h->L, 0, sizeof(double) * (size_t)n * n, s));
-      k_to_dense<<<ceil_div(n, TPB), TPB, 0, s>>>(n, A.rp, A.ci, A.v, h->L);
-      AMG_CHECK_LAUNCH();
-      k_cholesky<<<1, 256, 0, s>>>(n, h->L, fl.d);
-      AMG_CHECK_LAUNCH();
+      {
+        ProfScope ps(s, AMG_K_SETUP_OTHER, 4.0 * (n + 1) + 12.0 * A.nnz + 16.0 * (double)n * n);
+        k_to_dense<<<ceil_div(n, TPB), TPB, 0, s>>>(n, A.rp, A.ci, A.v, h->L);
+        AMG_CHECK_LAUNCH();
+        k_cholesky<<<1, 256, 0, s>>>(n, h->L, fl.d);
+        AMG_CHECK_LAUNCH();
+      }
       read_flags(m, fl);
       if (fl.h[4]) fail(AMG_ERR_NOT_SPD, "dense Cholesky of the last level met a non-positive pivot");
       h->nlevels = k + 1;
@@ -841,24 +616,30 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     DCsr &P = L.P;
     {
       Buf<int> pcnt(m, n);
-      k_interp_count<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, L.cf, pcnt.p);
-      AMG_CHECK_LAUNCH();
+      {
+        ProfScope ps(s, AMG_K_INTERP, 4.0 * (n + 1) + 5.0 * A.nnz + 5.0 * n);
+        k_interp_count<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, L.cf, pcnt.p);
+        AMG_CHECK_LAUNCH();
+      }
       P.n = n;
       P.ncols = nc;
       P.rp = m.get_n<int>((size_t)n + 1);
       P.nnz = scan_counts(m, pcnt.p, P.rp, n);
       P.ci = m.get_n<int>(std::max<int64_t>(P.nnz, 1));
       P.v = m.get_n<double>(std::max<int64_t>(P.nnz, 1));
-      k_interp_fill<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, P.rp, P.ci, P.v);
-      AMG_CHECK_LAUNCH();
+      {
+        ProfScope ps(s, AMG_K_INTERP, 8.0 * (n + 1) + 13.0 * A.nnz + 5.0 * n + 12.0 * P.nnz);
+        k_interp_fill<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, P.rp, P.ci, P.v);
+        AMG_CHECK_LAUNCH();
+      }
     }
     S.reset();
     ST.reset();
     cidx.reset();
     transpose(m, P, nc, L.R);
     DCsr AP;
-    spgemm(m, fl, A, P, nc, AP);
-    spgemm(m, fl, L.R, AP, nc, h->lev[k + 1].A);
+    spgemm(m, fl.d, A, P, nc, AP);
+    spgemm(m, fl.d, L.R, AP, nc, h->lev[k + 1].A);
     free_csr(m, AP);
     read_flags(m, fl);
     if (fl.h[3]) fail(AMG_ERR_UNSUPPORTED, "SpGEMM hash table overflow");

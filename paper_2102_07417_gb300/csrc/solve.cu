@@ -385,49 +385,6 @@ __global__ void k_to_bf16(int64_t n, const double *__restrict__ a, __nv_bfloat16
 
 inline int grid_for(int64_t n) { return std::max(1, std::min<int>(ceil_div(n, TPB), MAX_GRID)); }
 
-// --------------------------------------------------------------- profiling --
-struct ProfScope {
-  amg_hierarchy *h;
-  int kind;
-  double bytes;
-  size_t slot = (size_t)-1;
-  ProfScope(amg_hierarchy *hh, int k, double b) : h(hh), kind(k), bytes(b) {
-    Profile &pr = h->prof;
-    if (!pr.on) return;
-    if (pr.used * 2 + 2 > pr.ev.size()) {
-      const size_t add = std::max<size_t>(1024, pr.ev.size());
-      for (size_t t = 0; t < add; ++t) {
-        cudaEvent_t e;
-        AMG_CUDA(cudaEventCreate(&e));
-        pr.ev.push_back(e);
-      }
-    }
-    slot = pr.used++;
-    pr.kind.resize(pr.used);
-    pr.bytes.resize(pr.used);
-    pr.kind[slot] = k;
-    pr.bytes[slot] = b;
-    AMG_CUDA(cudaEventRecord(pr.ev[2 * slot], h->mem.stream));
-  }
-  ~ProfScope() {
-    if (slot != (size_t)-1) cudaEventRecord(h->prof.ev[2 * slot + 1], h->mem.stream);
-  }
-};
-
-void prof_collect(amg_hierarchy *h) {
-  Profile &pr = h->prof;
-  if (!pr.used) return;
-  AMG_CUDA(cudaStreamSynchronize(h->mem.stream));
-  for (size_t s = 0; s < pr.used; ++s) {
-    float ms = 0.f;
-    AMG_CUDA(cudaEventElapsedTime(&ms, pr.ev[2 * s], pr.ev[2 * s + 1]));
-    pr.launches[pr.kind[s]] += 1;
-    pr.ms[pr.kind[s]] += ms;
-    pr.total_bytes[pr.kind[s]] += pr.bytes[s];
-  }
-  pr.used = 0;
-}
-
 // ---------------------------------------------------------------- V-cycle --
 template <typename T>
 struct VTypes;
@@ -474,7 +431,7 @@ void cycle_level(amg_hierarchy *h, int k, const CycleCtx &cc) {
   const int n = A.n;
   const double bt = sizeof(T), bp = sizeof(TP);
   if (k == h->nlevels - 1) {
-    ProfScope ps(h, AMG_K_COARSE, 8.0 * (double)n * n + 2.0 * bt * n);
+    ProfScope ps(h->mem.stream, AMG_K_COARSE, 8.0 * (double)n * n + 2.0 * bt * n);
     const int th = std::min(1024, std::max(32, (n + 31) / 32 * 32));
     k_coarse_solve<T><<<1, th, sizeof(double) * n, s>>>(n, h->L, vec<T>(L.y), vec<T>(L.z), cc.done);
     AMG_CHECK_LAUNCH();
@@ -487,13 +444,13 @@ void cycle_level(amg_hierarchy *h, int k, const CycleCtx &cc) {
   const double abytes = (idx_bytes + bt) * (double)A.nnz + 4.0 * (n + 1);
   // extra pre-smoothing sweeps (nu1 > 1): s <- s + wd (y - A s)
   for (int it = 1; it < prm.nu1; ++it) {
-    ProfScope ps(h, AMG_K_OTHER, abytes + 4.0 * bt * n);
+    ProfScope ps(h->mem.stream, AMG_K_SOLVE_OTHER, abytes + 4.0 * bt * n);
     k_jacobi<T><<<grid_for(n), TPB, 0, s>>>(n, A.rp, A.ci, a, wd, y, sv, w, cc.done);
     AMG_CHECK_LAUNCH();
     std::swap(sv, w);
   }
   {
-    ProfScope ps(h, AMG_K_SMOOTH_RESID, abytes + 3.0 * bt * n);
+    ProfScope ps(h->mem.stream, AMG_K_SMOOTH_RESID, abytes + 3.0 * bt * n);
     k_smooth_resid<T><<<grid_for(n), TPB, 0, s>>>(n, A.rp, A.ci, a, y, sv, r, cc.done);
     AMG_CHECK_LAUNCH();
   }
@@ -502,7 +459,7 @@ void cycle_level(amg_hierarchy *h, int k, const CycleCtx &cc) {
   const bool c_last = (k + 1 == h->nlevels - 1);
   {
     const DCsr &R = L.R;
-    ProfScope ps(h, AMG_K_RESTRICT, (idx_bytes + bp) * (double)R.nnz + 4.0 * (nc + 1) + bt * n + bt * nc +
+    ProfScope ps(h->mem.stream, AMG_K_RESTRICT, (idx_bytes + bp) * (double)R.nnz + 4.0 * (nc + 1) + bt * n + bt * nc +
                                         (c_last ? 0.0 : 2.0 * bt * nc));
     k_restrict<T, TP><<<grid_for(nc), TPB, 0, s>>>(nc, R.rp, R.ci, pr_vals<T, TP>(R), r, vec<T>(C.y),
                                                    c_last ? nullptr : VTypes<T>::wd(C), vec<T>(C.s),
@@ -512,7 +469,7 @@ void cycle_level(amg_hierarchy *h, int k, const CycleCtx &cc) {
   cycle_level<T, TP>(h, k + 1, cc);
   {
     const DCsr &P = L.P;
-    ProfScope ps(h, AMG_K_PROLONG, (idx_bytes + bp) * (double)P.nnz + 4.0 * (n + 1) + 2.0 * bt * n + bt * nc);
+    ProfScope ps(h->mem.stream, AMG_K_PROLONG, (idx_bytes + bp) * (double)P.nnz + 4.0 * (n + 1) + 2.0 * bt * n + bt * nc);
     k_prolong<T, TP><<<grid_for(n), TPB, 0, s>>>(n, P.rp, P.ci, pr_vals<T, TP>(P), sv, vec<T>(C.z), r, cc.done);
     AMG_CHECK_LAUNCH();
   }
@@ -520,14 +477,14 @@ void cycle_level(amg_hierarchy *h, int k, const CycleCtx &cc) {
   // post-smoothing: nu2 sweeps from t (in r)
   T *t = r;
   if (prm.nu2 == 0) {
-    ProfScope ps(h, AMG_K_OTHER, 2.0 * bt * n);
+    ProfScope ps(h->mem.stream, AMG_K_SOLVE_OTHER, 2.0 * bt * n);
     k_copy<T><<<grid_for(n), TPB, 0, s>>>(n, t, vec<T>(L.z));
     AMG_CHECK_LAUNCH();
     return;
   }
   for (int it = 0; it < prm.nu2; ++it) {
     T *dst = (it == prm.nu2 - 1) ? vec<T>(L.z) : (t == r ? w : r);
-    ProfScope ps(h, it == prm.nu2 - 1 ? AMG_K_SMOOTH_POST : AMG_K_OTHER, abytes + 4.0 * bt * n);
+    ProfScope ps(h->mem.stream, it == prm.nu2 - 1 ? AMG_K_SMOOTH_POST : AMG_K_SOLVE_OTHER, abytes + 4.0 * bt * n);
     k_jacobi<T><<<grid_for(n), TPB, 0, s>>>(n, A.rp, A.ci, a, wd, y, t, dst, cc.done);
     AMG_CHECK_LAUNCH();
     t = dst;
@@ -546,7 +503,7 @@ void vcycle(amg_hierarchy *h, double *z, const CycleCtx &cc) {
   const T *t;
   bool sweep = true;
   if (h->nlevels == 1) {
-    ProfScope ps(h, AMG_K_COARSE, 8.0 * (double)n * n + 2.0 * bt * n);
+    ProfScope ps(h->mem.stream, AMG_K_COARSE, 8.0 * (double)n * n + 2.0 * bt * n);
     const int th = std::min(1024, std::max(32, (n + 31) / 32 * 32));
     k_coarse_solve<T><<<1, th, sizeof(double) * n, s>>>(n, h->L, y, vec<T>(L0.z), cc.done);
     AMG_CHECK_LAUNCH();
@@ -559,7 +516,7 @@ void vcycle(amg_hierarchy *h, double *z, const CycleCtx &cc) {
     const T *wd = VTypes<T>::wd(L0);
     const double abytes = (idx_bytes + bt) * (double)L0.A.nnz + 4.0 * (n + 1);
     for (int it = 0; it + 1 < h->prm.nu2; ++it) {  // all but the last post sweep
-      ProfScope ps(h, AMG_K_OTHER, abytes + 4.0 * bt * n);
+      ProfScope ps(h->mem.stream, AMG_K_SOLVE_OTHER, abytes + 4.0 * bt * n);
       k_jacobi<T><<<grid_for(n), TPB, 0, s>>>(n, L0.A.rp, L0.A.ci, a, wd, y, tt, w, cc.done);
       AMG_CHECK_LAUNCH();
       std::swap(tt, w);
@@ -572,7 +529,7 @@ void vcycle(amg_hierarchy *h, double *z, const CycleCtx &cc) {
   double bytes = 8.0 * n + bt * n;  // z (FP64) write, t read
   if (sweep) bytes += (idx_bytes + bt) * (double)L0.A.nnz + 4.0 * (n + 1) + 2.0 * bt * n;
   if (cc.mode != POST_APPLY) bytes += 8.0 * n + (cc.mode == POST_FIRST ? 8.0 * n : (cc.flexible ? 8.0 * n : 0.0));
-  ProfScope ps(h, AMG_K_SMOOTH_POST, bytes);
+  ProfScope ps(h->mem.stream, AMG_K_SMOOTH_POST, bytes);
   if (sweep)
     k_post0<T, true><<<grid_for(n), TPB, 0, s>>>(n, L0.A.rp, L0.A.ci, a, wd, y, t, z, h->r, h->q, h->p, cc.mode,
                                                  cc.flexible, h->sc, cc.done, h->partials, h->counter);
@@ -615,7 +572,7 @@ int pcg_impl(amg_hierarchy *h, const double *b, double *x, double rtol, int maxi
   // y0 aliases r in FP64 mode
   T *y0 = vec<T>(L0.y);
   {
-    ProfScope ps(h, AMG_K_OTHER, (12.0) * A.nnz + 4.0 * (n + 1) + 8.0 * 3 * n + (fp64 ? 0 : bt * n) + 2 * bt * n);
+    ProfScope ps(h->mem.stream, AMG_K_SOLVE_OTHER, (12.0) * A.nnz + 4.0 * (n + 1) + 8.0 * 3 * n + (fp64 ? 0 : bt * n) + 2 * bt * n);
     k_init<T><<<grid_for(n), TPB, 0, s>>>(n, A.rp, A.ci, A.v, b, x, h->r, VTypes<T>::wd(L0), y0, vec<T>(L0.s),
                                           !fp64, h->prm.nu1 > 0, rtol, h->sc, h->hist, h->partials, h->counter);
     AMG_CHECK_LAUNCH();
@@ -628,12 +585,12 @@ int pcg_impl(amg_hierarchy *h, const double *b, double *x, double rtol, int maxi
   int launched = 0;
   for (int it = 1; it <= maxit; ++it) {
     {
-      ProfScope ps(h, AMG_K_SPMV_DOT, spmv_bytes);
+      ProfScope ps(h->mem.stream, AMG_K_SPMV_DOT, spmv_bytes);
       k_spmv_dot<<<grid_for(n), TPB, 0, s>>>(n, A.rp, A.ci, A.v, h->p, h->q, h->sc, h->partials, h->counter);
       AMG_CHECK_LAUNCH();
     }
     {
-      ProfScope ps(h, AMG_K_PCG_UPDATE, upd_bytes * n);
+      ProfScope ps(h->mem.stream, AMG_K_PCG_UPDATE, upd_bytes * n);
       k_pcg_update<T><<<grid_for(n), TPB, 0, s>>>(n, x, h->r, h->p, h->q, VTypes<T>::wd(L0), y0, vec<T>(L0.s), !fp64,
                                                   h->prm.nu1 > 0, h->sc, h->hist, h->hist_cap, h->d_done,
                                                   h->partials, h->counter);
@@ -641,7 +598,7 @@ int pcg_impl(amg_hierarchy *h, const double *b, double *x, double rtol, int maxi
     }
     vcycle<T, TP>(h, h->z, cc);
     {
-      ProfScope ps(h, AMG_K_DIRECTION, 24.0 * n);
+      ProfScope ps(h->mem.stream, AMG_K_DIRECTION, 24.0 * n);
       k_direction<<<grid_for(n), TPB, 0, s>>>(n, h->z, h->p, h->sc);
       AMG_CHECK_LAUNCH();
     }
@@ -656,7 +613,7 @@ int pcg_impl(amg_hierarchy *h, const double *b, double *x, double rtol, int maxi
   PcgScalars out{};
   AMG_CUDA(cudaMemcpyAsync(&out, h->sc, sizeof(out), cudaMemcpyDeviceToHost, s));
   AMG_CUDA(cudaStreamSynchronize(s));
-  prof_collect(h);
+  prof_collect(s);
   if (iters_out) *iters_out = out.iters;
   if (hist_out && hist_cap > 0) {
     const int cnt = std::min(hist_cap, out.iters + 1);
@@ -713,8 +670,11 @@ void prepare_solve(amg_hierarchy *h) {
       L.wd32 = m.get_n<float>(n);
       h->bytes += 4 * (size_t)n;
     }
-    k_make_wd<<<grid_for(n), TPB, 0, s>>>(n, L.A.rp, L.A.ci, L.A.v, h->prm.omega, L.wd, L.wd32);
-    AMG_CHECK_LAUNCH();
+    {
+      ProfScope ps(s, AMG_K_SETUP_OTHER, 4.0 * (n + 1) + 12.0 * L.A.nnz + 12.0 * n);
+      k_make_wd<<<grid_for(n), TPB, 0, s>>>(n, L.A.rp, L.A.ci, L.A.v, h->prm.omega, L.wd, L.wd32);
+      AMG_CHECK_LAUNCH();
+    }
     if (prec != AMG_PREC_FP64) {
       L.A.v32 = m.get_n<float>(std::max<int64_t>(L.A.nnz, 1));
       h->bytes += 4 * (size_t)L.A.nnz;
@@ -761,8 +721,6 @@ void release_solve(amg_hierarchy *h) {
   h->h_done = nullptr;
   for (auto &e : h->iter_ev)
     if (e) cudaEventDestroy(e);
-  for (auto e : h->prof.ev) cudaEventDestroy(e);
-  h->prof.ev.clear();
 }
 
 int pcg_solve(amg_hierarchy *h, const double *b, double *x, double rtol, int maxit, int *iters, double *hist,
@@ -780,12 +738,12 @@ void vcycle_apply(amg_hierarchy *h, const double *y, double *z) {
     case AMG_PREC_FP32: vcycle_apply_impl<float, float>(h, y, z); break;
     default: vcycle_apply_impl<float, __nv_bfloat16>(h, y, z); break;
   }
-  prof_collect(h);
+  prof_collect(h->mem.stream);
 }
 
 void spmv_level(amg_hierarchy *h, int level, const double *x, double *y) {
   const DCsr &A = h->lev[level].A;
-  ProfScope ps(h, AMG_K_OTHER, 12.0 * A.nnz + 4.0 * (A.n + 1) + 16.0 * A.n);
+  ProfScope ps(h->mem.stream, AMG_K_SOLVE_OTHER, 12.0 * A.nnz + 4.0 * (A.n + 1) + 16.0 * A.n);
   k_spmv64<<<grid_for(A.n), TPB, 0, h->mem.stream>>>(A.n, A.rp, A.ci, A.v, x, y);
   AMG_CHECK_LAUNCH();
 }

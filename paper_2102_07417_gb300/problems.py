@@ -183,6 +183,36 @@ def graph_laplacian_spd(n: int, deg: int, shift: float, seed: int) -> CSR:
     return dense_to_csr(d, {"kind": "graph_laplacian", "seed": seed})
 
 
+def graph_with_hubs(n: int, deg: int, hubs: int, hub_deg: int, shift: float, seed: int) -> CSR:
+    """Random weighted graph Laplacian plus shift * I with a few high-degree hub
+    nodes (long rows, wide Galerkin products)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m = n * deg // 2
+    a = list(rng.integers(0, n, size=m))
+    b = list(rng.integers(0, n, size=m))
+    for h in range(hubs):
+        nb = rng.choice(n, size=hub_deg, replace=False)
+        a += [h] * hub_deg
+        b += list(nb)
+    a, b = np.array(a), np.array(b)
+    keep = a != b
+    a, b = a[keep], b[keep]
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    key = np.unique(lo.astype(np.int64) * n + hi)
+    lo, hi = key // n, key % n
+    w = rng.uniform(0.5, 1.5, size=lo.size)
+    rows = np.concatenate([lo, hi, np.arange(n)])
+    cols = np.concatenate([hi, lo, np.arange(n)])
+    deg_w = np.bincount(lo, weights=w, minlength=n) + np.bincount(hi, weights=w, minlength=n)
+    vals = np.concatenate([-w, -w, deg_w + shift])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=rowptr[1:])
+    return CSR(n, rowptr.astype(np.int32), cols.astype(np.int32), vals.astype(np.float64),
+               {"kind": "graph_with_hubs", "seed": seed})
+
+
 def dense_to_csr(d: np.ndarray, meta=None) -> CSR:
     n = d.shape[0]
     mask = d != 0.0

@@ -71,6 +71,8 @@ CASES = {
     "diffusion3d_20": lambda: pr.diffusion3d(20, 2.0, 2)[0],
     "graph_laplacian_700": lambda: pr.graph_laplacian_spd(700, 7, 0.05, 3),
     "poisson1d_301": lambda: pr.poisson1d(301),
+    # hub rows give Galerkin rows in every SpGEMM tier (product bounds up to ~10^4)
+    "graph_hubs_6000": lambda: pr.graph_with_hubs(6000, 6, 4, 2500, 0.05, 8),
 }
 
 
