@@ -131,6 +131,35 @@ int amg_vcycle_apply(amg_hierarchy *h, const double *y, double *z, void *stream)
 /* y = A_k x with the FP64 copy of level k's operator; x, y device arrays of n_k doubles. */
 int amg_spmv(amg_hierarchy *h, int32_t level, const double *x, double *y, void *stream);
 
+/* q = A p and (p, q) in one pass, allocating no device memory.  The paper
+ * has no counterpart: this is a library convenience around the CG loop's
+ * fused SpMV + dot product.
+ *
+ * Some callers cannot call cudaMalloc at the point where they need this
+ * product: a process whose device memory is already handed out to another
+ * allocator (a framework's caching pool sized to nearly all of HBM), a
+ * latency-critical loop that must not risk the device-wide synchronisation
+ * cudaMalloc/cudaFree can cause, or code that must not fail with "out of
+ * memory" halfway through an iteration.  This entry point takes every input
+ * and output from the caller and keeps its only scratch (per-block partial
+ * sums and a ticket counter, 16 KiB + 256 B) in a fixed array inside the
+ * library that each device holds from the moment the library's device code is
+ * loaded until the process exits.
+ *
+ * A as CSR (rowptr[n+1], colidx[nnz], val[nnz]) and p[n], q[n], pq[1] are
+ * device pointers on the current device; q receives A p and *pq receives
+ * (p, A p), both FP64, stream-ordered on `stream` (nothing is synchronised).
+ * Limit: n <= 16,777,216 rows (the scratch holds 2048 block partials of 8192
+ * rows each); larger n returns AMG_ERR_UNSUPPORTED before any GPU work.
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the scratch array and it keeps the previous
+ * call's contents; the ticket is cleared at the start of each call, but calls
+ * that overlap on the GPU (e.g. on two streams at once) race on it and give
+ * wrong results: serialise them. */
+int amg_spmv_dot_noalloc(int32_t n, int32_t nnz, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                         const double *p, double *q, double *pq, void *stream);
+
 /* Result of a one-call solve. */
 typedef struct {
   int32_t iters;

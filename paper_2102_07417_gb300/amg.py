@@ -36,7 +36,8 @@ SETUP_KERNELS = KERNEL_NAMES[9:]
 # Names exported by the C ABI (each declared in include/amg.h).
 EXPORTS = ["amg_params_default", "amg_setup", "amg_pcg_solve", "amg_vcycle_apply", "amg_spmv", "amg_solve",
            "amg_hierarchy_info", "amg_hierarchy_export", "amg_hierarchy_bytes", "amg_free", "amg_profile_enable",
-           "amg_profile_read", "amg_launch_count", "amg_status_string", "amg_last_error"]
+           "amg_profile_read", "amg_launch_count", "amg_status_string", "amg_last_error",
+           "amg_spmv_dot_noalloc"]
 
 
 class AmgError(RuntimeError):
