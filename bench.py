@@ -80,17 +80,18 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_for(kernel_class: str):
-    """DRAM bytes per launch of a kernel class from the committed ncu summary, if
-    it was captured on the current kernel source (else None)."""
+def traffic_for(kernel_class: str, level):
+    """DRAM bytes per launch of a kernel class (on a level) from the committed ncu
+    summary, if it was captured on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.md")
     if not os.path.exists(path):
         return None
     src = os.path.join(ROOT, "paper_2102_07417_gb300", "csrc", "solve.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    want = f"{kernel_class}@{level}" if level is not None else kernel_class
     for line in open(path):
-        m = re.match(r"^\|\s*`?(\w+)`?\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]{16})\s*\|", line)
-        if m and m.group(1) == kernel_class and m.group(3) == sha:
+        m = re.match(r"^\|\s*`?([\w@]+)`?\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]{16})\s*\|", line)
+        if m and m.group(1) == want and m.group(3) == sha:
             return float(m.group(2))
     return None
 
@@ -275,13 +276,24 @@ def run_gpu(args, rank, world, dist):
     if p.xstar is not None:
         x_err = float(np.linalg.norm(x_dev.cpu().numpy() - p.xstar) / np.linalg.norm(p.xstar))
 
-    # roofline of the dominant kernel class (largest summed event time in the timed region)
+    # roofline of the dominant kernel: the (kernel class, level) pair with the
+    # largest summed event time in the timed region
     peak, peak_src = peaks()
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    d = prof[dom]
+    nlev = rec["info"]["nlevels"]
+    per_level = {lv: amg.profile_read(lv) for lv in range(nlev)}
+    cands = [(d["ms"], name, lv) for lv, pl in per_level.items() for name, d in pl.items() if d["launches"]]
+    for name, d in prof.items():  # launches outside any level (set-up kernels)
+        rest_ms = d["ms"] - sum(per_level[lv][name]["ms"] for lv in per_level)
+        if rest_ms > 1e-9:
+            cands.append((rest_ms, name, None))
+    _, dom, dom_lv = max(cands)
+    if dom_lv is None:
+        d = {k: prof[dom][k] - sum(per_level[lv][dom][k] for lv in per_level) for k in ("launches", "ms", "bytes")}
+    else:
+        d = per_level[dom_lv][dom]
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-    tr = traffic_for(dom)
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+    tr = traffic_for(dom, dom_lv)
+    roof = {"bound": "hbm", "kernel": dom, "level": dom_lv, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
             "avg_launch_us": d["ms"] * 1e3 / max(d["launches"], 1),
             "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
@@ -291,6 +303,10 @@ def run_gpu(args, rank, world, dist):
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                    "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                for k, v in prof.items() if v["launches"]}
+    by_level = {lv: {k: {"ms_per_step": round(v["ms"] / args.steps, 4),
+                         "gbs": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None}
+                     for k, v in pl.items() if v["launches"]}
+                for lv, pl in per_level.items()}
 
     # end to end through the public one-call API with host buffers (H2D / D2H inside)
     e2e = None
@@ -338,7 +354,7 @@ def run_gpu(args, rank, world, dist):
         "roofline": roof,
         "vcycle_hbm": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s", "peak": peak,
                        "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None},
-        "kernels": kernels,
+        "kernels": kernels, "kernels_by_level": by_level,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
     print(json.dumps(out), flush=True)

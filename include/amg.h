@@ -199,11 +199,12 @@ void amg_free(amg_hierarchy *h);
 /* Per-kernel timing with CUDA events on each launch's stream (process-wide,
  * not thread-safe).  amg_profile_enable(1) clears the totals and starts
  * recording every libamg kernel launch; amg_profile_enable(0) stops.
- * amg_profile_read(kernel, &launches, &ms, &bytes) returns, for kernel class
- * `kernel` (AMG_K_*), the number of launches, their summed event-timed
- * duration and the algorithmic bytes they move (int32 indices, values and
- * vectors counted once per launch; the accounting behind the roofline).
- * Totals include every call that has returned. */
+ * amg_profile_read(kernel, level, &launches, &ms, &bytes) returns, for kernel
+ * class `kernel` (AMG_K_*) on hierarchy level `level` (-1: all levels and
+ * launches that belong to none), the number of launches, their summed
+ * event-timed duration and the algorithmic bytes they move (int32 indices,
+ * values and vectors counted once per launch; the accounting behind the
+ * roofline).  Totals include every call that has returned. */
 #define AMG_K_SPMV_DOT 0      /* PCG: q = A p and (p, q) */
 #define AMG_K_PCG_UPDATE 1    /* PCG: x += alpha p, r -= alpha q, ||r||, smoother input */
 #define AMG_K_SMOOTH_RESID 2  /* V-cycle: r_k = y_k - A_k s_k (pre-smoothed residual) */
@@ -221,7 +222,7 @@ void amg_free(amg_hierarchy *h);
 #define AMG_K_SETUP_OTHER 14  /* set-up: scans, dense factor, casts, diagonal */
 #define AMG_K_COUNT 15
 int amg_profile_enable(int32_t on);
-int amg_profile_read(int32_t kernel, int64_t *launches, double *ms, double *bytes);
+int amg_profile_read(int32_t kernel, int32_t level, int64_t *launches, double *ms, double *bytes);
 
 /* Number of libamg kernel launches in this process so far. */
 int64_t amg_launch_count(void);

@@ -103,7 +103,7 @@ def load(build_if_missing: bool = True):
     L.amg_free.argtypes = [vp]
     L.amg_free.restype = None
     L.amg_profile_enable.argtypes = [i32]
-    L.amg_profile_read.argtypes = [i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]
+    L.amg_profile_read.argtypes = [i32, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]
     L.amg_launch_count.argtypes = []
     L.amg_launch_count.restype = C.c_int64
     L.amg_status_string.argtypes = [C.c_int]
@@ -276,12 +276,12 @@ def profile(on: bool):
     check(load().amg_profile_enable(1 if on else 0), "amg_profile_enable")
 
 
-def profile_read() -> dict:
-    """Per kernel class: launches, summed event time (ms) and algorithmic bytes."""
+def profile_read(level: int = -1) -> dict:
+    """Per kernel class (on one level, or all with -1): launches, summed event time (ms), algorithmic bytes."""
     out = {}
     for k, name in enumerate(KERNEL_NAMES):
         n, ms, by = C.c_int64(), C.c_double(), C.c_double()
-        check(load().amg_profile_read(k, C.byref(n), C.byref(ms), C.byref(by)), "amg_profile_read")
+        check(load().amg_profile_read(k, level, C.byref(n), C.byref(ms), C.byref(by)), "amg_profile_read")
         out[name] = {"launches": n.value, "ms": ms.value, "bytes": by.value}
     return out
 

@@ -88,6 +88,28 @@ struct Buf {
   }
 };
 
+// Row-to-lane mapping of the solve kernels: G lanes per row, transposed or vector form.
+struct RowMap {
+  int g = 1;
+  bool tr = true;
+};
+
+// Sliced-ELLPACK copy of a CSR matrix for the solve kernels: slices of 32
+// rows stored column-major (entry k of the slice's lane l at off[s] + 32 k + l),
+// padded with value 0 at a column the row already uses; rows optionally permuted (sorted by length, longest
+// first, within windows of 256 rows) so that a slice's rows have similar
+// lengths and a warp issues one FMA per stored entry, not per padded one.
+struct Sell {
+  int nslices = 0;
+  int64_t nent = 0;
+  int *off = nullptr;             // [nslices + 1] entry offsets (multiples of 32)
+  int *col = nullptr;             // [nent]
+  double *v = nullptr;            // [nent] FP64 values (when needed)
+  float *v32 = nullptr;           // FP32 values (FP32 modes)
+  __nv_bfloat16 *v16 = nullptr;   // BF16 values (P and R in the BF16 ablation)
+  int *perm = nullptr;            // [n] row held by each slot; nullptr = identity
+};
+
 // CSR matrix on the device (int32 indices).  Value arrays for each storage type.
 struct DCsr {
   int n = 0, ncols = 0;
@@ -96,6 +118,10 @@ struct DCsr {
   double *v = nullptr;           // FP64 master copy
   float *v32 = nullptr;          // FP32 copy (FP32 modes)
   __nv_bfloat16 *v16 = nullptr;  // BF16 copy (P and R in the BF16 ablation)
+  RowMap map;    // solve kernels in the V-cycle precision
+  RowMap map64;  // FP64 products with this matrix
+  bool use_sell = false;  // solve kernels read `sell` instead of the CSR arrays
+  Sell sell;
 };
 
 // Scalars of one PCG solve, resident on the device.
@@ -122,16 +148,17 @@ struct Level {
   void *y = nullptr, *s = nullptr, *r = nullptr, *z = nullptr, *w = nullptr;
 };
 
-// Process-wide per-launch event timing (amg_profile_enable).
+// Process-wide per-launch event timing (amg_profile_enable), per kernel class
+// and hierarchy level (index kMaxLevels: launches that belong to no level).
 struct Profile {
   bool on = false;
   std::vector<cudaEvent_t> ev;  // pool of events, two per recorded launch
-  std::vector<int> kind;        // kernel class of each recorded pair
+  std::vector<int> kind;        // kernel class * (kMaxLevels + 1) + level slot of each pair
   std::vector<double> bytes;    // algorithmic bytes of each recorded pair
   size_t used = 0;
-  int64_t launches[AMG_K_COUNT] = {};
-  double ms[AMG_K_COUNT] = {};
-  double total_bytes[AMG_K_COUNT] = {};
+  int64_t launches[AMG_K_COUNT][kMaxLevels + 1] = {};
+  double ms[AMG_K_COUNT][kMaxLevels + 1] = {};
+  double total_bytes[AMG_K_COUNT][kMaxLevels + 1] = {};
 };
 extern Profile g_prof;
 
@@ -139,7 +166,7 @@ extern Profile g_prof;
 struct ProfScope {
   size_t slot = (size_t)-1;
   cudaStream_t stream;
-  ProfScope(cudaStream_t s, int kind, double bytes);
+  ProfScope(cudaStream_t s, int kind, double bytes, int level = -1);
   ~ProfScope();
 };
 // Folds recorded event pairs into the totals; synchronises `s` first.
@@ -152,7 +179,8 @@ struct amg_hierarchy {
   amg_params prm{};
   int nlevels = 0;
   amg::Level lev[amg::kMaxLevels];
-  double *L = nullptr;  // dense Cholesky factor of the last level (row-major, lower)
+  double *L = nullptr;     // dense Cholesky factor of the last level (row-major, lower)
+  double *Linv = nullptr;  // its inverse (row-major, lower)
   int nL = 0;
   // PCG vectors (level 0, FP64)
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;

@@ -16,7 +16,7 @@ static thread_local char g_err[512] = "";
 std::atomic<long long> g_launches{0};
 Profile g_prof;
 
-ProfScope::ProfScope(cudaStream_t s, int kind, double bytes) : stream(s) {
+ProfScope::ProfScope(cudaStream_t s, int kind, double bytes, int level) : stream(s) {
   Profile &pr = g_prof;
   if (!pr.on) return;
   if (pr.used * 2 + 2 > pr.ev.size()) {
@@ -32,7 +32,7 @@ ProfScope::ProfScope(cudaStream_t s, int kind, double bytes) : stream(s) {
     pr.kind.resize(pr.used);
     pr.bytes.resize(pr.used);
   }
-  pr.kind[slot] = kind;
+  pr.kind[slot] = kind * (kMaxLevels + 1) + ((level >= 0 && level < kMaxLevels) ? level : kMaxLevels);
   pr.bytes[slot] = bytes;
   AMG_CUDA(cudaEventRecord(pr.ev[2 * slot], s));
 }
@@ -49,9 +49,10 @@ void prof_collect(cudaStream_t s) {
     float ms = 0.f;
     AMG_CUDA(cudaEventSynchronize(pr.ev[2 * k + 1]));
     AMG_CUDA(cudaEventElapsedTime(&ms, pr.ev[2 * k], pr.ev[2 * k + 1]));
-    pr.launches[pr.kind[k]] += 1;
-    pr.ms[pr.kind[k]] += ms;
-    pr.total_bytes[pr.kind[k]] += pr.bytes[k];
+    const int kind = pr.kind[k] / (kMaxLevels + 1), lvl = pr.kind[k] % (kMaxLevels + 1);
+    pr.launches[kind][lvl] += 1;
+    pr.ms[kind][lvl] += ms;
+    pr.total_bytes[kind][lvl] += pr.bytes[k];
   }
   pr.used = 0;
 }
@@ -336,22 +337,32 @@ int amg_profile_enable(int32_t on) {
   amg::Profile &pr = amg::g_prof;
   pr.on = on != 0;
   if (on) {
-    for (int k = 0; k < AMG_K_COUNT; ++k) {
-      pr.launches[k] = 0;
-      pr.ms[k] = 0.0;
-      pr.total_bytes[k] = 0.0;
-    }
+    for (int k = 0; k < AMG_K_COUNT; ++k)
+      for (int l = 0; l <= amg::kMaxLevels; ++l) {
+        pr.launches[k][l] = 0;
+        pr.ms[k][l] = 0.0;
+        pr.total_bytes[k][l] = 0.0;
+      }
     pr.used = 0;
   }
   return AMG_OK;
 }
 
-int amg_profile_read(int32_t kernel, int64_t *launches, double *ms, double *bytes) {
+int amg_profile_read(int32_t kernel, int32_t level, int64_t *launches, double *ms, double *bytes) {
   if (kernel < 0 || kernel >= AMG_K_COUNT) return bad("kernel class out of range");
+  if (level < -1 || level >= amg::kMaxLevels) return bad("level out of range");
   const amg::Profile &pr = amg::g_prof;
-  if (launches) *launches = pr.launches[kernel];
-  if (ms) *ms = pr.ms[kernel];
-  if (bytes) *bytes = pr.total_bytes[kernel];
+  int64_t n = 0;
+  double t = 0.0, b = 0.0;
+  for (int l = 0; l <= amg::kMaxLevels; ++l) {
+    if (level >= 0 && l != level) continue;
+    n += pr.launches[kernel][l];
+    t += pr.ms[kernel][l];
+    b += pr.total_bytes[kernel][l];
+  }
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  if (bytes) *bytes = b;
   return AMG_OK;
 }
 

@@ -415,6 +415,20 @@ __global__ void k_cholesky(int n, double *M, int *flags) {
   }
 }
 
+// Inverse of the lower Cholesky factor, column by column (thread j solves
+// L x = e_j by forward substitution); the last level's solve then applies
+// L^-1 and L^-T as two dense triangular products.
+__global__ void k_tri_inverse(int n, const double *__restrict__ L, double *__restrict__ Li) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int i = 0; i < j; ++i) Li[(size_t)i * n + j] = 0.0;
+  for (int i = j; i < n; ++i) {
+    double s = (i == j) ? 1.0 : 0.0;
+    for (int k = j; k < i; ++k) s = __dadd_rn(s, -__dmul_rn(L[(size_t)i * n + k], Li[(size_t)k * n + j]));
+    Li[(size_t)i * n + j] = __ddiv_rn(s, L[(size_t)i * n + i]);
+  }
+}
+
 // ------------------------------------------------------------ host side --
 struct Flags {
   int *d = nullptr;
@@ -608,6 +622,12 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       }
       read_flags(m, fl);
       if (fl.h[4]) fail(AMG_ERR_NOT_SPD, "dense Cholesky of the last level met a non-positive pivot");
+      h->Linv = m.get_n<double>((size_t)n * n);
+      {
+        ProfScope ps(s, AMG_K_SETUP_OTHER, 16.0 * (double)n * n);
+        k_tri_inverse<<<ceil_div(n, 64), 64, 0, s>>>(n, h->L, h->Linv);
+        AMG_CHECK_LAUNCH();
+      }
       h->nlevels = k + 1;
       break;
     }

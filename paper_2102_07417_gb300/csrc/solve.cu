@@ -4,22 +4,30 @@
 // V-cycle on level k < L with damped Jacobi (S = I - omega D^-1 A, Eq.
 // smoother) and zero initial guess; wd_k = omega / diag(A_k):
 //   s_k = wd_k .* y_k                 written by whichever kernel produced y_k
-//   r_k = y_k - A_k s_k               k_smooth_resid
-//   y_{k+1} = R_k r_k, s_{k+1}        k_restrict
+//   r_k = y_k - A_k s_k               OpResid
+//   y_{k+1} = R_k r_k, s_{k+1}        OpRestrict
 //   z_{k+1} = V-cycle(y_{k+1})        recursion; z_L = L^-T L^-1 y_L (k_coarse_solve)
-//   t_k = s_k + P_k z_{k+1}           k_prolong  (prolongation + correction)
-//   z_k = t_k + wd_k .* (y_k - A_k t_k)   k_smooth_post (level 0: fused with the CG dots)
-// nu1 > 1 or nu2 > 1 adds plain Jacobi sweeps (k_jacobi); nu = 0 drops them.
+//   t_k = s_k + P_k z_{k+1}           OpProlong  (prolongation + correction)
+//   z_k = t_k + wd_k .* (y_k - A_k t_k)   OpJacobi (level 0: OpPost0, fused with the CG dots)
+// nu1 > 1 or nu2 > 1 adds plain Jacobi sweeps; nu = 0 drops them.
 //
-// Every kernel is HBM-bound sparse or vector work: thread-per-row CSR with
-// one FMA per nonzero (FP64 throughput on this part is ~1.2 TFLOP/s, so the
-// FP64 kernels spend exactly one DFMA per stored entry), grid-stride loops
-// over a grid sized in multiples of the SM count, and dot products reduced
-// per block with warp shuffles and finished by the last block to arrive
-// (one grid-level reduction, deterministic order).
+// FP64 arithmetic on this part runs at ~1.2 TFLOP/s (about 2 DFMA lanes per
+// clock per SM), so FP64 issue slots, not HBM bandwidth, bind the FP64 solve:
+// one DFMA per stored entry already needs most of the FP64 pipe at full
+// bandwidth.  Every sparse kernel is one row "op" (residual, restriction,
+// prolongation, smoothing, CG product) run by one of two row kernels:
+//   k_sell  -- matrices with >= 32768 rows, stored additionally in sliced
+//              ELLPACK (32-row slices, column-major, rows length-sorted within
+//              256-row windows when that cuts padding): a lane per row, fully
+//              coalesced loads, one FMA issued per stored slot, and residuals
+//              y - A x folded into the FMA chain;
+//   k_rows  -- smaller CSR matrices, G lanes per row (latency-bound levels).
+// Dot products are reduced per block with warp shuffles and finished by the
+// last block to arrive (one grid-level reduction, fixed order, deterministic).
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <type_traits>
 
@@ -31,6 +39,7 @@ namespace {
 
 constexpr int TPB = 256;
 constexpr int MAX_GRID = kNumSMs * 8;
+constexpr unsigned FULL = 0xffffffffu;
 
 template <typename T>
 __device__ __forceinline__ T ld(const T *p) {
@@ -40,28 +49,23 @@ __device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(
 __device__ __forceinline__ float tof(float v) { return v; }
 __device__ __forceinline__ double tof(double v) { return v; }
 
-template <typename TP, typename T>
-__device__ __forceinline__ T cvt(TP v) {
-  return static_cast<T>(tof(v));
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
   return v;
 }
 
-// Block-reduces up to three partial sums, writes them to partials[3*block+c]
-// and returns true in every thread of the last block to finish, whose
-// out[c] then holds the grid totals (summed in block order).
+// Block-reduces NV partial sums, writes them to partials[3*block+c] and
+// returns true in every thread of the last block to finish, whose out[c] then
+// holds the grid totals (summed in block order).
 template <int NV>
-__device__ bool grid_reduce(double (&v)[NV], double *partials, unsigned int *counter, double (&out)[NV]) {
+__device__ bool grid_reduce(const double (&v)[NV], double *partials, unsigned int *counter, double (&out)[NV]) {
   __shared__ double red[NV][TPB / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < NV; ++c) {
-    double s = warp_sum(v[c]);
+    const double s = warp_sum(v[c]);
     if (lane == 0) red[c][w] = s;
   }
   __syncthreads();
@@ -69,12 +73,11 @@ __device__ bool grid_reduce(double (&v)[NV], double *partials, unsigned int *cou
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
       double s = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[c][k];
+      for (int k = 0; k < TPB / 32; ++k) s += red[c][k];
       partials[3 * blockIdx.x + c] = s;
     }
     __threadfence();
-    const unsigned t = atomicAdd(counter, 1u);
-    last = (t == gridDim.x - 1);
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!last) return false;
@@ -85,86 +88,440 @@ __device__ bool grid_reduce(double (&v)[NV], double *partials, unsigned int *cou
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
 #pragma unroll
     for (int c = 0; c < NV; ++c) acc[c] += __ldcg(&partials[3 * b + c]);
+  __syncthreads();
 #pragma unroll
   for (int c = 0; c < NV; ++c) {
-    double s = warp_sum(acc[c]);
-    __syncthreads();
+    const double s = warp_sum(acc[c]);
     if (lane == 0) red[c][w] = s;
   }
   __syncthreads();
 #pragma unroll
   for (int c = 0; c < NV; ++c) {
     double s = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[c][k];
+    for (int k = 0; k < TPB / 32; ++k) s += red[c][k];
     out[c] = s;
   }
   if (threadIdx.x == 0) *counter = 0u;
   return true;
 }
 
-#define GRID_STRIDE(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
-
-// r = b - A x;  (b, b), (r, r);  V-cycle input y0 / s0.  Sets the tolerance and
-// marks the solve done when ||r_0|| < rtol ||b|| (or b = 0).
-template <typename T>
-__global__ void __launch_bounds__(TPB) k_init(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                              const double *__restrict__ a, const double *__restrict__ b,
-                                              const double *__restrict__ x, double *__restrict__ r,
-                                              const T *__restrict__ wd, T *__restrict__ y0, T *__restrict__ s0,
-                                              bool write_y, bool pre, double rtol, PcgScalars *sc, double *hist,
-                                              double *partials, unsigned int *counter) {
-  double v[2] = {0.0, 0.0};
-  GRID_STRIDE(i, n) {
-    double acc = 0.0;
-    for (int p = rp[i]; p < rp[i + 1]; ++p) acc = fma(ld(a + p), ld(x + ci[p]), acc);
-    const double bi = b[i], ri = bi - acc;
-    r[i] = ri;
-    v[0] = fma(bi, bi, v[0]);
-    v[1] = fma(ri, ri, v[1]);
-    const T yi = static_cast<T>(ri);
-    if (write_y) y0[i] = yi;
-    s0[i] = pre ? wd[i] * yi : T(0);
-  }
-  double tot[2];
-  if (grid_reduce<2>(v, partials, counter, tot) && threadIdx.x == 0) {
-    sc->bb = tot[0];
-    sc->rr = tot[1];
-    sc->tol = rtol * sqrt(tot[0]);
-    const double res = sqrt(tot[1]);
-    hist[0] = res;
-    sc->iters = 0;
-    sc->status = AMG_OK;
-    sc->done = (res < sc->tol || tot[0] == 0.0) ? 1 : 0;
-  }
-}
-
-// q = A p;  alpha = rho / (p, q);  breakdown when (p, q) <= 0 or NaN.
-__global__ void __launch_bounds__(TPB) k_spmv_dot(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                                  const double *__restrict__ a, const double *__restrict__ p,
-                                                  double *__restrict__ q, PcgScalars *sc, double *partials,
-                                                  unsigned int *counter) {
-  if (sc->done) return;
-  double v[1] = {0.0};
-  GRID_STRIDE(i, n) {
-    double acc = 0.0;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) acc = fma(ld(a + k), ld(p + ci[k]), acc);
-    q[i] = acc;
-    v[0] = fma(p[i], acc, v[0]);
-  }
-  double tot[1];
-  if (grid_reduce<1>(v, partials, counter, tot) && threadIdx.x == 0) {
-    sc->pq = tot[0];
-    if (!(tot[0] > 0.0)) {
-      sc->status = AMG_ERR_BREAKDOWN;
-      sc->done = 1;
-    } else {
-      sc->alpha = sc->rho / tot[0];
+// v[r] = this lane's partial sum of row r of its G-row group; returns the
+// full sum of row `sub` of the group.  Each step halves the rows a lane holds
+// (keeping the half its bit selects and adding the partner's copy of that
+// half), so a lane performs G/2 + G/4 + ... + 1 = G-1 additions.
+template <int G, typename T>
+__device__ __forceinline__ T transpose_reduce(T (&v)[G], int sub) {
+#pragma unroll
+  for (int d = G / 2; d >= 1; d >>= 1) {
+    const bool up = (sub & d) != 0;
+#pragma unroll
+    for (int j = 0; j < d; ++j) {
+      const T keep = up ? v[j + d] : v[j];
+      const T send = up ? v[j] : v[j + d];
+      v[j] = keep + __shfl_xor_sync(FULL, send, d);
     }
   }
+  return v[0];
 }
 
-// x += alpha p;  r -= alpha q;  ||r||;  convergence test;  V-cycle input.
+template <int NV>
+struct Acc {
+  double v[NV > 0 ? NV : 1];
+};
+
+// Row kernel on CSR, transposed form (TR = true): a warp takes 32 consecutive
+// rows; a group of G lanes owns G of them, each lane keeping one partial sum
+// per row of its group, then transpose_reduce leaves row base+lane's sum in
+// lane `lane` (G-1 additions per row, coalesced epilogue).  Vector form
+// (TR = false): G lanes per row, one row per group at a time, butterfly
+// reduction; used for levels with few rows, where parallelism matters more
+// than the extra additions.  For each row i: sum_i = sum_p mat(p) vec(ci[p])
+// (when the op has a matrix; ops with kNeg receive init(i) - sum_i), then
+// op.out(i, ., acc); finally op.finish(acc) in every thread.
+template <int G, bool TR, class Op>
+__global__ void __launch_bounds__(TPB) k_rows(int n, const int *__restrict__ rp, const int *__restrict__ ci, Op op) {
+  using T = typename Op::T;
+  constexpr int NA = Op::NV > 0 ? Op::NV : 1;
+  if (op.skip()) return;
+  const int lane = threadIdx.x & 31, sub = lane & (G - 1), grp = lane / G;
+  const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5, nw = (gridDim.x * TPB) >> 5;
+  Acc<NA> acc;
+#pragma unroll
+  for (int c = 0; c < NA; ++c) acc.v[c] = 0.0;
+  if constexpr (TR) {
+    for (int base = gw * 32; base < n; base += nw * 32) {
+      T sum = T(0);
+      if constexpr (Op::kMatrix) {
+        T part[G];
+        const int r0 = base + grp * G;
+#pragma unroll
+        for (int r = 0; r < G; ++r) {
+          part[r] = T(0);
+          const int row = r0 + r;
+          if (row < n) {
+            const int e = rp[row + 1];
+#pragma unroll 4
+            for (int p = rp[row] + sub; p < e; p += G) part[r] = fma(op.mat(p), op.vec(ci[p]), part[r]);
+          }
+        }
+        if constexpr (G == 1) sum = part[0];
+        else sum = transpose_reduce<G>(part, sub);
+      }
+      const int row = base + lane;
+      if (row < n) {
+        if constexpr (Op::kNeg) sum = op.init(row) - sum;
+        op.out(row, sum, acc);
+      }
+    }
+  } else {
+    constexpr int RPW = 32 / G;  // rows per warp step
+    for (int base = gw * RPW; base < n; base += nw * RPW) {
+      const int row = base + grp;
+      T sum = T(0);
+      if constexpr (Op::kMatrix) {
+        if (row < n) {
+          const int e = rp[row + 1];
+#pragma unroll 4
+          for (int p = rp[row] + sub; p < e; p += G) sum = fma(op.mat(p), op.vec(ci[p]), sum);
+        }
+#pragma unroll
+        for (int d = G / 2; d >= 1; d >>= 1) sum += __shfl_xor_sync(FULL, sum, d);
+      }
+      if (row < n && sub == 0) {
+        if constexpr (Op::kNeg) sum = op.init(row) - sum;
+        op.out(row, sum, acc);
+      }
+    }
+  }
+  op.finish(acc);
+}
+
+// Row kernel on the sliced-ELLPACK copy: a warp per 32-row slice, a lane per
+// row, the slice's entries read column-major (each warp load is 32
+// consecutive entries), exactly one FMA issued per stored slot; ops with
+// kNeg start from init(row) and subtract, so y - A x costs no extra add.
+template <class Op>
+__global__ void __launch_bounds__(TPB) k_sell(int n, int nslices, const int *__restrict__ off,
+                                              const int *__restrict__ col, const int *__restrict__ perm, Op op) {
+  using T = typename Op::T;
+  constexpr int NA = Op::NV > 0 ? Op::NV : 1;
+  if (op.skip()) return;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5, nw = (gridDim.x * TPB) >> 5;
+  Acc<NA> acc;
+#pragma unroll
+  for (int c = 0; c < NA; ++c) acc.v[c] = 0.0;
+  for (int s = gw; s < nslices; s += nw) {
+    const int q = s * 32 + lane;
+    const bool valid = q < n;
+    const int row = valid ? (perm ? perm[q] : q) : 0;
+    const int b = off[s] + lane, len = (off[s + 1] - off[s]) >> 5;
+    T sum = (Op::kNeg && valid) ? op.init(row) : T(0);
+#pragma unroll 8
+    for (int k = 0; k < len; ++k) {
+      const int idx = b + 32 * k;
+      const int c = __ldg(col + idx);
+      if constexpr (Op::kNeg) sum = fma(-op.mat(idx), op.vec(c), sum);
+      else sum = fma(op.mat(idx), op.vec(c), sum);
+    }
+    if (valid) op.out(row, sum, acc);
+  }
+  op.finish(acc);
+}
+
+// --------------------------------------------------------- SELL building --
+constexpr int SELL_WIN = 256;  // rows per sorting window
+
+// Maximum row length of each 32-row slice, times 32 (entries of the slice).
+__global__ void k_sell_count(int n, int nslices, const int *__restrict__ rp, const int *__restrict__ perm,
+                             int *__restrict__ cnt) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nslices) return;
+  int mx = 0;
+  for (int l = 0; l < 32; ++l) {
+    const int q = s * 32 + l;
+    if (q >= n) break;
+    const int row = perm ? perm[q] : q;
+    mx = max(mx, rp[row + 1] - rp[row]);
+  }
+  cnt[s] = 32 * mx;
+}
+
+// Sorts each window of SELL_WIN rows by length, longest first (ties by row).
+__global__ void __launch_bounds__(SELL_WIN) k_sell_perm(int n, const int *__restrict__ rp, int *__restrict__ perm) {
+  __shared__ long long key[SELL_WIN];
+  const int t = threadIdx.x, row = blockIdx.x * SELL_WIN + t;
+  key[t] = row < n ? ((long long)(0x7fffffff - (rp[row + 1] - rp[row])) << 32) | (unsigned)row : LLONG_MAX;
+  __syncthreads();
+  for (int k = 2; k <= SELL_WIN; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int u = t ^ j;
+      if (u > t) {
+        const long long a = key[t], b = key[u];
+        if ((a > b) == ((t & k) == 0)) {
+          key[t] = b;
+          key[u] = a;
+        }
+      }
+      __syncthreads();
+    }
+  if (row < n) perm[row] = (int)(key[t] & 0xffffffffLL);
+}
+
+__global__ void k_sell_fill(int n, int nslices, const int *__restrict__ rp, const int *__restrict__ ci,
+                            const double *__restrict__ a, const int *__restrict__ perm, const int *__restrict__ off,
+                            int *__restrict__ col, double *__restrict__ v, float *__restrict__ v32,
+                            __nv_bfloat16 *__restrict__ v16) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = q >> 5, l = q & 31;
+  if (s >= nslices) return;
+  const int row = q < n ? (perm ? perm[q] : q) : -1;
+  const int b = off[s], len = (off[s + 1] - b) >> 5;
+  const int rb = row >= 0 ? rp[row] : 0, rl = row >= 0 ? rp[row + 1] - rb : 0;
+  for (int k = 0; k < len; ++k) {
+    const int idx = b + 32 * k + l;
+    const bool in = k < rl;
+    const double val = in ? a[rb + k] : 0.0;
+    // padding repeats the row's last column (0 for an empty row) with value
+    // 0, so the solve kernels need no branch on padding slots
+    col[idx] = in ? ci[rb + k] : (rl > 0 ? ci[rb + rl - 1] : 0);
+    if (v) v[idx] = val;
+    if (v32) v32[idx] = static_cast<float>(val);
+    if (v16) v16[idx] = __float2bfloat16_rn(static_cast<float>(val));
+  }
+}
+
+// ------------------------------------------------------------------ ops --
+// Each op: T (arithmetic type of the row sums), NV (number of grid-reduced
+// sums), kMatrix, kNeg (the row value is init(i) - sum instead of sum),
+// skip(), mat(p), vec(c), init(i), out(i, value, acc), finish(acc).
+
+// r = b - A x;  (b, b), (r, r);  V-cycle input y0 (FP32 modes) and s0.
+template <typename TV>
+struct OpInit {
+  using T = double;
+  static constexpr int NV = 2;
+  static constexpr bool kMatrix = true, kNeg = true;
+  const double *a, *x, *b;
+  double *r;
+  const TV *wd;
+  TV *y0, *s0;
+  bool write_y, pre;
+  double rtol;
+  PcgScalars *sc;
+  double *hist, *partials;
+  unsigned int *counter;
+  __device__ bool skip() const { return false; }
+  __device__ double mat(int p) const { return ld(a + p); }
+  __device__ double vec(int c) const { return ld(x + c); }
+  __device__ double init(int i) const { return b[i]; }
+  __device__ void out(int i, double ri, Acc<NV> &acc) const {
+    const double bi = b[i];
+    r[i] = ri;
+    acc.v[0] = fma(bi, bi, acc.v[0]);
+    acc.v[1] = fma(ri, ri, acc.v[1]);
+    const TV yi = static_cast<TV>(ri);
+    if (write_y) y0[i] = yi;
+    s0[i] = pre ? wd[i] * yi : TV(0);
+  }
+  __device__ void finish(Acc<NV> &acc) const {
+    double tot[2];
+    if (grid_reduce<2>(acc.v, partials, counter, tot) && threadIdx.x == 0) {
+      sc->bb = tot[0];
+      sc->rr = tot[1];
+      sc->tol = rtol * sqrt(tot[0]);
+      const double res = sqrt(tot[1]);
+      hist[0] = res;
+      sc->iters = 0;
+      sc->status = AMG_OK;
+      sc->done = (res < sc->tol || tot[0] == 0.0) ? 1 : 0;
+    }
+  }
+};
+
+// q = A p;  alpha = rho / (p, q);  breakdown when (p, q) <= 0 or NaN.
+struct OpSpmvDot {
+  using T = double;
+  static constexpr int NV = 1;
+  static constexpr bool kMatrix = true, kNeg = false;
+  const double *a, *p;
+  double *q;
+  PcgScalars *sc;
+  double *partials;
+  unsigned int *counter;
+  __device__ bool skip() const { return sc->done; }
+  __device__ double mat(int k) const { return ld(a + k); }
+  __device__ double vec(int c) const { return ld(p + c); }
+  __device__ double init(int) const { return 0.0; }
+  __device__ void out(int i, double sum, Acc<NV> &acc) const {
+    q[i] = sum;
+    acc.v[0] = fma(p[i], sum, acc.v[0]);
+  }
+  __device__ void finish(Acc<NV> &acc) const {
+    double tot[1];
+    if (grid_reduce<1>(acc.v, partials, counter, tot) && threadIdx.x == 0) {
+      sc->pq = tot[0];
+      if (!(tot[0] > 0.0)) {
+        sc->status = AMG_ERR_BREAKDOWN;
+        sc->done = 1;
+      } else {
+        sc->alpha = sc->rho / tot[0];
+      }
+    }
+  }
+};
+
+// y = A x (FP64, amg_spmv)
+struct OpSpmv {
+  using T = double;
+  static constexpr int NV = 0;
+  static constexpr bool kMatrix = true, kNeg = false;
+  const double *a, *x;
+  double *y;
+  __device__ bool skip() const { return false; }
+  __device__ double mat(int k) const { return ld(a + k); }
+  __device__ double vec(int c) const { return ld(x + c); }
+  __device__ double init(int) const { return 0.0; }
+  __device__ void out(int i, double sum, Acc<1> &) const { y[i] = sum; }
+  __device__ void finish(Acc<1> &) const {}
+};
+
+// r = y - A s
+template <typename TT>
+struct OpResid {
+  using T = TT;
+  static constexpr int NV = 0;
+  static constexpr bool kMatrix = true, kNeg = true;
+  const T *a, *s, *y;
+  T *r;
+  const int *done;
+  __device__ bool skip() const { return *done; }
+  __device__ T mat(int k) const { return ld(a + k); }
+  __device__ T vec(int c) const { return ld(s + c); }
+  __device__ T init(int i) const { return y[i]; }
+  __device__ void out(int i, T res, Acc<1> &) const { r[i] = res; }
+  __device__ void finish(Acc<1> &) const {}
+};
+
+// y_c = R r;  s_c = wd_c .* y_c (pre = 1), 0 (pre = 0), not written (pre = -1)
+template <typename TT, typename TP>
+struct OpRestrict {
+  using T = TT;
+  static constexpr int NV = 0;
+  static constexpr bool kMatrix = true, kNeg = false;
+  const TP *rv;
+  const T *r, *wd;
+  T *yc, *sc;
+  int pre;
+  const int *done;
+  __device__ bool skip() const { return *done; }
+  __device__ T mat(int k) const { return static_cast<T>(tof(rv[k])); }
+  __device__ T vec(int c) const { return ld(r + c); }
+  __device__ T init(int) const { return T(0); }
+  __device__ void out(int i, T sum, Acc<1> &) const {
+    yc[i] = sum;
+    if (pre >= 0) sc[i] = pre ? wd[i] * sum : T(0);
+  }
+  __device__ void finish(Acc<1> &) const {}
+};
+
+// t = s + P z_c
+template <typename TT, typename TP>
+struct OpProlong {
+  using T = TT;
+  static constexpr int NV = 0;
+  static constexpr bool kMatrix = true, kNeg = false;
+  const TP *pv;
+  const T *s, *zc;
+  T *t;
+  const int *done;
+  __device__ bool skip() const { return *done; }
+  __device__ T mat(int k) const { return static_cast<T>(tof(pv[k])); }
+  __device__ T vec(int c) const { return ld(zc + c); }
+  __device__ T init(int) const { return T(0); }
+  __device__ void out(int i, T sum, Acc<1> &) const { t[i] = s[i] + sum; }
+  __device__ void finish(Acc<1> &) const {}
+};
+
+// z = t + wd .* (y - A t)
+template <typename TT>
+struct OpJacobi {
+  using T = TT;
+  static constexpr int NV = 0;
+  static constexpr bool kMatrix = true, kNeg = true;
+  const T *a, *wd, *y, *t;
+  T *z;
+  const int *done;
+  __device__ bool skip() const { return *done; }
+  __device__ T mat(int k) const { return ld(a + k); }
+  __device__ T vec(int c) const { return ld(t + c); }
+  __device__ T init(int i) const { return y[i]; }
+  __device__ void out(int i, T res, Acc<1> &) const { z[i] = fma(wd[i], res, t[i]); }
+  __device__ void finish(Acc<1> &) const {}
+};
+
+enum Post0Mode { POST_APPLY = 0, POST_FIRST = 1, POST_ITER = 2 };
+
+// Level-0 post-smoothing fused with the CG bookkeeping:
+//   z = t + wd .* (y - A t) (SWEEP) or z = t, written in FP64;
+//   APPLY: nothing else; FIRST: rho = (r, z), p = z;
+//   ITER:  beta = (z, r) / rho (standard) or -alpha (z, q) / rho (flexible:
+//          (z_{k+1}, r_{k+1} - r_k) with r_{k+1} - r_k = -alpha q_k), rho = (r, z).
+template <typename TT, bool SWEEP>
+struct OpPost0 {
+  using T = TT;
+  static constexpr int NV = 2;
+  static constexpr bool kMatrix = SWEEP, kNeg = SWEEP;
+  const T *a, *wd, *y, *t;
+  double *z;
+  const double *r, *q;
+  double *p;
+  int mode, flexible;
+  PcgScalars *sc;
+  const int *done;
+  double *partials;
+  unsigned int *counter;
+  __device__ bool skip() const { return *done; }
+  __device__ T mat(int k) const { return ld(a + k); }
+  __device__ T vec(int c) const { return ld(t + c); }
+  __device__ T init(int i) const { return y[i]; }
+  __device__ void out(int i, T res, Acc<NV> &acc) const {
+    const T zi = SWEEP ? fma(wd[i], res, t[i]) : t[i];
+    const double zd = static_cast<double>(zi);
+    z[i] = zd;
+    if (mode != POST_APPLY) {
+      acc.v[0] = fma(r[i], zd, acc.v[0]);
+      if (mode == POST_FIRST) p[i] = zd;
+      else if (flexible) acc.v[1] = fma(zd, q[i], acc.v[1]);
+    }
+  }
+  __device__ void finish(Acc<NV> &acc) const {
+    if (mode == POST_APPLY) return;
+    double tot[2];
+    if (grid_reduce<2>(acc.v, partials, counter, tot) && threadIdx.x == 0) {
+      sc->rz = tot[0];
+      sc->zq = tot[1];
+      if (mode == POST_ITER) sc->beta = flexible ? -sc->alpha * tot[1] / sc->rho : tot[0] / sc->rho;
+      sc->rho = tot[0];
+    }
+  }
+};
+
+// ------------------------------------------------------ streaming kernels --
 template <typename T>
+struct Vec2;
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+
+// x += alpha p;  r -= alpha q;  ||r||;  convergence test;  V-cycle input y0 / s0.
+// VEC: two elements per thread with 16-byte loads (all pointers 16-byte aligned).
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(TPB) k_pcg_update(int n, double *__restrict__ x, double *__restrict__ r,
                                                     const double *__restrict__ p, const double *__restrict__ q,
                                                     const T *__restrict__ wd, T *__restrict__ y0,
@@ -174,7 +531,38 @@ __global__ void __launch_bounds__(TPB) k_pcg_update(int n, double *__restrict__ 
   if (sc->done) return;
   const double alpha = sc->alpha;
   double v[1] = {0.0};
-  GRID_STRIDE(i, n) {
+  if (VEC) {
+    using T2 = typename Vec2<T>::type;
+    const int n2 = n >> 1;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n2; j += gridDim.x * blockDim.x) {
+      double2 xv = reinterpret_cast<double2 *>(x)[j];
+      double2 rv = reinterpret_cast<double2 *>(r)[j];
+      const double2 pv = reinterpret_cast<const double2 *>(p)[j];
+      const double2 qv = reinterpret_cast<const double2 *>(q)[j];
+      xv.x = fma(alpha, pv.x, xv.x);
+      xv.y = fma(alpha, pv.y, xv.y);
+      rv.x = fma(-alpha, qv.x, rv.x);
+      rv.y = fma(-alpha, qv.y, rv.y);
+      reinterpret_cast<double2 *>(x)[j] = xv;
+      reinterpret_cast<double2 *>(r)[j] = rv;
+      v[0] = fma(rv.x, rv.x, v[0]);
+      v[0] = fma(rv.y, rv.y, v[0]);
+      T2 yv, sv;
+      yv.x = static_cast<T>(rv.x);
+      yv.y = static_cast<T>(rv.y);
+      if (write_y) reinterpret_cast<T2 *>(y0)[j] = yv;
+      if (pre) {
+        const T2 w = reinterpret_cast<const T2 *>(wd)[j];
+        sv.x = w.x * yv.x;
+        sv.y = w.y * yv.y;
+      } else {
+        sv.x = sv.y = T(0);
+      }
+      reinterpret_cast<T2 *>(s0)[j] = sv;
+    }
+  }
+  const int start = VEC ? (n & ~1) : 0;
+  for (int i = start + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
@@ -200,146 +588,48 @@ __global__ void __launch_bounds__(TPB) k_pcg_update(int n, double *__restrict__ 
   }
 }
 
-// r = y - A s
-template <typename T>
-__global__ void __launch_bounds__(TPB) k_smooth_resid(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                                      const T *__restrict__ a, const T *__restrict__ y,
-                                                      const T *__restrict__ s, T *__restrict__ r,
-                                                      const int *__restrict__ done) {
-  if (*done) return;
-  GRID_STRIDE(i, n) {
-    T acc = y[i];
-    for (int p = rp[i]; p < rp[i + 1]; ++p) acc = fma(-ld(a + p), ld(s + ci[p]), acc);
-    r[i] = acc;
-  }
-}
-
-// y_c = R r;  s_c = wd_c .* y_c (or 0)
-template <typename T, typename TP>
-__global__ void __launch_bounds__(TPB) k_restrict(int nc, const int *__restrict__ rp, const int *__restrict__ ci,
-                                                  const TP *__restrict__ rv, const T *__restrict__ r,
-                                                  T *__restrict__ yc, const T *__restrict__ wdc, T *__restrict__ sc_,
-                                                  int pre, const int *__restrict__ done) {
-  if (*done) return;
-  GRID_STRIDE(I, nc) {
-    T acc = T(0);
-    for (int p = rp[I]; p < rp[I + 1]; ++p) acc = fma(cvt<TP, T>(rv[p]), ld(r + ci[p]), acc);
-    yc[I] = acc;
-    if (pre >= 0) sc_[I] = pre ? wdc[I] * acc : T(0);
-  }
-}
-
-// t = s + P z_c
-template <typename T, typename TP>
-__global__ void __launch_bounds__(TPB) k_prolong(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                                 const TP *__restrict__ pv, const T *__restrict__ s,
-                                                 const T *__restrict__ zc, T *__restrict__ t,
-                                                 const int *__restrict__ done) {
-  if (*done) return;
-  GRID_STRIDE(i, n) {
-    T acc = s[i];
-    for (int p = rp[i]; p < rp[i + 1]; ++p) acc = fma(cvt<TP, T>(pv[p]), ld(zc + ci[p]), acc);
-    t[i] = acc;
-  }
-}
-
-// z = t + wd .* (y - A t)   (one damped Jacobi step from t)
-template <typename T>
-__global__ void __launch_bounds__(TPB) k_jacobi(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                                const T *__restrict__ a, const T *__restrict__ wd,
-                                                const T *__restrict__ y, const T *__restrict__ t,
-                                                T *__restrict__ z, const int *__restrict__ done) {
-  if (*done) return;
-  GRID_STRIDE(i, n) {
-    T acc = y[i];
-    for (int p = rp[i]; p < rp[i + 1]; ++p) acc = fma(-ld(a + p), ld(t + ci[p]), acc);
-    z[i] = fma(wd[i], acc, t[i]);
-  }
-}
-
-enum Post0Mode { POST_APPLY = 0, POST_FIRST = 1, POST_ITER = 2 };
-
-// Level-0 post-smoothing fused with the CG bookkeeping:
-//   z = t + wd .* (y - A t)  (SWEEP) or z = t, written in FP64;
-//   APPLY: nothing else; FIRST: rho = (r, z), p = z;
-//   ITER:  beta = (z, r) / rho (standard) or -alpha (z, q) / rho (flexible:
-//          (z_{k+1}, r_{k+1} - r_k) with r_{k+1} - r_k = -alpha q_k), rho = (r, z).
-template <typename T, bool SWEEP>
-__global__ void __launch_bounds__(TPB) k_post0(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                               const T *__restrict__ a, const T *__restrict__ wd,
-                                               const T *__restrict__ y, const T *__restrict__ t,
-                                               double *__restrict__ z, const double *__restrict__ r,
-                                               const double *__restrict__ q, double *__restrict__ p, int mode,
-                                               int flexible, PcgScalars *sc, const int *__restrict__ done,
-                                               double *partials, unsigned int *counter) {
-  if (*done) return;
-  double v[2] = {0.0, 0.0};
-  GRID_STRIDE(i, n) {
-    T zi = t[i];
-    if (SWEEP) {
-      T acc = y[i];
-      for (int k = rp[i]; k < rp[i + 1]; ++k) acc = fma(-ld(a + k), ld(t + ci[k]), acc);
-      zi = fma(wd[i], acc, zi);
-    }
-    const double zd = static_cast<double>(zi);
-    z[i] = zd;
-    if (mode != POST_APPLY) {
-      v[0] = fma(r[i], zd, v[0]);
-      if (mode == POST_FIRST) p[i] = zd;
-      else if (flexible) v[1] = fma(zd, q[i], v[1]);
-    }
-  }
-  if (mode == POST_APPLY) return;
-  double tot[2];
-  if (grid_reduce<2>(v, partials, counter, tot) && threadIdx.x == 0) {
-    sc->rz = tot[0];
-    sc->zq = tot[1];
-    if (mode == POST_ITER) sc->beta = flexible ? -sc->alpha * tot[1] / sc->rho : tot[0] / sc->rho;
-    sc->rho = tot[0];
-  }
-}
-
 // p = z + beta p
+template <bool VEC>
 __global__ void __launch_bounds__(TPB) k_direction(int n, const double *__restrict__ z, double *__restrict__ p,
                                                    const PcgScalars *sc) {
   if (sc->done) return;
   const double beta = sc->beta;
-  GRID_STRIDE(i, n) p[i] = fma(beta, p[i], z[i]);
+  if (VEC) {
+    const int n2 = n >> 1;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n2; j += gridDim.x * blockDim.x) {
+      double2 pv = reinterpret_cast<double2 *>(p)[j];
+      const double2 zv = reinterpret_cast<const double2 *>(z)[j];
+      pv.x = fma(beta, pv.x, zv.x);
+      pv.y = fma(beta, pv.y, zv.y);
+      reinterpret_cast<double2 *>(p)[j] = pv;
+    }
+  }
+  const int start = VEC ? (n & ~1) : 0;
+  for (int i = start + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
 }
 
-// z = L^-T L^-1 y on the last level (dense Cholesky factor, one block).
+// z = L^-T (L^-1 y) on the last level, with Li = L^-1 precomputed from the
+// dense Cholesky factor: two triangular matrix-vector products (one block,
+// one row per thread), instead of 2n dependent substitution steps.
 template <typename T>
-__global__ void k_coarse_solve(int n, const double *__restrict__ L, const T *__restrict__ y, T *__restrict__ z,
+__global__ void k_coarse_solve(int n, const double *__restrict__ Li, const T *__restrict__ y, T *__restrict__ z,
                                const int *__restrict__ done) {
   if (*done) return;
-  extern __shared__ double w[];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = static_cast<double>(y[i]);
+  extern __shared__ double sm[];
+  double *yy = sm, *w = sm + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) yy[i] = static_cast<double>(y[i]);
   __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) w[j] = w[j] / L[(size_t)j * n + j];
-    __syncthreads();
-    const double wj = w[j];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) w[i] = fma(-L[(size_t)i * n + j], wj, w[i]);
-    __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j <= i; ++j) s = fma(Li[(size_t)i * n + j], yy[j], s);
+    w[i] = s;
   }
-  for (int j = n - 1; j >= 0; --j) {
-    if (threadIdx.x == 0) w[j] = w[j] / L[(size_t)j * n + j];
-    __syncthreads();
-    const double wj = w[j];
-    for (int i = threadIdx.x; i < j; i += blockDim.x) w[i] = fma(-L[(size_t)j * n + i], wj, w[i]);
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] = static_cast<T>(w[i]);
-}
-
-// y = A x (FP64), for amg_spmv
-__global__ void __launch_bounds__(TPB) k_spmv64(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                                const double *__restrict__ a, const double *__restrict__ x,
-                                                double *__restrict__ y) {
-  GRID_STRIDE(i, n) {
-    double acc = 0.0;
-    for (int p = rp[i]; p < rp[i + 1]; ++p) acc = fma(ld(a + p), ld(x + ci[p]), acc);
-    y[i] = acc;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int k = i; k < n; ++k) s = fma(Li[(size_t)k * n + i], w[k], s);
+    z[i] = static_cast<T>(s);
   }
 }
 
@@ -347,7 +637,7 @@ __global__ void __launch_bounds__(TPB) k_spmv64(int n, const int *__restrict__ r
 template <typename T>
 __global__ void k_load_y0(int n, const double *__restrict__ src, const T *__restrict__ wd, T *__restrict__ y,
                           T *__restrict__ s, bool write_y, bool pre) {
-  GRID_STRIDE(i, n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const T yi = static_cast<T>(src[i]);
     if (write_y) y[i] = yi;
     s[i] = pre ? wd[i] * yi : T(0);
@@ -356,14 +646,14 @@ __global__ void k_load_y0(int n, const double *__restrict__ src, const T *__rest
 
 template <typename T>
 __global__ void k_copy(int n, const T *__restrict__ a, T *__restrict__ b) {
-  GRID_STRIDE(i, n) b[i] = a[i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = a[i];
 }
 
 // wd = omega / a_ii
 __global__ void k_make_wd(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                           const double *__restrict__ a, double omega, double *__restrict__ wd,
                           float *__restrict__ wd32) {
-  GRID_STRIDE(i, n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double d = 1.0;
     for (int p = rp[i]; p < rp[i + 1]; ++p)
       if (ci[p] == i) d = a[p];
@@ -385,19 +675,136 @@ __global__ void k_to_bf16(int64_t n, const double *__restrict__ a, __nv_bfloat16
 
 inline int grid_for(int64_t n) { return std::max(1, std::min<int>(ceil_div(n, TPB), MAX_GRID)); }
 
+// How a CSR matrix's rows are mapped to lanes (see k_rows).
+template <bool TR, class Op>
+void launch_rows_g(int G, int grid, int n, const int *rp, const int *ci, const Op &op, cudaStream_t s) {
+  switch (G) {
+    case 1: k_rows<1, TR, Op><<<grid, TPB, 0, s>>>(n, rp, ci, op); break;
+    case 2: k_rows<2, TR, Op><<<grid, TPB, 0, s>>>(n, rp, ci, op); break;
+    case 4: k_rows<4, TR, Op><<<grid, TPB, 0, s>>>(n, rp, ci, op); break;
+    case 8: k_rows<8, TR, Op><<<grid, TPB, 0, s>>>(n, rp, ci, op); break;
+    case 16: k_rows<16, TR, Op><<<grid, TPB, 0, s>>>(n, rp, ci, op); break;
+    default: k_rows<32, TR, Op><<<grid, TPB, 0, s>>>(n, rp, ci, op); break;
+  }
+}
+
+template <class Op>
+void launch_rows(RowMap map, int n, const int *rp, const int *ci, const Op &op, cudaStream_t s) {
+  if (map.tr || map.g == 1) {
+    launch_rows_g<true>(map.g, grid_for(n), n, rp, ci, op, s);
+  } else {
+    const int64_t lanes = (int64_t)n * map.g;
+    launch_rows_g<false>(map.g, std::max(1, std::min<int>(ceil_div(lanes, TPB), MAX_GRID)), n, rp, ci, op, s);
+  }
+  AMG_CHECK_LAUNCH();
+}
+
+// Runs `op` over the rows of M: the SELL kernel when M has a SELL copy (the
+// op's value pointer must then point into it), else the CSR row kernel.
+template <class Op>
+void launch_mat(const DCsr &M, const RowMap &map, const Op &op, cudaStream_t s) {
+  if (M.use_sell) {
+    const int grid = std::max(1, std::min(ceil_div(M.sell.nslices, TPB / 32), MAX_GRID));
+    k_sell<Op><<<grid, TPB, 0, s>>>(M.n, M.sell.nslices, M.sell.off, M.sell.col, M.sell.perm, op);
+    AMG_CHECK_LAUNCH();
+  } else {
+    launch_rows(map, M.n, M.rp, M.ci, op, s);
+  }
+}
+
+// Lane mapping of a CSR matrix (used below the SELL threshold).  Large FP64
+// matrices: transposed form with G about a quarter of the mean row length
+// (each extra lane costs one FP64 add per row).  Otherwise the vector form
+// with enough lanes per row to put ~2^19 lanes to work (capped by the row
+// length and 32): small coarse levels are latency-bound.
+RowMap choose_map(int64_t nnz, int n, bool fp64) {
+  RowMap m;
+  const double avg = n ? (double)nnz / n : 0.0;
+  if (fp64 && n >= (1 << 18)) {
+    const double want = avg / 4.0;
+    while (m.g < 32 && 2 * m.g <= want) m.g <<= 1;
+    m.tr = true;
+    return m;
+  }
+  int cap = 1;
+  while (cap < 32 && cap < avg) cap <<= 1;
+  int g = 1;
+  while (g < cap && (int64_t)n * g < (1 << 19)) g <<= 1;
+  m.g = g;
+  m.tr = false;
+  return m;
+}
+
+// Matrices with at least this many rows get a SELL copy (thread per row
+// needs enough rows to fill the GPU; smaller ones use the CSR vector form).
+constexpr int kSellMinRows = 1 << 15;
+
+// Builds M's SELL copy with the requested value types.  Rows are permuted
+// (length-sorted within windows) only when that cuts the padding of the
+// identity order by more than 3 %.
+void build_sell(Mem &m, DCsr &M, bool want64, bool want32, bool want16) {
+  cudaStream_t s = m.stream;
+  Sell &S = M.sell;
+  const int n = M.n;
+  S.nslices = ceil_div(n, 32);
+  Buf<int> cnt(m, (size_t)S.nslices + 1);
+  S.off = m.get_n<int>((size_t)S.nslices + 1);
+  {
+    ProfScope ps(s, AMG_K_SETUP_OTHER, 8.0 * n);
+    k_sell_count<<<ceil_div(S.nslices, TPB), TPB, 0, s>>>(n, S.nslices, M.rp, nullptr, cnt.p);
+    AMG_CHECK_LAUNCH();
+  }
+  S.nent = scan_counts(m, cnt.p, S.off, S.nslices);
+  if ((double)S.nent > 1.03 * (double)M.nnz + 32.0) {
+    S.perm = m.get_n<int>(n);
+    ProfScope ps(s, AMG_K_SETUP_OTHER, 16.0 * n);
+    k_sell_perm<<<ceil_div(n, SELL_WIN), SELL_WIN, 0, s>>>(n, M.rp, S.perm);
+    AMG_CHECK_LAUNCH();
+    k_sell_count<<<ceil_div(S.nslices, TPB), TPB, 0, s>>>(n, S.nslices, M.rp, S.perm, cnt.p);
+    AMG_CHECK_LAUNCH();
+    S.nent = scan_counts(m, cnt.p, S.off, S.nslices);
+  }
+  const size_t ne = (size_t)std::max<int64_t>(S.nent, 1);
+  S.col = m.get_n<int>(ne);
+  if (want64) S.v = m.get_n<double>(ne);
+  if (want32) S.v32 = m.get_n<float>(ne);
+  if (want16) S.v16 = m.get_n<__nv_bfloat16>(ne);
+  {
+    ProfScope ps(s, AMG_K_SETUP_OTHER, 4.0 * (n + 1) + 12.0 * M.nnz + 16.0 * S.nent);
+    k_sell_fill<<<ceil_div((int64_t)S.nslices * 32, TPB), TPB, 0, s>>>(n, S.nslices, M.rp, M.ci, M.v, S.perm, S.off,
+                                                                       S.col, S.v, S.v32, S.v16);
+    AMG_CHECK_LAUNCH();
+  }
+  M.use_sell = true;
+}
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 // ---------------------------------------------------------------- V-cycle --
+// Value arrays of A (V-cycle precision or FP64) and of P / R (storage type
+// TP) in whichever layout the solve kernels read.
 template <typename T>
-struct VTypes;
+const T *avals(const DCsr &M);
 template <>
-struct VTypes<double> {
-  static const double *A(const DCsr &m) { return m.v; }
-  static const double *wd(const Level &l) { return l.wd; }
-};
+const double *avals<double>(const DCsr &M) { return M.use_sell ? M.sell.v : M.v; }
 template <>
-struct VTypes<float> {
-  static const float *A(const DCsr &m) { return m.v32; }
-  static const float *wd(const Level &l) { return l.wd32; }
-};
+const float *avals<float>(const DCsr &M) { return M.use_sell ? M.sell.v32 : M.v32; }
+
+template <typename TP>
+const TP *pvals(const DCsr &M);
+template <>
+const double *pvals<double>(const DCsr &M) { return M.use_sell ? M.sell.v : M.v; }
+template <>
+const float *pvals<float>(const DCsr &M) { return M.use_sell ? M.sell.v32 : M.v32; }
+template <>
+const __nv_bfloat16 *pvals<__nv_bfloat16>(const DCsr &M) { return M.use_sell ? M.sell.v16 : M.v16; }
+
+template <typename T>
+const T *wdv(const Level &l);
+template <>
+const double *wdv<double>(const Level &l) { return l.wd; }
+template <>
+const float *wdv<float>(const Level &l) { return l.wd32; }
 
 template <typename T>
 inline T *vec(void *p) {
@@ -405,21 +812,31 @@ inline T *vec(void *p) {
 }
 
 struct CycleCtx {
-  const int *done;   // device flag: when set, every kernel returns at once
-  int mode;          // Post0Mode
+  const int *done;  // device flag: when set, every kernel returns at once
+  int mode;         // Post0Mode
   int flexible;
 };
 
-template <typename T, typename TP>
-const TP *pr_vals(const DCsr &m);
-template <>
-const double *pr_vals<double, double>(const DCsr &m) { return m.v; }
-template <>
-const float *pr_vals<float, float>(const DCsr &m) { return m.v32; }
-template <>
-const __nv_bfloat16 *pr_vals<float, __nv_bfloat16>(const DCsr &m) { return m.v16; }
-
 constexpr double idx_bytes = 4.0;
+
+template <typename T>
+void jacobi_sweep(amg_hierarchy *h, int k, const T *y, const T *t, T *z, const int *done, int kind) {
+  Level &L = h->lev[k];
+  const DCsr &A = L.A;
+  const double bt = sizeof(T);
+  ProfScope ps(h->mem.stream, kind, (idx_bytes + bt) * (double)A.nnz + 4.0 * (A.n + 1) + 4.0 * bt * A.n, k);
+  OpJacobi<T> op{avals<T>(A), wdv<T>(L), y, t, z, done};
+  launch_mat(A, A.map, op, h->mem.stream);
+}
+
+template <typename T>
+void coarse_solve(amg_hierarchy *h, int n, const T *y, T *z, const int *done) {
+  cudaStream_t s = h->mem.stream;
+  ProfScope ps(s, AMG_K_COARSE, 8.0 * (double)n * n + 2.0 * sizeof(T) * n, h->nlevels - 1);
+  const int th = std::min(1024, std::max(32, (n + 31) / 32 * 32));
+  k_coarse_solve<T><<<1, th, 2 * sizeof(double) * n, s>>>(n, h->Linv, y, z, done);
+  AMG_CHECK_LAUNCH();
+}
 
 // Levels k >= 1 (and level 0 up to the prolongation).  On entry y_k and s_k
 // are in place; on exit z_k (k > 0) or t_0 (k = 0, in lev[0].r) is written.
@@ -431,62 +848,50 @@ void cycle_level(amg_hierarchy *h, int k, const CycleCtx &cc) {
   const int n = A.n;
   const double bt = sizeof(T), bp = sizeof(TP);
   if (k == h->nlevels - 1) {
-    ProfScope ps(h->mem.stream, AMG_K_COARSE, 8.0 * (double)n * n + 2.0 * bt * n);
-    const int th = std::min(1024, std::max(32, (n + 31) / 32 * 32));
-    k_coarse_solve<T><<<1, th, sizeof(double) * n, s>>>(n, h->L, vec<T>(L.y), vec<T>(L.z), cc.done);
-    AMG_CHECK_LAUNCH();
+    coarse_solve<T>(h, n, vec<T>(L.y), vec<T>(L.z), cc.done);
     return;
   }
   const amg_params &prm = h->prm;
-  const T *a = VTypes<T>::A(A);
-  const T *wd = VTypes<T>::wd(L);
   T *y = vec<T>(L.y), *sv = vec<T>(L.s), *r = vec<T>(L.r), *w = vec<T>(L.w);
-  const double abytes = (idx_bytes + bt) * (double)A.nnz + 4.0 * (n + 1);
-  // extra pre-smoothing sweeps (nu1 > 1): s <- s + wd (y - A s)
-  for (int it = 1; it < prm.nu1; ++it) {
-    ProfScope ps(h->mem.stream, AMG_K_SOLVE_OTHER, abytes + 4.0 * bt * n);
-    k_jacobi<T><<<grid_for(n), TPB, 0, s>>>(n, A.rp, A.ci, a, wd, y, sv, w, cc.done);
-    AMG_CHECK_LAUNCH();
+  for (int it = 1; it < prm.nu1; ++it) {  // extra pre-smoothing sweeps
+    jacobi_sweep<T>(h, k, y, sv, w, cc.done, AMG_K_SOLVE_OTHER);
     std::swap(sv, w);
   }
   {
-    ProfScope ps(h->mem.stream, AMG_K_SMOOTH_RESID, abytes + 3.0 * bt * n);
-    k_smooth_resid<T><<<grid_for(n), TPB, 0, s>>>(n, A.rp, A.ci, a, y, sv, r, cc.done);
-    AMG_CHECK_LAUNCH();
+    ProfScope ps(s, AMG_K_SMOOTH_RESID, (idx_bytes + bt) * (double)A.nnz + 4.0 * (n + 1) + 3.0 * bt * n, k);
+    OpResid<T> op{avals<T>(A), sv, y, r, cc.done};
+    launch_mat(A, A.map, op, s);
   }
   Level &C = h->lev[k + 1];
   const int nc = C.A.n;
   const bool c_last = (k + 1 == h->nlevels - 1);
   {
     const DCsr &R = L.R;
-    ProfScope ps(h->mem.stream, AMG_K_RESTRICT, (idx_bytes + bp) * (double)R.nnz + 4.0 * (nc + 1) + bt * n + bt * nc +
-                                        (c_last ? 0.0 : 2.0 * bt * nc));
-    k_restrict<T, TP><<<grid_for(nc), TPB, 0, s>>>(nc, R.rp, R.ci, pr_vals<T, TP>(R), r, vec<T>(C.y),
-                                                   c_last ? nullptr : VTypes<T>::wd(C), vec<T>(C.s),
-                                                   c_last ? -1 : (prm.nu1 > 0 ? 1 : 0), cc.done);
-    AMG_CHECK_LAUNCH();
+    ProfScope ps(s, AMG_K_RESTRICT, (idx_bytes + bp) * (double)R.nnz + 4.0 * (nc + 1) + bt * n + bt * nc +
+                                        (c_last ? 0.0 : 2.0 * bt * nc), k);
+    OpRestrict<T, TP> op{pvals<TP>(R), r, c_last ? nullptr : wdv<T>(C), vec<T>(C.y), vec<T>(C.s),
+                         c_last ? -1 : (prm.nu1 > 0 ? 1 : 0), cc.done};
+    launch_mat(R, R.map, op, s);
   }
   cycle_level<T, TP>(h, k + 1, cc);
   {
     const DCsr &P = L.P;
-    ProfScope ps(h->mem.stream, AMG_K_PROLONG, (idx_bytes + bp) * (double)P.nnz + 4.0 * (n + 1) + 2.0 * bt * n + bt * nc);
-    k_prolong<T, TP><<<grid_for(n), TPB, 0, s>>>(n, P.rp, P.ci, pr_vals<T, TP>(P), sv, vec<T>(C.z), r, cc.done);
-    AMG_CHECK_LAUNCH();
+    ProfScope ps(s, AMG_K_PROLONG, (idx_bytes + bp) * (double)P.nnz + 4.0 * (n + 1) + 2.0 * bt * n + bt * nc, k);
+    OpProlong<T, TP> op{pvals<TP>(P), sv, vec<T>(C.z), r, cc.done};
+    launch_mat(P, P.map, op, s);
   }
   if (k == 0) return;  // level 0's post-smoothing is fused with the CG bookkeeping
-  // post-smoothing: nu2 sweeps from t (in r)
   T *t = r;
   if (prm.nu2 == 0) {
-    ProfScope ps(h->mem.stream, AMG_K_SOLVE_OTHER, 2.0 * bt * n);
+    ProfScope ps(s, AMG_K_SOLVE_OTHER, 2.0 * bt * n, k);
     k_copy<T><<<grid_for(n), TPB, 0, s>>>(n, t, vec<T>(L.z));
     AMG_CHECK_LAUNCH();
     return;
   }
   for (int it = 0; it < prm.nu2; ++it) {
-    T *dst = (it == prm.nu2 - 1) ? vec<T>(L.z) : (t == r ? w : r);
-    ProfScope ps(h->mem.stream, it == prm.nu2 - 1 ? AMG_K_SMOOTH_POST : AMG_K_SOLVE_OTHER, abytes + 4.0 * bt * n);
-    k_jacobi<T><<<grid_for(n), TPB, 0, s>>>(n, A.rp, A.ci, a, wd, y, t, dst, cc.done);
-    AMG_CHECK_LAUNCH();
+    const bool lastp = it == prm.nu2 - 1;
+    T *dst = lastp ? vec<T>(L.z) : (t == r ? w : r);
+    jacobi_sweep<T>(h, k, y, t, dst, cc.done, lastp ? AMG_K_SMOOTH_POST : AMG_K_SOLVE_OTHER);
     t = dst;
   }
 }
@@ -497,46 +902,39 @@ template <typename T, typename TP>
 void vcycle(amg_hierarchy *h, double *z, const CycleCtx &cc) {
   cudaStream_t s = h->mem.stream;
   Level &L0 = h->lev[0];
-  const int n = L0.A.n;
+  const DCsr &A = L0.A;
+  const int n = A.n;
   const double bt = sizeof(T);
   const T *y = vec<T>(L0.y);
   const T *t;
   bool sweep = true;
   if (h->nlevels == 1) {
-    ProfScope ps(h->mem.stream, AMG_K_COARSE, 8.0 * (double)n * n + 2.0 * bt * n);
-    const int th = std::min(1024, std::max(32, (n + 31) / 32 * 32));
-    k_coarse_solve<T><<<1, th, sizeof(double) * n, s>>>(n, h->L, y, vec<T>(L0.z), cc.done);
-    AMG_CHECK_LAUNCH();
+    coarse_solve<T>(h, n, y, vec<T>(L0.z), cc.done);
     t = vec<T>(L0.z);
     sweep = false;
   } else {
     cycle_level<T, TP>(h, 0, cc);
     T *tt = vec<T>(L0.r), *w = vec<T>(L0.w);
-    const T *a = VTypes<T>::A(L0.A);
-    const T *wd = VTypes<T>::wd(L0);
-    const double abytes = (idx_bytes + bt) * (double)L0.A.nnz + 4.0 * (n + 1);
     for (int it = 0; it + 1 < h->prm.nu2; ++it) {  // all but the last post sweep
-      ProfScope ps(h->mem.stream, AMG_K_SOLVE_OTHER, abytes + 4.0 * bt * n);
-      k_jacobi<T><<<grid_for(n), TPB, 0, s>>>(n, L0.A.rp, L0.A.ci, a, wd, y, tt, w, cc.done);
-      AMG_CHECK_LAUNCH();
+      jacobi_sweep<T>(h, 0, y, tt, w, cc.done, AMG_K_SOLVE_OTHER);
       std::swap(tt, w);
     }
     t = tt;
     sweep = h->prm.nu2 > 0;
   }
-  const T *a = VTypes<T>::A(L0.A);
-  const T *wd = VTypes<T>::wd(L0);
   double bytes = 8.0 * n + bt * n;  // z (FP64) write, t read
-  if (sweep) bytes += (idx_bytes + bt) * (double)L0.A.nnz + 4.0 * (n + 1) + 2.0 * bt * n;
+  if (sweep) bytes += (idx_bytes + bt) * (double)A.nnz + 4.0 * (n + 1) + 2.0 * bt * n;
   if (cc.mode != POST_APPLY) bytes += 8.0 * n + (cc.mode == POST_FIRST ? 8.0 * n : (cc.flexible ? 8.0 * n : 0.0));
-  ProfScope ps(h->mem.stream, AMG_K_SMOOTH_POST, bytes);
-  if (sweep)
-    k_post0<T, true><<<grid_for(n), TPB, 0, s>>>(n, L0.A.rp, L0.A.ci, a, wd, y, t, z, h->r, h->q, h->p, cc.mode,
-                                                 cc.flexible, h->sc, cc.done, h->partials, h->counter);
-  else
-    k_post0<T, false><<<grid_for(n), TPB, 0, s>>>(n, L0.A.rp, L0.A.ci, a, wd, y, t, z, h->r, h->q, h->p, cc.mode,
-                                                  cc.flexible, h->sc, cc.done, h->partials, h->counter);
-  AMG_CHECK_LAUNCH();
+  ProfScope ps(s, AMG_K_SMOOTH_POST, bytes, 0);
+  if (sweep) {
+    OpPost0<T, true> op{avals<T>(A), wdv<T>(L0), y, t, z, h->r, h->q, h->p, cc.mode, cc.flexible,
+                        h->sc, cc.done, h->partials, h->counter};
+    launch_mat(A, A.map, op, s);
+  } else {
+    OpPost0<T, false> op{nullptr, wdv<T>(L0), y, t, z, h->r, h->q, h->p, cc.mode, cc.flexible,
+                         h->sc, cc.done, h->partials, h->counter};
+    launch_rows(RowMap{}, n, A.rp, A.ci, op, s);
+  }
 }
 
 template <typename T>
@@ -544,8 +942,8 @@ void load_y0(amg_hierarchy *h, const double *src) {
   Level &L0 = h->lev[0];
   const int n = L0.A.n;
   const bool write_y = !std::is_same<T, double>::value || L0.y != (void *)src;
-  k_load_y0<T><<<grid_for(n), TPB, 0, h->mem.stream>>>(n, src, VTypes<T>::wd(L0), vec<T>(L0.y), vec<T>(L0.s),
-                                                        write_y, h->prm.nu1 > 0);
+  k_load_y0<T><<<grid_for(n), TPB, 0, h->mem.stream>>>(n, src, wdv<T>(L0), vec<T>(L0.y), vec<T>(L0.s), write_y,
+                                                        h->prm.nu1 > 0);
   AMG_CHECK_LAUNCH();
 }
 
@@ -569,41 +967,48 @@ int pcg_impl(amg_hierarchy *h, const double *b, double *x, double rtol, int maxi
   AMG_CUDA(cudaMemcpyAsync(h->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   *h->h_done = 0;
   const int *done = &h->sc->done;
-  // y0 aliases r in FP64 mode
-  T *y0 = vec<T>(L0.y);
+  T *y0 = vec<T>(L0.y);  // aliases r in FP64 mode
+  T *s0 = vec<T>(L0.s);
+  const T *wd0 = wdv<T>(L0);
+  const bool pre = h->prm.nu1 > 0;
+  const double *a64 = avals<double>(A);
   {
-    ProfScope ps(h->mem.stream, AMG_K_SOLVE_OTHER, (12.0) * A.nnz + 4.0 * (n + 1) + 8.0 * 3 * n + (fp64 ? 0 : bt * n) + 2 * bt * n);
-    k_init<T><<<grid_for(n), TPB, 0, s>>>(n, A.rp, A.ci, A.v, b, x, h->r, VTypes<T>::wd(L0), y0, vec<T>(L0.s),
-                                          !fp64, h->prm.nu1 > 0, rtol, h->sc, h->hist, h->partials, h->counter);
-    AMG_CHECK_LAUNCH();
+    ProfScope ps(s, AMG_K_SOLVE_OTHER, 12.0 * A.nnz + 4.0 * (n + 1) + 8.0 * 3 * n + (fp64 ? 0 : bt * n) + 2 * bt * n);
+    OpInit<T> op{a64, x, b, h->r, wd0, y0, s0, !fp64, pre, rtol, h->sc, h->hist, h->partials, h->counter};
+    launch_mat(A, A.map64, op, s);
   }
   CycleCtx cc{done, POST_FIRST, flexible};
   vcycle<T, TP>(h, h->z, cc);
   cc.mode = POST_ITER;
   const double spmv_bytes = 12.0 * A.nnz + 4.0 * (n + 1) + 16.0 * n;
   const double upd_bytes = 48.0 + 2.0 * bt + (fp64 ? 0.0 : bt);
-  int launched = 0;
+  const bool vec_ok = aligned16(x) && aligned16(h->r) && aligned16(h->p) && aligned16(h->q) && aligned16(wd0) &&
+                      aligned16(s0) && aligned16(y0) && aligned16(h->z);
   for (int it = 1; it <= maxit; ++it) {
     {
-      ProfScope ps(h->mem.stream, AMG_K_SPMV_DOT, spmv_bytes);
-      k_spmv_dot<<<grid_for(n), TPB, 0, s>>>(n, A.rp, A.ci, A.v, h->p, h->q, h->sc, h->partials, h->counter);
-      AMG_CHECK_LAUNCH();
+      ProfScope ps(s, AMG_K_SPMV_DOT, spmv_bytes, 0);
+      OpSpmvDot op{a64, h->p, h->q, h->sc, h->partials, h->counter};
+      launch_mat(A, A.map64, op, s);
     }
     {
-      ProfScope ps(h->mem.stream, AMG_K_PCG_UPDATE, upd_bytes * n);
-      k_pcg_update<T><<<grid_for(n), TPB, 0, s>>>(n, x, h->r, h->p, h->q, VTypes<T>::wd(L0), y0, vec<T>(L0.s), !fp64,
-                                                  h->prm.nu1 > 0, h->sc, h->hist, h->hist_cap, h->d_done,
-                                                  h->partials, h->counter);
+      ProfScope ps(s, AMG_K_PCG_UPDATE, upd_bytes * n, 0);
+      if (vec_ok)
+        k_pcg_update<T, true><<<grid_for((n + 1) / 2), TPB, 0, s>>>(n, x, h->r, h->p, h->q, wd0, y0, s0, !fp64, pre,
+                                                                    h->sc, h->hist, h->hist_cap, h->d_done,
+                                                                    h->partials, h->counter);
+      else
+        k_pcg_update<T, false><<<grid_for(n), TPB, 0, s>>>(n, x, h->r, h->p, h->q, wd0, y0, s0, !fp64, pre, h->sc,
+                                                           h->hist, h->hist_cap, h->d_done, h->partials, h->counter);
       AMG_CHECK_LAUNCH();
     }
     vcycle<T, TP>(h, h->z, cc);
     {
-      ProfScope ps(h->mem.stream, AMG_K_DIRECTION, 24.0 * n);
-      k_direction<<<grid_for(n), TPB, 0, s>>>(n, h->z, h->p, h->sc);
+      ProfScope ps(s, AMG_K_DIRECTION, 24.0 * n, 0);
+      if (vec_ok) k_direction<true><<<grid_for((n + 1) / 2), TPB, 0, s>>>(n, h->z, h->p, h->sc);
+      else k_direction<false><<<grid_for(n), TPB, 0, s>>>(n, h->z, h->p, h->sc);
       AMG_CHECK_LAUNCH();
     }
     AMG_CUDA(cudaEventRecord(h->iter_ev[it & 1], s));
-    ++launched;
     // keep one iteration in flight: wait for the previous one, then test the flag
     if (it > 1) {
       AMG_CUDA(cudaEventSynchronize(h->iter_ev[(it - 1) & 1]));
@@ -632,15 +1037,11 @@ void vcycle_apply_impl(amg_hierarchy *h, const double *y, double *z) {
 }
 
 template <typename T>
-size_t alloc_vectors(amg_hierarchy *h) {
-  size_t bytes = 0;
+void alloc_vectors(amg_hierarchy *h) {
   for (int k = 0; k < h->nlevels; ++k) {
     Level &L = h->lev[k];
     const int n = L.A.n;
-    auto get = [&](size_t cnt) {
-      bytes += cnt * sizeof(T);
-      return static_cast<void *>(h->mem.get_n<T>(cnt));
-    };
+    auto get = [&](size_t cnt) { return static_cast<void *>(h->mem.get_n<T>(cnt)); };
     if (k == 0 && std::is_same<T, double>::value) L.y = h->r;  // FP64: V-cycle input is the CG residual
     else L.y = get(n);
     L.z = get(n);
@@ -650,7 +1051,6 @@ size_t alloc_vectors(amg_hierarchy *h) {
       L.w = get(n);
     }
   }
-  return bytes;
 }
 
 }  // namespace
@@ -659,41 +1059,55 @@ void prepare_solve(amg_hierarchy *h) {
   Mem &m = h->mem;
   cudaStream_t s = m.stream;
   const int prec = h->prm.precision;
+  const bool fp64 = prec == AMG_PREC_FP64;
   const int n0 = h->lev[0].A.n;
-  // omega / diag, FP32 copies of the hierarchy
+  AMG_CUDA(cudaFuncSetAttribute(k_coarse_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * sizeof(double) * kMaxDense)));
+  AMG_CUDA(cudaFuncSetAttribute(k_coarse_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * sizeof(double) * kMaxDense)));
   for (int k = 0; k < h->nlevels; ++k) {
     Level &L = h->lev[k];
     const int n = L.A.n;
-    L.wd = m.get_n<double>(n);
-    h->bytes += 8 * (size_t)n;
-    if (prec != AMG_PREC_FP64) {
-      L.wd32 = m.get_n<float>(n);
-      h->bytes += 4 * (size_t)n;
+    const bool last = k == h->nlevels - 1;
+    L.A.map = choose_map(L.A.nnz, L.A.n, fp64);
+    L.A.map64 = choose_map(L.A.nnz, L.A.n, true);
+    if (!last) {
+      L.P.map = choose_map(L.P.nnz, L.P.n, fp64);
+      L.R.map = choose_map(L.R.nnz, L.R.n, fp64);
     }
+    L.wd = m.get_n<double>(n);
+    if (!fp64) L.wd32 = m.get_n<float>(n);
     {
       ProfScope ps(s, AMG_K_SETUP_OTHER, 4.0 * (n + 1) + 12.0 * L.A.nnz + 12.0 * n);
       k_make_wd<<<grid_for(n), TPB, 0, s>>>(n, L.A.rp, L.A.ci, L.A.v, h->prm.omega, L.wd, L.wd32);
       AMG_CHECK_LAUNCH();
     }
-    if (prec != AMG_PREC_FP64) {
+    if (!fp64) {  // CSR FP32 copies (the CSR kernels of small levels and the export keep them)
       L.A.v32 = m.get_n<float>(std::max<int64_t>(L.A.nnz, 1));
-      h->bytes += 4 * (size_t)L.A.nnz;
-      k_to_f32<<<grid_for(L.A.nnz), TPB, 0, s>>>(L.A.nnz, L.A.v, L.A.v32);
-      AMG_CHECK_LAUNCH();
-      if (k < h->nlevels - 1) {
+      {
+        ProfScope ps(s, AMG_K_SETUP_OTHER, 12.0 * L.A.nnz);
+        k_to_f32<<<grid_for(L.A.nnz), TPB, 0, s>>>(L.A.nnz, L.A.v, L.A.v32);
+        AMG_CHECK_LAUNCH();
+      }
+      if (!last) {
         for (DCsr *M : {&L.P, &L.R}) {
+          ProfScope ps(s, AMG_K_SETUP_OTHER, (prec == AMG_PREC_FP32 ? 12.0 : 10.0) * M->nnz);
           if (prec == AMG_PREC_FP32) {
             M->v32 = m.get_n<float>(std::max<int64_t>(M->nnz, 1));
-            h->bytes += 4 * (size_t)M->nnz;
             k_to_f32<<<grid_for(M->nnz), TPB, 0, s>>>(M->nnz, M->v, M->v32);
           } else {
             M->v16 = m.get_n<__nv_bfloat16>(std::max<int64_t>(M->nnz, 1));
-            h->bytes += 2 * (size_t)M->nnz;
             k_to_bf16<<<grid_for(M->nnz), TPB, 0, s>>>(M->nnz, M->v, M->v16);
           }
           AMG_CHECK_LAUNCH();
         }
       }
+    }
+    // SELL copies for the large matrices (A also in FP64 on level 0 for the CG products)
+    if (n >= kSellMinRows) build_sell(m, L.A, fp64 || k == 0, !fp64, false);
+    if (!last) {
+      if (L.P.n >= kSellMinRows) build_sell(m, L.P, fp64, prec == AMG_PREC_FP32, prec == AMG_PREC_FP32_BF16PR);
+      if (L.R.n >= kSellMinRows) build_sell(m, L.R, fp64, prec == AMG_PREC_FP32, prec == AMG_PREC_FP32_BF16PR);
     }
   }
   // CG vectors (FP64) and scalars
@@ -701,14 +1115,14 @@ void prepare_solve(amg_hierarchy *h) {
   h->z = m.get_n<double>(n0);
   h->p = m.get_n<double>(n0);
   h->q = m.get_n<double>(n0);
-  h->bytes += 32 * (size_t)n0;
   h->sc = m.get_n<PcgScalars>(1);
   h->d_zero = m.get_n<int>(1);
   AMG_CUDA(cudaMemsetAsync(h->d_zero, 0, sizeof(int), s));
   h->partials = m.get_n<double>(3 * MAX_GRID);
   h->counter = m.get_n<unsigned int>(1);
   AMG_CUDA(cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), s));
-  h->bytes += (prec == AMG_PREC_FP64) ? alloc_vectors<double>(h) : alloc_vectors<float>(h);
+  if (fp64) alloc_vectors<double>(h);
+  else alloc_vectors<float>(h);
   AMG_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&h->h_done), sizeof(int), cudaHostAllocMapped));
   *h->h_done = 0;
   AMG_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void **>(&h->d_done), h->h_done, 0));
@@ -744,8 +1158,13 @@ void vcycle_apply(amg_hierarchy *h, const double *y, double *z) {
 void spmv_level(amg_hierarchy *h, int level, const double *x, double *y) {
   const DCsr &A = h->lev[level].A;
   ProfScope ps(h->mem.stream, AMG_K_SOLVE_OTHER, 12.0 * A.nnz + 4.0 * (A.n + 1) + 16.0 * A.n);
-  k_spmv64<<<grid_for(A.n), TPB, 0, h->mem.stream>>>(A.n, A.rp, A.ci, A.v, x, y);
-  AMG_CHECK_LAUNCH();
+  if (A.use_sell && A.sell.v) {
+    OpSpmv op{A.sell.v, x, y};
+    launch_mat(A, A.map64, op, h->mem.stream);
+  } else {
+    OpSpmv op{A.v, x, y};
+    launch_rows(A.map64, A.n, A.rp, A.ci, op, h->mem.stream);
+  }
 }
 
 }  // namespace amg

@@ -75,6 +75,13 @@ CASES = {
     "graph_hubs_6000": lambda: pr.graph_with_hubs(6000, 6, 4, 2500, 0.05, 8),
 }
 
+# Matrices with >= 32768 rows run the solve kernels on their sliced-ELLPACK
+# copies; the random graph's varying degrees make the copy length-sorted.
+LARGE = {
+    "diffusion3d_40": lambda: pr.diffusion3d(40, 2.0, 3)[0],
+    "graph_50000": lambda: pr.graph_with_hubs(50000, 8, 0, 0, 0.05, 4),
+}
+
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("seed", [0, 17])
@@ -129,6 +136,33 @@ def test_vcycle_reduced_precision(prec, tol):
     zo = ho.vcycle(y)
     zg = hg.vcycle(dev(y)).cpu().numpy()
     assert np.abs(zg - zo).max() <= tol * np.abs(zo).max()
+
+
+@pytest.mark.parametrize("name", list(LARGE))
+@pytest.mark.parametrize("prec,tol", [(amg.PREC_FP64, 1e-12), (amg.PREC_FP32, 1e-5)])
+def test_vcycle_parity_large_levels(name, prec, tol):
+    A = LARGE[name]()
+    ho = O.Hierarchy(A, seed=2)
+    hg = amg.Hierarchy(A, seed=2, precision=prec)
+    y = np.random.default_rng(3).standard_normal(A.n)
+    zo = ho.vcycle(y)
+    zg = hg.vcycle(dev(y)).cpu().numpy()
+    assert np.abs(zg - zo).max() <= tol * np.abs(zo).max()
+    if prec == amg.PREC_FP64:
+        rp, ci, v = ho.A(0)
+        x = np.random.default_rng(4).standard_normal(A.n)
+        yo = O.spmv(A, x)
+        yg = hg.spmv(0, dev(x)).cpu().numpy()
+        assert np.abs(yg - yo).max() <= 1e-13 * np.abs(yo).max()
+
+
+@pytest.mark.parametrize("name", list(LARGE))
+def test_pcg_fp64_parity_large(name):
+    A = LARGE[name]()
+    b = pr.uniform(A.n, 12)
+    xo, ito, ho_, xg, itg, hg_ = _solve_both(A, b)
+    assert itg == ito
+    assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
 
 
 def test_spmv_parity_all_levels():
