@@ -7,19 +7,21 @@
 // from 0 (__dadd_rn).  Every output row lists its columns in ascending order
 // and keeps every structurally produced entry.  Compiled with --fmad=false.
 //
-// Rows are binned by the bound ub_i = sum_{p in X_i} nnz(Y_{k_p}) on the
-// number of products:
-//   tier 0  ub <= 32     a warp per row, one candidate product per lane, kept
-//                        in registers; duplicates found with __match_any_sync,
-//                        each group summed by its lowest lane in lane order
-//                        (lane order = p order, so the sum is canonical);
-//   tier 1-3 ub <= 64 / 256 / 1024   a warp per row, shared-memory hash set
-//                        of 128 / 512 / 2048 slots, keys bitonic-sorted, then
-//                        the values summed p by p into a shared accumulator;
-//   tier 4  ub <= 4096   a block per row, 8192-slot table in shared memory;
-//   tier 5  larger       a block per row, table in a global scratch slice.
-// Each tier runs twice: a symbolic pass (distinct-column count per row, then
-// a scan gives the row pointers) and a fill pass (columns + values).
+// One numeric pass.  Each row i gets ub_i = sum_{p in X_i} nnz(Y_{k_p})
+// slots of scratch (an upper bound on its distinct columns); the row's sorted
+// columns and sums are written there with their count, and a compaction copies
+// the rows into the final CSR.  Rows are binned by ub_i into tiers, each a
+// stable (row-ordered) list so that neighbouring warps work on neighbouring
+// rows:
+//   tier 0    ub <= 32     a warp per row, one candidate product per lane in
+//                          registers; duplicates found with __match_any_sync,
+//                          each group summed by its lowest lane in lane order
+//                          (lane order = p order, so the sum is canonical);
+//   tier 1-5  ub <= 64 ... 1024   a warp per row, a shared-memory hash set of
+//                          2 ub_max slots (128 ... 2048), keys bitonic-sorted,
+//                          then the values summed p by p into shared memory;
+//   tier 6    ub <= 4096   a block per row, 8192-slot table in shared memory;
+//   tier 7    larger       a block per row, table in a global scratch slice.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,20 +36,24 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int TPB = 256;
 constexpr int WARPS = TPB / 32;
-constexpr int NTIER = 6;
-constexpr int BTAB = 8192;  // tier-4 table slots
+constexpr int NTIER = 8;
+constexpr int BTAB = 8192;  // tier-6 table slots
+constexpr int TILE = 1024;  // rows per binning tile
+
+__device__ __forceinline__ int tier_of(int64_t ub) {
+  return ub <= 32 ? 0 : ub <= 64 ? 1 : ub <= 128 ? 2 : ub <= 256 ? 3 : ub <= 512 ? 4 : ub <= 1024 ? 5
+         : ub <= 4096 ? 6 : 7;
+}
 
 // flags[3] is set on a full hash table (cannot happen while ub <= slots / 2).
-__device__ __forceinline__ bool hash_insert(int *table, unsigned mask, int key, int *flags) {
+__device__ __forceinline__ void hash_insert(int *table, unsigned mask, int key, int *flags) {
   unsigned h = ((unsigned)key * 2654435761u) & mask;
   for (unsigned probe = 0; probe <= mask; ++probe) {
     const int prev = atomicCAS(&table[h], -1, key);
-    if (prev == -1) return true;
-    if (prev == key) return false;
+    if (prev == -1 || prev == key) return;
     h = (h + 1) & mask;
   }
   flags[3] = 1;
-  return false;
 }
 
 __device__ __forceinline__ int lower_bound(const int *a, int len, int key) {
@@ -66,13 +72,18 @@ __device__ __forceinline__ int next_pow2(int v) {
   return p;
 }
 
-__global__ void k_bin_rows(int m, const int *__restrict__ xrp, const int *__restrict__ xci,
-                           const int *__restrict__ yrp, int *__restrict__ lists, int *__restrict__ counts,
-                           int *__restrict__ max_ub, int *flags) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  int cls = -1;
-  if (i < m) {
+// ------------------------------------------------------------- binning ----
+// ub and tier per row; per-tile tier counts; largest ub of the global tier.
+__global__ void __launch_bounds__(TPB) k_bin_rows(int m, const int *__restrict__ xrp, const int *__restrict__ xci,
+                                                  const int *__restrict__ yrp, int *__restrict__ ub_out,
+                                                  int8_t *__restrict__ tier, int *__restrict__ tile_cnt,
+                                                  int *__restrict__ max_ub, int *flags) {
+  __shared__ int cnt[NTIER];
+  if (threadIdx.x < NTIER) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < TILE; t += TPB) {
+    const int i = blockIdx.x * TILE + t;
+    if (i >= m) break;
     int64_t ub = 0;
     for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
       const int k = xci[p];
@@ -82,53 +93,112 @@ __global__ void k_bin_rows(int m, const int *__restrict__ xrp, const int *__rest
       flags[3] = 1;
       ub = 1 << 30;
     }
-    cls = ub <= 32 ? 0 : ub <= 64 ? 1 : ub <= 256 ? 2 : ub <= 1024 ? 3 : ub <= 4096 ? 4 : 5;
-    if (cls == NTIER - 1) atomicMax(max_ub, (int)ub);
+    const int c = tier_of(ub);
+    ub_out[i] = (int)ub;
+    tier[i] = (int8_t)c;
+    atomicAdd(&cnt[c], 1);
+    if (c == NTIER - 1) atomicMax(max_ub, (int)ub);
   }
-  for (int c = 0; c < NTIER; ++c) {
-    const unsigned mask = __ballot_sync(FULL, cls == c);
-    if (!mask) continue;
-    const int leader = __ffs(mask) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&counts[c], __popc(mask));
-    base = __shfl_sync(FULL, base, leader);
-    if (cls == c) lists[(int64_t)c * m + base + __popc(mask & ((1u << lane) - 1u))] = i;
+  __syncthreads();
+  if (threadIdx.x < NTIER) tile_cnt[blockIdx.x * NTIER + threadIdx.x] = cnt[threadIdx.x];
+}
+
+// Exclusive offsets of every (tile, tier) pair in the concatenated tier
+// lists (tier-major, tiles in order); totals[t] = rows in tier t.
+__global__ void k_tier_offsets(int ntiles, const int *__restrict__ tile_cnt, int *__restrict__ tile_off,
+                               int *__restrict__ totals) {
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int t = 0; t < NTIER; ++t) {
+    // serial over tiles in chunks: one thread per tile chunk would need a
+    // scan; tile counts are few (n / 1024), a block-wide scan per chunk
+    __shared__ int chunk[TPB];
+    int carry = 0;
+    for (int c0 = 0; c0 < ntiles; c0 += TPB) {
+      const int j = c0 + threadIdx.x;
+      const int v = j < ntiles ? tile_cnt[j * NTIER + t] : 0;
+      chunk[threadIdx.x] = v;
+      __syncthreads();
+      for (int d = 1; d < TPB; d <<= 1) {  // inclusive Hillis-Steele scan
+        const int add = threadIdx.x >= d ? chunk[threadIdx.x - d] : 0;
+        __syncthreads();
+        chunk[threadIdx.x] += add;
+        __syncthreads();
+      }
+      if (j < ntiles) tile_off[j * NTIER + t] = base + carry + chunk[threadIdx.x] - v;
+      carry += chunk[TPB - 1];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      totals[t] = carry;
+      base += carry;
+    }
+    __syncthreads();
+  }
+}
+
+// Writes each row to its tier's list at its stable (row-ordered) position.
+__global__ void __launch_bounds__(TPB) k_tier_scatter(int m, const int8_t *__restrict__ tier,
+                                                      const int *__restrict__ tile_off, int *__restrict__ lists) {
+  __shared__ int run[NTIER];
+  __shared__ int wcnt[NTIER][WARPS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x < NTIER) run[threadIdx.x] = tile_off[blockIdx.x * NTIER + threadIdx.x];
+  __syncthreads();
+  for (int t0 = 0; t0 < TILE; t0 += TPB) {
+    const int i = blockIdx.x * TILE + t0 + threadIdx.x;
+    const int c = i < m ? tier[i] : -1;
+    unsigned myb = 0;
+    for (int t = 0; t < NTIER; ++t) {
+      const unsigned b = __ballot_sync(FULL, c == t);
+      if (lane == 0) wcnt[t][w] = __popc(b);
+      if (c == t) myb = b;
+    }
+    __syncthreads();
+    if (c >= 0) {
+      int pos = run[c] + __popc(myb & ((1u << lane) - 1u));
+      for (int ww = 0; ww < w; ++ww) pos += wcnt[c][ww];
+      lists[pos] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x < NTIER) {
+      int s = 0;
+      for (int ww = 0; ww < WARPS; ++ww) s += wcnt[threadIdx.x][ww];
+      run[threadIdx.x] += s;
+    }
+    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------- tier 0 ----
-template <bool FILL>
 __global__ void __launch_bounds__(TPB) k_spgemm_reg(const int *__restrict__ rows, int nrows,
                                                     const int *__restrict__ xrp, const int *__restrict__ xci,
                                                     const double *__restrict__ xv, const int *__restrict__ yrp,
                                                     const int *__restrict__ yci, const double *__restrict__ yv,
-                                                    const int *__restrict__ crp, int *__restrict__ cci,
-                                                    double *__restrict__ cv, int *__restrict__ cnt) {
+                                                    const int *__restrict__ off, int *__restrict__ tci,
+                                                    double *__restrict__ tcv, int *__restrict__ cnt) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (int r = gw; r < nrows; r += nw) {
     const int i = rows[r];
     int key = INT_MAX;
     double val = 0.0;
-    int off = 0;
+    int o = 0;
     for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
       const int k = xci[p];
       const int yb = yrp[k], len = yrp[k + 1] - yb;
-      if (lane >= off && lane < off + len) {
-        const int q = yb + lane - off;
+      if (lane >= o && lane < o + len) {
+        const int q = yb + lane - o;
         key = yci[q];
-        if (FILL) val = __dmul_rn(xv[p], yv[q]);
+        val = __dmul_rn(xv[p], yv[q]);
       }
-      off += len;
+      o += len;
     }
-    const bool valid = lane < off;
+    const bool valid = lane < o;
     const unsigned grp = __match_any_sync(FULL, key);
     const bool leader = valid && (__ffs(grp) - 1) == lane;
     const unsigned lmask = __ballot_sync(FULL, leader);
-    if (!FILL) {
-      if (lane == 0) cnt[i] = __popc(lmask);
-      continue;
-    }
     int rank = 0;
     for (int j = 0; j < 32; ++j) {
       const int kj = __shfl_sync(FULL, key, j);
@@ -143,24 +213,25 @@ __global__ void __launch_bounds__(TPB) k_spgemm_reg(const int *__restrict__ rows
       if (leader && mm) acc = __dadd_rn(acc, v);
       mm &= mm - 1u;
     }
+    const int base = off[i];
     if (leader) {
-      const int pos = crp[i] + rank;
-      cci[pos] = key;
-      cv[pos] = acc;
+      tci[base + rank] = key;
+      tcv[base + rank] = acc;
     }
+    if (lane == 0) cnt[i] = __popc(lmask);
   }
 }
 
-// -------------------------------------------------------- tiers 1-3 ----
+// -------------------------------------------------------- tiers 1-5 ----
 // Shared memory per warp: TAB ints (hash table, then reused as TAB/2 double
 // accumulators) + TAB/2 ints (the row's distinct columns, then sorted).
-template <int TAB, bool FILL>
+template <int TAB>
 __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ rows, int nrows,
                                                      const int *__restrict__ xrp, const int *__restrict__ xci,
                                                      const double *__restrict__ xv, const int *__restrict__ yrp,
                                                      const int *__restrict__ yci, const double *__restrict__ yv,
-                                                     const int *__restrict__ crp, int *__restrict__ cci,
-                                                     double *__restrict__ cv, int *__restrict__ cnt, int *flags) {
+                                                     const int *__restrict__ off, int *__restrict__ tci,
+                                                     double *__restrict__ tcv, int *__restrict__ cnt, int *flags) {
   constexpr int HALF = TAB / 2;
   extern __shared__ __align__(16) int smem_i[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -185,11 +256,6 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
       if (key >= 0) keys[count + __popc(bal & ((1u << lane) - 1u))] = key;
       count += __popc(bal);
     }
-    if (!FILL) {
-      if (lane == 0) cnt[i] = count;
-      __syncwarp();
-      continue;
-    }
     const int np2 = next_pow2(count);
     for (int t = count + lane; t < np2; t += 32) keys[t] = INT_MAX;
     __syncwarp();
@@ -207,11 +273,7 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
         }
         __syncwarp();
       }
-    const int cb = crp[i];
-    for (int e = lane; e < count; e += 32) {
-      cci[cb + e] = keys[e];
-      acc[e] = 0.0;
-    }
+    for (int e = lane; e < count; e += 32) acc[e] = 0.0;
     __syncwarp();
     for (int p = xb; p < xe; ++p) {
       const int k = xci[p];
@@ -222,22 +284,27 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
       }
       __syncwarp();
     }
-    for (int e = lane; e < count; e += 32) cv[cb + e] = acc[e];
+    const int base = off[i];
+    for (int e = lane; e < count; e += 32) {
+      tci[base + e] = keys[e];
+      tcv[base + e] = acc[e];
+    }
+    if (lane == 0) cnt[i] = count;
     __syncwarp();
   }
 }
 
-// -------------------------------------------------------- tiers 4-5 ----
+// -------------------------------------------------------- tiers 6-7 ----
 // A block per row; table of `cap` slots (then cap/2 double accumulators) and
 // cap/2 keys, in shared memory (GLOBAL = false, cap = BTAB) or in this block's
 // slice of global scratch (GLOBAL = true).
-template <bool FILL, bool GLOBAL>
+template <bool GLOBAL>
 __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ rows, int nrows,
                                                       const int *__restrict__ xrp, const int *__restrict__ xci,
                                                       const double *__restrict__ xv, const int *__restrict__ yrp,
                                                       const int *__restrict__ yci, const double *__restrict__ yv,
-                                                      const int *__restrict__ crp, int *__restrict__ cci,
-                                                      double *__restrict__ cv, int *__restrict__ cnt, int *flags,
+                                                      const int *__restrict__ off, int *__restrict__ tci,
+                                                      double *__restrict__ tcv, int *__restrict__ cnt, int *flags,
                                                       int *gscratch, int gcap) {
   extern __shared__ __align__(16) int smem_b[];
   __shared__ int s_count;
@@ -262,11 +329,6 @@ __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ ro
     }
     __syncthreads();
     const int count = s_count;
-    if (!FILL) {
-      if (threadIdx.x == 0) cnt[i] = count;
-      __syncthreads();
-      continue;
-    }
     const int np2 = next_pow2(count);
     for (int t = count + threadIdx.x; t < np2; t += blockDim.x) keys[t] = INT_MAX;
     __syncthreads();
@@ -284,11 +346,7 @@ __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ ro
         }
         __syncthreads();
       }
-    const int cb = crp[i];
-    for (int e = threadIdx.x; e < count; e += blockDim.x) {
-      cci[cb + e] = keys[e];
-      acc[e] = 0.0;
-    }
+    for (int e = threadIdx.x; e < count; e += blockDim.x) acc[e] = 0.0;
     __syncthreads();
     for (int p = xb; p < xe; ++p) {
       const int k = xci[p];
@@ -299,8 +357,28 @@ __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ ro
       }
       __syncthreads();
     }
-    for (int e = threadIdx.x; e < count; e += blockDim.x) cv[cb + e] = acc[e];
+    const int base = off[i];
+    for (int e = threadIdx.x; e < count; e += blockDim.x) {
+      tci[base + e] = keys[e];
+      tcv[base + e] = acc[e];
+    }
+    if (threadIdx.x == 0) cnt[i] = count;
     __syncthreads();
+  }
+}
+
+// Copies each row's count entries from its scratch slot to the final CSR.
+__global__ void __launch_bounds__(TPB) k_compact(int m, const int *__restrict__ off, const int *__restrict__ tci,
+                                                 const double *__restrict__ tcv, const int *__restrict__ crp,
+                                                 int *__restrict__ cci, double *__restrict__ cv) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = gw; i < m; i += nw) {
+    const int src = off[i], dst = crp[i], len = crp[i + 1] - dst;
+    for (int e = lane; e < len; e += 32) {
+      cci[dst + e] = tci[src + e];
+      cv[dst + e] = tcv[src + e];
+    }
   }
 }
 
@@ -310,17 +388,26 @@ constexpr size_t hash_smem() {
 }
 constexpr size_t block_smem = (size_t)(BTAB + BTAB / 2) * sizeof(int);
 
-template <int TAB, bool FILL>
-void launch_hash(int nr, const int *list, const DCsr &X, const DCsr &Y, DCsr &C, int *cnt, int *flags, cudaStream_t s) {
+struct Args {
+  const DCsr *X, *Y;
+  const int *off;
+  int *tci;
+  double *tcv;
+  int *cnt, *flags;
+  cudaStream_t s;
+};
+
+template <int TAB>
+void launch_hash(int nr, const int *list, const Args &a) {
   static bool attr = false;
   if (!attr) {
-    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_hash<TAB, FILL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_hash<TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)hash_smem<TAB>()));
     attr = true;
   }
   const int grid = std::max(1, std::min(ceil_div(nr, WARPS), kNumSMs * 32));
-  k_spgemm_hash<TAB, FILL><<<grid, TPB, hash_smem<TAB>(), s>>>(list, nr, X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, C.rp,
-                                                               C.ci, C.v, cnt, flags);
+  k_spgemm_hash<TAB><<<grid, TPB, hash_smem<TAB>(), a.s>>>(list, nr, a.X->rp, a.X->ci, a.X->v, a.Y->rp, a.Y->ci,
+                                                           a.Y->v, a.off, a.tci, a.tcv, a.cnt, a.flags);
   AMG_CHECK_LAUNCH();
 }
 
@@ -329,15 +416,23 @@ void launch_hash(int nr, const int *list, const DCsr &X, const DCsr &Y, DCsr &C,
 void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C) {
   cudaStream_t s = m.stream;
   const int rows = X.n;
-  Buf<int> lists(m, (size_t)rows * NTIER);
-  Buf<int> meta(m, NTIER + 1);  // per-tier counts, max ub of the last tier
+  const int ntiles = ceil_div(rows, TILE);
+  Buf<int> ub(m, (size_t)rows + 1), off(m, (size_t)rows + 1), lists(m, (size_t)rows);
+  Buf<int8_t> tier(m, (size_t)rows);
+  Buf<int> tile_cnt(m, (size_t)ntiles * NTIER), tile_off(m, (size_t)ntiles * NTIER);
+  Buf<int> meta(m, NTIER + 1);  // per-tier row counts, max ub of the last tier
   AMG_CUDA(cudaMemsetAsync(meta.p, 0, sizeof(int) * (NTIER + 1), s));
   const double xy_bytes = 4.0 * (rows + 1) + 12.0 * X.nnz + 4.0 * (Y.n + 1) + 12.0 * Y.nnz;
   {
-    ProfScope ps(s, AMG_K_SPGEMM, 4.0 * (rows + 1) + 4.0 * X.nnz + 4.0 * (Y.n + 1) + 4.0 * rows);
-    k_bin_rows<<<ceil_div(rows, TPB), TPB, 0, s>>>(rows, X.rp, X.ci, Y.rp, lists.p, meta.p, meta.p + NTIER, flags);
+    ProfScope ps(s, AMG_K_SPGEMM, 4.0 * (rows + 1) + 4.0 * X.nnz + 4.0 * (Y.n + 1) + 9.0 * rows);
+    k_bin_rows<<<ntiles, TPB, 0, s>>>(rows, X.rp, X.ci, Y.rp, ub.p, tier.p, tile_cnt.p, meta.p + NTIER, flags);
+    AMG_CHECK_LAUNCH();
+    k_tier_offsets<<<1, TPB, 0, s>>>(ntiles, tile_cnt.p, tile_off.p, meta.p);
+    AMG_CHECK_LAUNCH();
+    k_tier_scatter<<<ntiles, TPB, 0, s>>>(rows, tier.p, tile_off.p, lists.p);
     AMG_CHECK_LAUNCH();
   }
+  const int64_t total_ub = scan_counts(m, ub.p, off.p, rows);  // syncs the stream
   int hm[NTIER + 1];
   AMG_CUDA(cudaMemcpyAsync(hm, meta.p, sizeof(hm), cudaMemcpyDeviceToHost, s));
   AMG_CUDA(cudaStreamSynchronize(s));
@@ -347,57 +442,57 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
   }
   int gcap = 2;
   while (gcap < 2 * std::max(hm[NTIER], 1)) gcap <<= 1;
-  const int gblocks = std::min(hm[5], kNumSMs * 2);
+  const int gblocks = std::min(hm[7], kNumSMs * 2);
   Buf<int> gscr;
-  if (hm[5] > 0) gscr = Buf<int>(m, (size_t)gblocks * ((size_t)gcap + gcap / 2));
+  if (hm[7] > 0) gscr = Buf<int>(m, (size_t)gblocks * ((size_t)gcap + gcap / 2));
   static bool attr = false;
   if (!attr) {
-    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_block<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem));
-    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_block<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem));
+    AMG_CUDA(cudaFuncSetAttribute(k_spgemm_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem));
     attr = true;
   }
-  auto list = [&](int t) { return lists.p + (size_t)t * rows; };
+  Buf<int> tci(m, (size_t)std::max<int64_t>(total_ub, 1));
+  Buf<double> tcv(m, (size_t)std::max<int64_t>(total_ub, 1));
   Buf<int> cnt(m, (size_t)rows + 1);
-  for (int pass = 0; pass < 2; ++pass) {
-    const bool fill = pass == 1;
-    if (fill) {
-      C.n = rows;
-      C.ncols = ncols;
-      C.rp = m.get_n<int>((size_t)rows + 1);
-      C.nnz = scan_counts(m, cnt.p, C.rp, rows);
-      C.ci = m.get_n<int>(std::max<int64_t>(C.nnz, 1));
-      C.v = m.get_n<double>(std::max<int64_t>(C.nnz, 1));
-    }
-    ProfScope ps(s, AMG_K_SPGEMM, fill ? xy_bytes + 12.0 * C.nnz + 4.0 * (rows + 1) : xy_bytes - 8.0 * (X.nnz + Y.nnz));
+  int start[NTIER + 1];
+  start[0] = 0;
+  for (int t = 0; t < NTIER; ++t) start[t + 1] = start[t] + hm[t];
+  auto list = [&](int t) { return lists.p + start[t]; };
+  const Args a{&X, &Y, off.p, tci.p, tcv.p, cnt.p, flags, s};
+  {
+    ProfScope ps(s, AMG_K_SPGEMM, xy_bytes + 12.0 * total_ub);
     if (hm[0] > 0) {
       const int grid = std::max(1, std::min(ceil_div(hm[0], WARPS), kNumSMs * 32));
-      if (fill)
-        k_spgemm_reg<true><<<grid, TPB, 0, s>>>(list(0), hm[0], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, C.rp, C.ci, C.v, cnt.p);
-      else
-        k_spgemm_reg<false><<<grid, TPB, 0, s>>>(list(0), hm[0], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, nullptr, nullptr, nullptr, cnt.p);
+      k_spgemm_reg<<<grid, TPB, 0, s>>>(list(0), hm[0], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off.p, tci.p, tcv.p, cnt.p);
       AMG_CHECK_LAUNCH();
     }
-    if (hm[1] > 0) fill ? launch_hash<128, true>(hm[1], list(1), X, Y, C, cnt.p, flags, s)
-                        : launch_hash<128, false>(hm[1], list(1), X, Y, C, cnt.p, flags, s);
-    if (hm[2] > 0) fill ? launch_hash<512, true>(hm[2], list(2), X, Y, C, cnt.p, flags, s)
-                        : launch_hash<512, false>(hm[2], list(2), X, Y, C, cnt.p, flags, s);
-    if (hm[3] > 0) fill ? launch_hash<2048, true>(hm[3], list(3), X, Y, C, cnt.p, flags, s)
-                        : launch_hash<2048, false>(hm[3], list(3), X, Y, C, cnt.p, flags, s);
-    if (hm[4] > 0) {
-      const int grid = std::max(1, std::min(hm[4], kNumSMs * 4));
-      if (fill)
-        k_spgemm_block<true, false><<<grid, TPB, block_smem, s>>>(list(4), hm[4], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, C.rp, C.ci, C.v, cnt.p, flags, nullptr, 0);
-      else
-        k_spgemm_block<false, false><<<grid, TPB, block_smem, s>>>(list(4), hm[4], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, nullptr, nullptr, nullptr, cnt.p, flags, nullptr, 0);
+    if (hm[1] > 0) launch_hash<128>(hm[1], list(1), a);
+    if (hm[2] > 0) launch_hash<256>(hm[2], list(2), a);
+    if (hm[3] > 0) launch_hash<512>(hm[3], list(3), a);
+    if (hm[4] > 0) launch_hash<1024>(hm[4], list(4), a);
+    if (hm[5] > 0) launch_hash<2048>(hm[5], list(5), a);
+    if (hm[6] > 0) {
+      const int grid = std::max(1, std::min(hm[6], kNumSMs * 4));
+      k_spgemm_block<false><<<grid, TPB, block_smem, s>>>(list(6), hm[6], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off.p,
+                                                          tci.p, tcv.p, cnt.p, flags, nullptr, 0);
       AMG_CHECK_LAUNCH();
     }
-    if (hm[5] > 0) {
-      if (fill)
-        k_spgemm_block<true, true><<<gblocks, TPB, 0, s>>>(list(5), hm[5], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, C.rp, C.ci, C.v, cnt.p, flags, gscr.p, gcap);
-      else
-        k_spgemm_block<false, true><<<gblocks, TPB, 0, s>>>(list(5), hm[5], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, nullptr, nullptr, nullptr, cnt.p, flags, gscr.p, gcap);
+    if (hm[7] > 0) {
+      k_spgemm_block<true><<<gblocks, TPB, 0, s>>>(list(7), hm[7], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off.p, tci.p,
+                                                   tcv.p, cnt.p, flags, gscr.p, gcap);
       AMG_CHECK_LAUNCH();
     }
+  }
+  C.n = rows;
+  C.ncols = ncols;
+  C.rp = m.get_n<int>((size_t)rows + 1);
+  C.nnz = scan_counts(m, cnt.p, C.rp, rows);
+  C.ci = m.get_n<int>(std::max<int64_t>(C.nnz, 1));
+  C.v = m.get_n<double>(std::max<int64_t>(C.nnz, 1));
+  {
+    ProfScope ps(s, AMG_K_SPGEMM, 24.0 * C.nnz + 8.0 * rows);
+    k_compact<<<std::max(1, std::min(ceil_div(rows, WARPS), kNumSMs * 32)), TPB, 0, s>>>(rows, off.p, tci.p, tcv.p,
+                                                                                         C.rp, C.ci, C.v);
+    AMG_CHECK_LAUNCH();
   }
 }
 
