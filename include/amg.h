@@ -124,6 +124,21 @@ int amg_setup(const amg_csr *A, const amg_params *params, const amg_allocator *a
 int amg_pcg_solve(amg_hierarchy *h, const double *b, double *x, double rtol, int32_t maxit, void *stream,
                   int32_t *iters, double *res_hist, int32_t hist_cap);
 
+/* PCG on k right-hand sides at once (Sec. 3.1: dense blocks stored row-wise
+ * for multiple right-hand sides).  B, X: device arrays of n x k doubles,
+ * row-major (entry (i, j) at i * k + j), 1 <= k <= 32; X holds the initial
+ * guesses on entry and the solutions on return.  Every column runs its own CG
+ * recurrence (its own alpha, beta, rho and stopping test ||r_j|| < rtol
+ * ||b_j||) while sharing each sparse product and V-cycle with the others (one
+ * SpMM per product); a converged column is frozen while the rest continue.
+ * iters[k], status[k] (host, may be NULL) receive each column's iteration
+ * count and status; res_hist (host, may be NULL) receives ||r_j|| after
+ * iteration t at res_hist[t * k + j] for t < hist_cap.  Returns AMG_OK when
+ * every column converged, else the first column error met.  Synchronises.
+ * The last level must satisfy 16 * n_L * k <= 200 KiB (AMG_ERR_UNSUPPORTED). */
+int amg_pcg_solve_batch(amg_hierarchy *h, int32_t k, const double *B, double *X, double rtol, int32_t maxit,
+                        void *stream, int32_t *iters, int32_t *status, double *res_hist, int32_t hist_cap);
+
 /* One application of the preconditioner z = B y (Algorithm 2 on level 0):
  * y, z device arrays of n doubles (FP64 in and out in every precision mode). */
 int amg_vcycle_apply(amg_hierarchy *h, const double *y, double *z, void *stream);

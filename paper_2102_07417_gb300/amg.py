@@ -34,7 +34,7 @@ SOLVE_KERNELS = KERNEL_NAMES[:9]
 SETUP_KERNELS = KERNEL_NAMES[9:]
 
 # Names exported by the C ABI (each declared in include/amg.h).
-EXPORTS = ["amg_params_default", "amg_setup", "amg_pcg_solve", "amg_vcycle_apply", "amg_spmv", "amg_solve",
+EXPORTS = ["amg_params_default", "amg_setup", "amg_pcg_solve", "amg_pcg_solve_batch", "amg_vcycle_apply", "amg_spmv", "amg_solve",
            "amg_hierarchy_info", "amg_hierarchy_export", "amg_hierarchy_bytes", "amg_free", "amg_profile_enable",
            "amg_profile_read", "amg_launch_count", "amg_status_string", "amg_last_error",
            "amg_spmv_dot_noalloc"]
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
     L.amg_params_default.argtypes = [C.POINTER(Params)]
     L.amg_setup.argtypes = [C.POINTER(Csr), C.POINTER(Params), C.POINTER(Allocator), vp, C.POINTER(vp)]
     L.amg_pcg_solve.argtypes = [vp, vp, vp, dbl, i32, vp, C.POINTER(i32), vp, i32]
+    L.amg_pcg_solve_batch.argtypes = [vp, i32, vp, vp, dbl, i32, vp, vp, vp, vp, i32]
     L.amg_vcycle_apply.argtypes = [vp, vp, vp, vp]
     L.amg_spmv.argtypes = [vp, i32, vp, vp, vp]
     L.amg_solve.argtypes = [C.POINTER(Csr), vp, vp, C.POINTER(Params), dbl, i32, C.POINTER(Allocator), vp,
@@ -221,6 +222,25 @@ class Hierarchy:
         if st not in (AMG_OK, AMG_ERR_NO_CONVERGENCE):
             check(st, "amg_pcg_solve")
         return x, it.value, st, (hbuf[: it.value + 1].copy() if hist else None)
+
+    def solve_batch(self, B, X=None, rtol: float = 1e-8, maxit: int = 500, hist: bool = False, stream=None):
+        """PCG on the k columns of B (CUDA float64, n x k row-major) at once.
+        Returns (X, iters[k], status[k], overall status, history (maxit+1, k) or None)."""
+        import torch
+
+        k = 1 if B.dim() == 1 else int(B.shape[1])
+        B = B.contiguous()
+        if X is None:
+            X = torch.zeros_like(B)
+        it = np.zeros(k, np.int32)
+        stv = np.zeros(k, np.int32)
+        hbuf = np.zeros((maxit + 1, k)) if hist else None
+        st = load().amg_pcg_solve_batch(self.h, k, _ptr(B), _ptr(X), rtol, maxit,
+                                        _stream_handle(stream) if stream else self.stream, it.ctypes.data,
+                                        stv.ctypes.data, hbuf.ctypes.data if hist else None, maxit + 1 if hist else 0)
+        if st not in (AMG_OK, AMG_ERR_NO_CONVERGENCE, AMG_ERR_BREAKDOWN):
+            check(st, "amg_pcg_solve_batch")
+        return X, it.tolist(), stv.tolist(), st, hbuf
 
     def vcycle(self, y, z=None, stream=None):
         import torch

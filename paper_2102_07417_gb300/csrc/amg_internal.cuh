@@ -205,6 +205,9 @@ void prepare_solve(amg_hierarchy *h);
 int pcg_solve(amg_hierarchy *h, const double *b, double *x, double rtol, int maxit, int *iters, double *hist,
               int hist_cap);
 void vcycle_apply(amg_hierarchy *h, const double *y, double *z);
+// batched right-hand sides (batch.cu)
+int pcg_solve_batch(amg_hierarchy *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
+                    int *status, double *hist, int hist_cap);
 void spmv_level(amg_hierarchy *h, int level, const double *x, double *y);
 void release_solve(amg_hierarchy *h);
 

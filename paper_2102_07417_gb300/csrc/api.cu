@@ -213,6 +213,18 @@ int amg_pcg_solve(amg_hierarchy *h, const double *b, double *x, double rtol, int
   AMG_GUARD_END
 }
 
+int amg_pcg_solve_batch(amg_hierarchy *h, int32_t k, const double *B, double *X, double rtol, int32_t maxit,
+                        void *stream, int32_t *iters, int32_t *status, double *res_hist, int32_t hist_cap) {
+  if (!h || !B || !X) return bad("NULL argument");
+  if (k < 1 || k > 32) return bad("k must be in 1..32");
+  if (!(rtol > 0.0) || maxit < 1) return bad("rtol must be > 0 and maxit >= 1");
+  if (res_hist && hist_cap < 0) return bad("hist_cap < 0");
+  AMG_GUARD_BEGIN
+  h->mem.stream = static_cast<cudaStream_t>(stream);
+  return amg::pcg_solve_batch(h, k, B, X, rtol, maxit, iters, status, res_hist, res_hist ? hist_cap : 0);
+  AMG_GUARD_END
+}
+
 int amg_vcycle_apply(amg_hierarchy *h, const double *y, double *z, void *stream) {
   if (!h || !y || !z) return bad("NULL argument");
   AMG_GUARD_BEGIN

@@ -1,0 +1,715 @@
+// batch.cu -- PCG on a block of k right-hand sides at once (Sec. 3.1: dense
+// blocks stored row-wise, "efficient for linear systems with multiple
+// right-hand-sides").  Vectors are n x k row-major; every sparse product is an
+// SpMM in which a group of K >= k lanes owns one row and lane j its column j,
+// so a nonzero is read once for all k columns and the k-wide gathers are
+// coalesced.  The V-cycle (Algorithm 2) and the CG recurrences are the same
+// as the single right-hand side path, with per-column scalars (alpha_j,
+// beta_j, rho_j) and a per-column convergence mask: a converged column is
+// frozen (its x and r are no longer updated) while the others continue.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+#include "amg_internal.cuh"
+
+namespace amg {
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int MAX_GRID = kNumSMs * 8;
+constexpr int KMAX = 32;  // largest block width
+
+struct BScal {
+  double rho[KMAX], alpha[KMAX], beta[KMAX], rr[KMAX], bb[KMAX], tol[KMAX];
+  int iters[KMAX], done[KMAX], status[KMAX];
+  int all_done, maxit, k;
+};
+
+__device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float tof(float v) { return v; }
+__device__ __forceinline__ double tof(double v) { return v; }
+
+// Per-column sums of NV values: v[c] is this thread's partial for column
+// (lane % K).  Block partials go to partials[(block * 3 + c) * KMAX + j]; the
+// last block to finish gets the totals out[c] for its column j = lane % K
+// (summed in block order, deterministic) and returns true.
+template <int K, int NV>
+__device__ bool col_reduce(const double (&v)[NV], double *partials, unsigned int *counter, double (&out)[NV]) {
+  __shared__ double red[NV][TPB];
+  __shared__ bool last;
+#pragma unroll
+  for (int c = 0; c < NV; ++c) red[c][threadIdx.x] = v[c];
+  __syncthreads();
+  if (threadIdx.x < K) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      double s = 0.0;
+      for (int m = threadIdx.x; m < TPB; m += K) s += red[c][m];
+      partials[(blockIdx.x * 3 + c) * KMAX + threadIdx.x] = s;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  if (threadIdx.x < K) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      double s = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(&partials[(b * 3 + c) * KMAX + threadIdx.x]);
+      out[c] = s;
+    }
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+template <int NV>
+struct BAcc {
+  double v[NV > 0 ? NV : 1];
+};
+
+// SpMM row kernel: group of K lanes per row, lane j = column j (< k).
+// For each (row, j): sum = sum_p mat(p) vec(ci[p], j); op.out(row, j, sum, acc).
+template <int K, class Op>
+__global__ void __launch_bounds__(TPB) k_brows(int n, int k, const int *__restrict__ rp, const int *__restrict__ ci,
+                                               Op op) {
+  using T = typename Op::T;
+  constexpr int NA = Op::NV > 0 ? Op::NV : 1;
+  if (op.skip()) return;
+  const int lane = threadIdx.x & 31, j = lane & (K - 1), grp = lane / K;
+  constexpr int RPW = 32 / K;
+  const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5, nw = (gridDim.x * TPB) >> 5;
+  BAcc<NA> acc;
+#pragma unroll
+  for (int c = 0; c < NA; ++c) acc.v[c] = 0.0;
+  for (int base = gw * RPW; base < n; base += nw * RPW) {
+    const int row = base + grp;
+    if (row < n && j < k) {
+      T sum = T(0);
+      if constexpr (Op::kMatrix) {
+        const int e = rp[row + 1];
+#pragma unroll 4
+        for (int p = rp[row]; p < e; ++p) sum = fma(op.mat(p), op.vec(ci[p], j), sum);
+      }
+      op.out(row, j, sum, acc);
+    }
+  }
+  op.finish(acc);
+}
+
+// ------------------------------------------------------------------ ops --
+// Block vectors are row-major with leading dimension k: v[i * k + j].
+
+// r = b - A x;  (b_j, b_j), (r_j, r_j);  V-cycle input y0 / s0.
+template <int K, typename TV>
+struct BInit {
+  using T = double;
+  static constexpr int NV = 2;
+  static constexpr bool kMatrix = true;
+  int k;
+  const double *a, *x, *b;
+  double *r;
+  const TV *wd;
+  TV *y0, *s0;
+  bool write_y, pre;
+  double rtol;
+  BScal *sc;
+  double *hist;
+  int hist_cap;
+  double *partials;
+  unsigned int *counter;
+  __device__ bool skip() const { return false; }
+  __device__ double mat(int p) const { return __ldg(a + p); }
+  __device__ double vec(int c, int j) const { return __ldg(x + (size_t)c * k + j); }
+  __device__ void out(int i, int j, double sum, BAcc<NV> &acc) const {
+    const size_t o = (size_t)i * k + j;
+    const double bi = b[o], ri = bi - sum;
+    r[o] = ri;
+    acc.v[0] = fma(bi, bi, acc.v[0]);
+    acc.v[1] = fma(ri, ri, acc.v[1]);
+    const TV yi = static_cast<TV>(ri);
+    if (write_y) y0[o] = yi;
+    s0[o] = pre ? wd[i] * yi : TV(0);
+  }
+  __device__ void finish(BAcc<NV> &acc) const {
+    double tot[2];
+    if (col_reduce<K, 2>(acc.v, partials, counter, tot)) {
+      const int j = threadIdx.x;
+      if (j < k) {
+        sc->bb[j] = tot[0];
+        sc->rr[j] = tot[1];
+        sc->tol[j] = rtol * sqrt(tot[0]);
+        const double res = sqrt(tot[1]);
+        if (hist_cap > 0) hist[j] = res;
+        sc->iters[j] = 0;
+        sc->status[j] = AMG_OK;
+        sc->done[j] = (res < sc->tol[j] || tot[0] == 0.0) ? 1 : 0;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int all = 1;
+        for (int c = 0; c < k; ++c) all &= sc->done[c];
+        sc->all_done = all;
+      }
+    }
+  }
+};
+
+// q = A p;  alpha_j = rho_j / (p_j, q_j) (columns not done).
+template <int K>
+struct BSpmvDot {
+  using T = double;
+  static constexpr int NV = 1;
+  static constexpr bool kMatrix = true;
+  int k;
+  const double *a, *p;
+  double *q;
+  BScal *sc;
+  double *partials;
+  unsigned int *counter;
+  __device__ bool skip() const { return sc->all_done; }
+  __device__ double mat(int t) const { return __ldg(a + t); }
+  __device__ double vec(int c, int j) const { return __ldg(p + (size_t)c * k + j); }
+  __device__ void out(int i, int j, double sum, BAcc<NV> &acc) const {
+    const size_t o = (size_t)i * k + j;
+    q[o] = sum;
+    acc.v[0] = fma(p[o], sum, acc.v[0]);
+  }
+  __device__ void finish(BAcc<NV> &acc) const {
+    double tot[1];
+    if (col_reduce<K, 1>(acc.v, partials, counter, tot)) {
+      const int j = threadIdx.x;
+      if (j < k && !sc->done[j]) {
+        if (!(tot[0] > 0.0)) {
+          sc->status[j] = AMG_ERR_BREAKDOWN;
+          sc->done[j] = 1;
+          sc->alpha[j] = 0.0;
+        } else {
+          sc->alpha[j] = sc->rho[j] / tot[0];
+        }
+      }
+    }
+  }
+};
+
+template <typename TT>
+struct BResid {  // r = y - A s
+  using T = TT;
+  static constexpr int NV = 0;
+  static constexpr bool kMatrix = true;
+  int k;
+  const T *a, *s, *y;
+  T *r;
+  const int *done;
+  __device__ bool skip() const { return *done; }
+  __device__ T mat(int p) const { return __ldg(a + p); }
+  __device__ T vec(int c, int j) const { return __ldg(s + (size_t)c * k + j); }
+  __device__ void out(int i, int j, T sum, BAcc<1> &) const {
+    const size_t o = (size_t)i * k + j;
+    r[o] = y[o] - sum;
+  }
+  __device__ void finish(BAcc<1> &) const {}
+};
+
+template <typename TT, typename TP>
+struct BRestrict {  // y_c = R r;  s_c = wd_c y_c (pre = 1), 0 (pre = 0), not written (pre = -1)
+  using T = TT;
+  static constexpr int NV = 0;
+  static constexpr bool kMatrix = true;
+  int k;
+  const TP *rv;
+  const T *r, *wd;
+  T *yc, *sc;
+  int pre;
+  const int *done;
+  __device__ bool skip() const { return *done; }
+  __device__ T mat(int p) const { return static_cast<T>(tof(rv[p])); }
+  __device__ T vec(int c, int j) const { return __ldg(r + (size_t)c * k + j); }
+  __device__ void out(int i, int j, T sum, BAcc<1> &) const {
+    const size_t o = (size_t)i * k + j;
+    yc[o] = sum;
+    if (pre >= 0) sc[o] = pre ? wd[i] * sum : T(0);
+  }
+  __device__ void finish(BAcc<1> &) const {}
+};
+
+template <typename TT, typename TP>
+struct BProlong {  // t = s + P z_c
+  using T = TT;
+  static constexpr int NV = 0;
+  static constexpr bool kMatrix = true;
+  int k;
+  const TP *pv;
+  const T *s, *zc;
+  T *t;
+  const int *done;
+  __device__ bool skip() const { return *done; }
+  __device__ T mat(int p) const { return static_cast<T>(tof(pv[p])); }
+  __device__ T vec(int c, int j) const { return __ldg(zc + (size_t)c * k + j); }
+  __device__ void out(int i, int j, T sum, BAcc<1> &) const {
+    const size_t o = (size_t)i * k + j;
+    t[o] = s[o] + sum;
+  }
+  __device__ void finish(BAcc<1> &) const {}
+};
+
+template <typename TT>
+struct BJacobi {  // z = t + wd (y - A t)
+  using T = TT;
+  static constexpr int NV = 0;
+  static constexpr bool kMatrix = true;
+  int k;
+  const T *a, *wd, *y, *t;
+  T *z;
+  const int *done;
+  __device__ bool skip() const { return *done; }
+  __device__ T mat(int p) const { return __ldg(a + p); }
+  __device__ T vec(int c, int j) const { return __ldg(t + (size_t)c * k + j); }
+  __device__ void out(int i, int j, T sum, BAcc<1> &) const {
+    const size_t o = (size_t)i * k + j;
+    z[o] = fma(wd[i], y[o] - sum, t[o]);
+  }
+  __device__ void finish(BAcc<1> &) const {}
+};
+
+enum { BPOST_APPLY = 0, BPOST_FIRST = 1, BPOST_ITER = 2 };
+
+// Level-0 post-smoothing (or copy) fused with the per-column CG bookkeeping.
+template <int K, typename TT, bool SWEEP>
+struct BPost0 {
+  using T = TT;
+  static constexpr int NV = 2;
+  static constexpr bool kMatrix = SWEEP;
+  int k;
+  const T *a, *wd, *y, *t;
+  double *z;
+  const double *r, *q;
+  double *p;
+  int mode, flexible;
+  BScal *sc;
+  const int *done;
+  double *partials;
+  unsigned int *counter;
+  __device__ bool skip() const { return *done; }
+  __device__ T mat(int pp) const { return __ldg(a + pp); }
+  __device__ T vec(int c, int j) const { return __ldg(t + (size_t)c * k + j); }
+  __device__ void out(int i, int j, T sum, BAcc<NV> &acc) const {
+    const size_t o = (size_t)i * k + j;
+    const T zi = SWEEP ? fma(wd[i], y[o] - sum, t[o]) : t[o];
+    const double zd = static_cast<double>(zi);
+    z[o] = zd;
+    if (mode != BPOST_APPLY) {
+      acc.v[0] = fma(r[o], zd, acc.v[0]);
+      if (mode == BPOST_FIRST) p[o] = zd;
+      else if (flexible) acc.v[1] = fma(zd, q[o], acc.v[1]);
+    }
+  }
+  __device__ void finish(BAcc<NV> &acc) const {
+    if (mode == BPOST_APPLY) return;
+    double tot[2];
+    if (col_reduce<K, 2>(acc.v, partials, counter, tot)) {
+      const int j = threadIdx.x;
+      if (j < k && !sc->done[j]) {
+        if (mode == BPOST_ITER)
+          sc->beta[j] = flexible ? -sc->alpha[j] * tot[1] / sc->rho[j] : tot[0] / sc->rho[j];
+        sc->rho[j] = tot[0];
+      }
+    }
+  }
+};
+
+// x += alpha_j p;  r -= alpha_j q (columns not done);  ||r_j||;  convergence;  V-cycle input.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_bupdate(int n, int k, double *__restrict__ x, double *__restrict__ r,
+                                                 const double *__restrict__ p, const double *__restrict__ q,
+                                                 const T *__restrict__ wd, T *__restrict__ y0, T *__restrict__ s0,
+                                                 bool write_y, bool pre, BScal *sc, double *hist, int hist_cap,
+                                                 int *host_done, double *partials, unsigned int *counter) {
+  if (sc->all_done) return;
+  __shared__ double s_alpha[KMAX];
+  __shared__ int s_done[KMAX];
+  if (threadIdx.x < k) {
+    s_done[threadIdx.x] = sc->done[threadIdx.x];
+    s_alpha[threadIdx.x] = s_done[threadIdx.x] ? 0.0 : sc->alpha[threadIdx.x];
+  }
+  __syncthreads();
+  // thread t handles column t % kk of consecutive entries (kk = power of two >= k)
+  int kk = 1;
+  while (kk < k) kk <<= 1;
+  const int j = threadIdx.x & (kk - 1);
+  double v = 0.0;
+  if (j < k) {
+    const double alpha = s_alpha[j];
+    const bool frozen = s_done[j];
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kk; i < n;
+         i += (int64_t)gridDim.x * blockDim.x / kk) {
+      const size_t o = (size_t)i * k + j;
+      double ri = r[o];
+      if (!frozen) {
+        x[o] = fma(alpha, p[o], x[o]);
+        ri = fma(-alpha, q[o], ri);
+        r[o] = ri;
+      }
+      v = fma(ri, ri, v);
+      const T yi = static_cast<T>(ri);
+      if (write_y) y0[o] = yi;
+      s0[o] = pre ? wd[i] * yi : T(0);
+    }
+  }
+  // per-column block partials (column = thread % kk)
+  __shared__ double red[TPB];
+  __shared__ bool last;
+  red[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x < kk) {
+    double s = 0.0;
+    for (int m = threadIdx.x; m < TPB; m += kk) s += red[m];
+    partials[(blockIdx.x * 3) * KMAX + threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < k) {
+    const int c = threadIdx.x;
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(&partials[(b * 3) * KMAX + c]);
+    if (!sc->done[c]) {
+      const int it = sc->iters[c] + 1;
+      sc->iters[c] = it;
+      sc->rr[c] = s;
+      const double res = sqrt(s);
+      if (it < hist_cap) hist[(size_t)it * k + c] = res;
+      if (res < sc->tol[c]) {
+        sc->done[c] = 1;
+      } else if (it >= sc->maxit) {
+        sc->status[c] = AMG_ERR_NO_CONVERGENCE;
+        sc->done[c] = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *counter = 0u;
+    int all = 1;
+    for (int c = 0; c < k; ++c) all &= sc->done[c];
+    sc->all_done = all;
+    if (all && host_done) *(volatile int *)host_done = 1;
+  }
+}
+
+// p = z + beta_j p (columns not done)
+__global__ void __launch_bounds__(TPB) k_bdirection(int64_t total, int k, const double *__restrict__ z,
+                                                    double *__restrict__ p, const BScal *sc) {
+  if (sc->all_done) return;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(o % k);
+    if (!sc->done[j]) p[o] = fma(sc->beta[j], p[o], z[o]);
+  }
+}
+
+// z = L^-T (L^-1 y) for the k columns of the last level (one block).
+template <typename T>
+__global__ void k_bcoarse(int n, int k, const double *__restrict__ Li, const T *__restrict__ y, T *__restrict__ z,
+                          const int *__restrict__ done) {
+  if (*done) return;
+  extern __shared__ double sm[];
+  double *yy = sm, *w = sm + (size_t)n * k;
+  for (int o = threadIdx.x; o < n * k; o += blockDim.x) yy[o] = static_cast<double>(y[o]);
+  __syncthreads();
+  for (int o = threadIdx.x; o < n * k; o += blockDim.x) {
+    const int i = o / k, j = o % k;
+    double s = 0.0;
+    for (int c = 0; c <= i; ++c) s = fma(Li[(size_t)i * n + c], yy[c * k + j], s);
+    w[o] = s;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < n * k; o += blockDim.x) {
+    const int i = o / k, j = o % k;
+    double s = 0.0;
+    for (int c = i; c < n; ++c) s = fma(Li[(size_t)c * n + i], w[c * k + j], s);
+    z[o] = static_cast<T>(s);
+  }
+}
+
+template <typename T>
+__global__ void k_bcopy(int64_t total, const T *__restrict__ a, T *__restrict__ b) {
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x)
+    b[o] = a[o];
+}
+
+inline int grid_for(int64_t work) { return std::max(1, std::min<int>(ceil_div(work, TPB), MAX_GRID)); }
+
+template <int K, class Op>
+void launch_b(int n, int k, const DCsr &M, const Op &op, cudaStream_t s) {
+  k_brows<K, Op><<<grid_for((int64_t)n * K), TPB, 0, s>>>(n, k, M.rp, M.ci, op);
+  AMG_CHECK_LAUNCH();
+}
+
+// --------------------------------------------------------------- driver --
+template <typename T>
+const T *csr_vals(const DCsr &M);
+template <>
+const double *csr_vals<double>(const DCsr &M) { return M.v; }
+template <>
+const float *csr_vals<float>(const DCsr &M) { return M.v32; }
+template <typename TP>
+const TP *pr_vals(const DCsr &M);
+template <>
+const double *pr_vals<double>(const DCsr &M) { return M.v; }
+template <>
+const float *pr_vals<float>(const DCsr &M) { return M.v32; }
+template <>
+const __nv_bfloat16 *pr_vals<__nv_bfloat16>(const DCsr &M) { return M.v16; }
+template <typename T>
+const T *wdv(const Level &l);
+template <>
+const double *wdv<double>(const Level &l) { return l.wd; }
+template <>
+const float *wdv<float>(const Level &l) { return l.wd32; }
+
+// Work vectors of one batched solve (n_k x k per level, V-cycle precision).
+template <typename T>
+struct BWork {
+  std::vector<Buf<T>> y, s, r, z, w;
+};
+
+template <int K, typename T, typename TP>
+struct Batch {
+  amg_hierarchy *h;
+  int k;
+  BWork<T> *wk;
+  BScal *sc;
+  double *partials;
+  unsigned int *counter;
+  double *r, *zz, *p, *q;  // level-0 CG blocks (FP64)
+
+  void cycle(int lv, const int *done) {
+    cudaStream_t s = h->mem.stream;
+    Level &L = h->lev[lv];
+    const DCsr &A = L.A;
+    const int n = A.n;
+    const double bt = sizeof(T), bp = sizeof(TP);
+    const int64_t nk = (int64_t)n * k;
+    if (lv == h->nlevels - 1) {
+      ProfScope ps(s, AMG_K_COARSE, 8.0 * (double)n * n + 2.0 * bt * nk, lv);
+      const int th = std::min(1024, std::max(32, (int)((nk + 31) / 32 * 32)));
+      k_bcoarse<T><<<1, th, 2 * sizeof(double) * nk, s>>>(n, k, h->Linv, wk->y[lv].p, wk->z[lv].p, done);
+      AMG_CHECK_LAUNCH();
+      return;
+    }
+    const amg_params &prm = h->prm;
+    T *y = wk->y[lv].p, *sv = wk->s[lv].p, *r = wk->r[lv].p, *w = wk->w[lv].p;
+    const double abytes = (4.0 + bt) * (double)A.nnz + 4.0 * (n + 1);
+    for (int it = 1; it < prm.nu1; ++it) {
+      ProfScope ps(s, AMG_K_SOLVE_OTHER, abytes + 4.0 * bt * nk, lv);
+      launch_b<K>(n, k, A, BJacobi<T>{k, csr_vals<T>(A), wdv<T>(L), y, sv, w, done}, s);
+      std::swap(sv, w);
+    }
+    {
+      ProfScope ps(s, AMG_K_SMOOTH_RESID, abytes + 3.0 * bt * nk, lv);
+      launch_b<K>(n, k, A, BResid<T>{k, csr_vals<T>(A), sv, y, r, done}, s);
+    }
+    Level &C = h->lev[lv + 1];
+    const int nc = C.A.n;
+    const bool c_last = lv + 1 == h->nlevels - 1;
+    {
+      ProfScope ps(s, AMG_K_RESTRICT, (4.0 + bp) * (double)L.R.nnz + 4.0 * (nc + 1) + bt * nk + 3.0 * bt * nc * k, lv);
+      launch_b<K>(nc, k, L.R,
+                  BRestrict<T, TP>{k, pr_vals<TP>(L.R), r, c_last ? nullptr : wdv<T>(C), wk->y[lv + 1].p,
+                                   c_last ? nullptr : wk->s[lv + 1].p, c_last ? -1 : (prm.nu1 > 0 ? 1 : 0), done},
+                  s);
+    }
+    cycle(lv + 1, done);
+    {
+      ProfScope ps(s, AMG_K_PROLONG, (4.0 + bp) * (double)L.P.nnz + 4.0 * (n + 1) + 2.0 * bt * nk + bt * nc * k, lv);
+      launch_b<K>(n, k, L.P, BProlong<T, TP>{k, pr_vals<TP>(L.P), sv, wk->z[lv + 1].p, r, done}, s);
+    }
+    if (lv == 0) return;
+    T *t = r;
+    if (prm.nu2 == 0) {
+      k_bcopy<T><<<grid_for(nk), TPB, 0, s>>>(nk, t, wk->z[lv].p);
+      AMG_CHECK_LAUNCH();
+      return;
+    }
+    for (int it = 0; it < prm.nu2; ++it) {
+      const bool lastp = it == prm.nu2 - 1;
+      T *dst = lastp ? wk->z[lv].p : (t == r ? w : r);
+      ProfScope ps(s, lastp ? AMG_K_SMOOTH_POST : AMG_K_SOLVE_OTHER, abytes + 4.0 * bt * nk, lv);
+      launch_b<K>(n, k, A, BJacobi<T>{k, csr_vals<T>(A), wdv<T>(L), y, t, dst, done}, s);
+      t = dst;
+    }
+  }
+
+  void vcycle(int mode, int flexible, const int *done) {
+    cudaStream_t s = h->mem.stream;
+    Level &L0 = h->lev[0];
+    const DCsr &A = L0.A;
+    const int n = A.n;
+    const int64_t nk = (int64_t)n * k;
+    const T *y = wk->y[0].p;
+    const T *t;
+    bool sweep = true;
+    if (h->nlevels == 1) {
+      cycle(0, done);
+      t = wk->z[0].p;
+      sweep = false;
+    } else {
+      cycle(0, done);
+      T *tt = wk->r[0].p, *w = wk->w[0].p;
+      for (int it = 0; it + 1 < h->prm.nu2; ++it) {
+        launch_b<K>(n, k, A, BJacobi<T>{k, csr_vals<T>(A), wdv<T>(L0), y, tt, w, done}, s);
+        std::swap(tt, w);
+      }
+      t = tt;
+      sweep = h->prm.nu2 > 0;
+    }
+    ProfScope ps(s, AMG_K_SMOOTH_POST, (sweep ? 12.0 * A.nnz : 0.0) + 40.0 * nk, 0);
+    if (sweep)
+      launch_b<K>(n, k, A, BPost0<K, T, true>{k, csr_vals<T>(A), wdv<T>(L0), y, t, zz, r, q, p, mode, flexible, sc,
+                                                done, partials, counter}, s);
+    else
+      launch_b<K>(n, k, A, BPost0<K, T, false>{k, csr_vals<T>(A), wdv<T>(L0), y, t, zz, r, q, p, mode, flexible, sc,
+                                                 done, partials, counter}, s);
+  }
+};
+
+template <int K, typename T, typename TP>
+int batch_impl(amg_hierarchy *h, int k, const double *B, double *X, double rtol, int maxit, int *iters, int *status,
+               double *hist_out, int hist_cap) {
+  Mem &m = h->mem;
+  cudaStream_t s = m.stream;
+  const Level &L0 = h->lev[0];
+  const DCsr &A = L0.A;
+  const int n = A.n;
+  const int64_t nk = (int64_t)n * k;
+  const bool fp64 = std::is_same<T, double>::value;
+  BWork<T> wk;
+  for (int lv = 0; lv < h->nlevels; ++lv) {
+    const size_t cnt = (size_t)h->lev[lv].A.n * k;
+    wk.y.emplace_back(m, cnt);
+    wk.z.emplace_back(m, cnt);
+    const bool work = lv < h->nlevels - 1 || lv == 0;
+    wk.s.emplace_back(m, work ? cnt : 1);
+    wk.r.emplace_back(m, work ? cnt : 1);
+    wk.w.emplace_back(m, work ? cnt : 1);
+  }
+  Buf<double> r(m, nk), zz(m, nk), p(m, nk), q(m, nk);
+  Buf<BScal> scb(m, 1);
+  Buf<double> partials(m, (size_t)MAX_GRID * 3 * KMAX);
+  Buf<unsigned int> counter(m, 1);
+  Buf<double> hist(m, (size_t)(maxit + 1) * k);
+  AMG_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
+  BScal init{};
+  init.maxit = maxit;
+  init.k = k;
+  AMG_CUDA(cudaMemcpyAsync(scb.p, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  *h->h_done = 0;
+  const int *done = &scb.p->all_done;
+  // FP64: the V-cycle input y0 is the CG residual block itself
+  T *y0 = fp64 ? reinterpret_cast<T *>(r.p) : wk.y[0].p;
+  if (fp64) {
+    wk.y[0].reset();
+    wk.y[0].p = y0;  // alias, not owned
+    wk.y[0].m = nullptr;
+  }
+  T *s0 = wk.s[0].p;
+  const bool pre = h->prm.nu1 > 0;
+  Batch<K, T, TP> bt{h, k, &wk, scb.p, partials.p, counter.p, r.p, zz.p, p.p, q.p};
+  {
+    ProfScope ps(s, AMG_K_SOLVE_OTHER, 12.0 * A.nnz + 40.0 * nk, 0);
+    launch_b<K>(n, k, A, BInit<K, T>{k, A.v, X, B, r.p, wdv<T>(L0), y0, s0, !fp64, pre, rtol, scb.p, hist.p, maxit + 1,
+                                     partials.p, counter.p}, s);
+  }
+  const int flexible = fp64 ? 0 : 1;
+  bt.vcycle(BPOST_FIRST, flexible, done);
+  for (int it = 1; it <= maxit; ++it) {
+    {
+      ProfScope ps(s, AMG_K_SPMV_DOT, 12.0 * A.nnz + 4.0 * (n + 1) + 24.0 * nk, 0);
+      launch_b<K>(n, k, A, BSpmvDot<K>{k, A.v, p.p, q.p, scb.p, partials.p, counter.p}, s);
+    }
+    {
+      ProfScope ps(s, AMG_K_PCG_UPDATE, (48.0 + 3.0 * sizeof(T)) * nk, 0);
+      k_bupdate<T><<<grid_for(nk), TPB, 0, s>>>(n, k, X, r.p, p.p, q.p, wdv<T>(L0), y0, s0, !fp64, pre, scb.p, hist.p,
+                                                maxit + 1, h->d_done, partials.p, counter.p);
+      AMG_CHECK_LAUNCH();
+    }
+    bt.vcycle(BPOST_ITER, flexible, done);
+    {
+      ProfScope ps(s, AMG_K_DIRECTION, 24.0 * nk, 0);
+      k_bdirection<<<grid_for(nk), TPB, 0, s>>>(nk, k, zz.p, p.p, scb.p);
+      AMG_CHECK_LAUNCH();
+    }
+    AMG_CUDA(cudaEventRecord(h->iter_ev[it & 1], s));
+    if (it > 1) {
+      AMG_CUDA(cudaEventSynchronize(h->iter_ev[(it - 1) & 1]));
+      if (*(volatile int *)h->h_done) break;
+    }
+  }
+  BScal out{};
+  AMG_CUDA(cudaMemcpyAsync(&out, scb.p, sizeof(out), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  prof_collect(s);
+  int worst = AMG_OK;
+  for (int j = 0; j < k; ++j) {
+    if (iters) iters[j] = out.iters[j];
+    if (status) status[j] = out.status[j];
+    if (out.status[j] != AMG_OK && worst == AMG_OK) worst = out.status[j];
+    if (!out.done[j] && worst == AMG_OK) worst = AMG_ERR_NO_CONVERGENCE;
+  }
+  if (hist_out && hist_cap > 0) {
+    const int rows = std::min(hist_cap, maxit + 1);
+    AMG_CUDA(cudaMemcpy(hist_out, hist.p, sizeof(double) * (size_t)rows * k, cudaMemcpyDeviceToHost));
+  }
+  return worst;
+}
+
+template <typename T, typename TP>
+int batch_dispatch(amg_hierarchy *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
+                   int *status, double *hist, int hist_cap) {
+  if (k <= 1) return batch_impl<1, T, TP>(h, k, B, X, rtol, maxit, iters, status, hist, hist_cap);
+  if (k <= 2) return batch_impl<2, T, TP>(h, k, B, X, rtol, maxit, iters, status, hist, hist_cap);
+  if (k <= 4) return batch_impl<4, T, TP>(h, k, B, X, rtol, maxit, iters, status, hist, hist_cap);
+  if (k <= 8) return batch_impl<8, T, TP>(h, k, B, X, rtol, maxit, iters, status, hist, hist_cap);
+  if (k <= 16) return batch_impl<16, T, TP>(h, k, B, X, rtol, maxit, iters, status, hist, hist_cap);
+  return batch_impl<32, T, TP>(h, k, B, X, rtol, maxit, iters, status, hist, hist_cap);
+}
+
+}  // namespace
+
+int pcg_solve_batch(amg_hierarchy *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
+                    int *status, double *hist, int hist_cap) {
+  if (h->nlevels > 0) {
+    const int nL = h->nL;
+    if ((size_t)2 * sizeof(double) * nL * k > 200 * 1024) {
+      set_error("last level of %d rows too large for a %d-column batch", nL, k);
+      throw Status{AMG_ERR_UNSUPPORTED};
+    }
+    static bool attr = false;
+    if (!attr) {
+      AMG_CUDA(cudaFuncSetAttribute(k_bcoarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      AMG_CUDA(cudaFuncSetAttribute(k_bcoarse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr = true;
+    }
+  }
+  switch (h->prm.precision) {
+    case AMG_PREC_FP64: return batch_dispatch<double, double>(h, k, B, X, rtol, maxit, iters, status, hist, hist_cap);
+    case AMG_PREC_FP32: return batch_dispatch<float, float>(h, k, B, X, rtol, maxit, iters, status, hist, hist_cap);
+    default: return batch_dispatch<float, __nv_bfloat16>(h, k, B, X, rtol, maxit, iters, status, hist, hist_cap);
+  }
+}
+
+}  // namespace amg

@@ -326,3 +326,80 @@ def test_setup_rejects_bad_input(mutate, code):
     with pytest.raises(amg.AmgError) as e:
         amg.Hierarchy(bad, max_levels=1 if mutate == "indefinite" else 25)
     assert e.value.code == code
+
+
+# ------------------------------------------------------ multiple right-hand sides --
+
+def _batch_rhs(n, k, seed):
+    return np.stack([pr.uniform(n, seed + j) for j in range(k)], axis=1)
+
+
+@pytest.mark.parametrize("name,k", [("diffusion3d_20", 3), ("poisson2d_64", 8), ("graph_laplacian_700", 1)])
+def test_batch_fp64_parity(name, k):
+    """Each column of a batched FP64 solve follows the oracle's single solve of that column."""
+    A = CASES[name]()
+    Bm = _batch_rhs(A.n, k, 21)
+    ho = O.Hierarchy(A, seed=0)
+    hg = amg.Hierarchy(A, seed=0)
+    X, iters, stats, st, hist = hg.solve_batch(dev(Bm), rtol=1e-8, hist=True)
+    assert st == amg.AMG_OK and stats == [0] * k
+    Xg = X.cpu().numpy().reshape(A.n, k)
+    for j in range(k):
+        sto, xo, ito, ho_, _ = ho.pcg(Bm[:, j], rtol=1e-8)
+        assert iters[j] == ito
+        assert np.linalg.norm(Xg[:, j] - xo) <= 1e-9 * np.linalg.norm(xo)
+        assert np.allclose(hist[: ito + 1, j], ho_, rtol=1e-6, atol=0)
+
+
+def test_batch_matches_single_gpu_solves():
+    A = LARGE["diffusion3d_40"]()
+    k = 5
+    Bm = _batch_rhs(A.n, k, 3)
+    hg = amg.Hierarchy(A, seed=1)
+    X, iters, stats, st, _ = hg.solve_batch(dev(Bm), rtol=1e-8)
+    Xg = X.cpu().numpy()
+    for j in range(k):
+        xs, its, sts, _ = hg.solve(dev(Bm[:, j]), rtol=1e-8)
+        assert iters[j] == its
+        assert np.linalg.norm(Xg[:, j] - xs.cpu().numpy()) <= 1e-10 * np.linalg.norm(Xg[:, j])
+
+
+@pytest.mark.parametrize("prec", [amg.PREC_FP32, amg.PREC_FP32_BF16PR])
+def test_batch_mixed_precision_16_columns(prec):
+    A, rng = pr.diffusion3d(24, 2.0, 2)
+    k = 16
+    Bm = _batch_rhs(A.n, k, 40)
+    hg = amg.Hierarchy(A, seed=0, precision=prec)
+    X, iters, stats, st, _ = hg.solve_batch(dev(Bm), rtol=1e-8)
+    assert st == amg.AMG_OK
+    Xg = X.cpu().numpy()
+    ho = O.Hierarchy(A, seed=0)
+    D = A.to_dense() if A.n <= 20000 else None
+    for j in (0, 7, 15):
+        _, xo, ito, _, _ = ho.pcg(Bm[:, j], rtol=1e-8)
+        assert np.linalg.norm(Xg[:, j] - xo) <= 1e-6 * np.linalg.norm(xo)
+        assert abs(iters[j] - ito) <= max(3, ito // 5)
+        res = np.linalg.norm(Bm[:, j] - A.matvec(Xg[:, j]))
+        assert res < 1.01e-8 * np.linalg.norm(Bm[:, j]) * 10  # true residual near the recursive one
+
+
+def test_batch_column_masks():
+    """A zero column converges at iteration 0 and stays zero; the others keep going."""
+    A = CASES["poisson2d_64"]()
+    Bm = _batch_rhs(A.n, 4, 5)
+    Bm[:, 2] = 0.0
+    hg = amg.Hierarchy(A)
+    X, iters, stats, st, _ = hg.solve_batch(dev(Bm), rtol=1e-10)
+    assert st == amg.AMG_OK and iters[2] == 0 and min(iters[0], iters[1], iters[3]) > 0
+    assert torch.count_nonzero(X[:, 2]) == 0
+
+
+def test_batch_limits():
+    A = CASES["poisson2d_64"]()
+    hg = amg.Hierarchy(A)
+    lib = amg.load()
+    Bm = dev(_batch_rhs(A.n, 2, 1))
+    assert lib.amg_pcg_solve_batch(hg.h, 33, Bm.data_ptr(), Bm.data_ptr(), 1e-8, 10, None, None, None, None, 0) \
+        == amg.AMG_ERR_INVALID_ARG
+    X, iters, stats, st, _ = hg.solve_batch(dev(_batch_rhs(A.n, 32, 2)), rtol=1e-8)
+    assert st == amg.AMG_OK and len(iters) == 32
