@@ -80,13 +80,17 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+KERNEL_SOURCE = {"spgemm": "spgemm.cu", "strength": "setup.cu", "pmis": "setup.cu", "interp": "setup.cu",
+                 "transpose": "setup.cu", "setup_other": "setup.cu"}
+
+
 def traffic_for(kernel_class: str, level):
     """DRAM bytes per launch of a kernel class (on a level) from the committed ncu
-    summary, if it was captured on the current kernel source (else None)."""
+    summary, if it was captured on the current source of that kernel (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.md")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_2102_07417_gb300", "csrc", "solve.cu")
+    src = os.path.join(ROOT, "paper_2102_07417_gb300", "csrc", KERNEL_SOURCE.get(kernel_class, "solve.cu"))
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     want = f"{kernel_class}@{level}" if level is not None else kernel_class
     for line in open(path):
