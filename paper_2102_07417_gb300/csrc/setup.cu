@@ -338,6 +338,218 @@ __global__ void k_interp_fill(int n, const int *__restrict__ rp, const int *__re
   }
 }
 
+// ------------------------------------------- warp-per-row variants --
+// Used on small levels whose rows are long (mean length >= 12): a warp per row,
+// lanes over the row's entries, so the dependent loads of one row are issued
+// in parallel instead of walked by one thread.  Results are identical to the
+// thread-per-row kernels (maxima, counts and flags do not depend on order;
+// the interpolation's FP64 sums are still formed left to right by one lane).
+#define WARP_ROW_BEGIN                                                              \
+  const int lane = threadIdx.x & 31;                                                \
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);       \
+  if (i >= n) return;
+
+__global__ void k_strength_w(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const double *__restrict__ a, double theta, uint8_t *__restrict__ S) {
+  WARP_ROW_BEGIN
+  const int b = rp[i], e = rp[i + 1];
+  double m = 0.0;
+  bool have = false;
+  for (int p = b + lane; p < e; p += 32) {
+    if (ci[p] == i) continue;
+    const double t = -a[p];
+    if (!have || t > m) m = t;
+    have = true;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const double om = __shfl_xor_sync(0xffffffffu, m, o);
+    const bool oh = __shfl_xor_sync(0xffffffffu, (int)have, o) != 0;
+    if (oh && (!have || om > m)) m = om;
+    have = have || oh;
+  }
+  const double thr = __dmul_rn(theta, m);
+  for (int p = b + lane; p < e; p += 32) S[p] = (have && m > 0.0 && ci[p] != i && -a[p] >= thr) ? 1 : 0;
+}
+
+__global__ void k_pmis_init_w(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                              const uint8_t *__restrict__ S, uint8_t *__restrict__ ST, double *__restrict__ lam,
+                              int8_t *__restrict__ st, uint64_t seed, int level, int *flags) {
+  WARP_ROW_BEGIN
+  int cnt = 0;
+  for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+    const int j = ci[p];
+    uint8_t t = 0;
+    if (j != i) {
+      const int q = find_col(ci, rp[j], rp[j + 1], i);
+      if (q < 0) flags[2] = 1;
+      else t = S[q];
+    }
+    ST[p] = t;
+    cnt += t;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) {
+    const uint64_t c = ((uint64_t)(uint32_t)level << 32) + (uint64_t)(uint32_t)i + 1ull;
+    const double u = (double)(splitmix64_at(seed, c) >> 11) * 0x1.0p-53;
+    lam[i] = __dadd_rn((double)cnt, u);
+    st[i] = cnt == 0 ? ST_F : ST_U;
+  }
+}
+
+__global__ void k_pmis_select_w(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                const uint8_t *__restrict__ S, const uint8_t *__restrict__ ST,
+                                const double *__restrict__ lam, const int8_t *__restrict__ st_old,
+                                int8_t *__restrict__ st_new) {
+  WARP_ROW_BEGIN
+  const int8_t s0 = st_old[i];
+  if (s0 != ST_U) {
+    if (lane == 0) st_new[i] = s0;
+    return;
+  }
+  const double li = lam[i];
+  bool beaten = false;
+  for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+    if (!(S[p] | ST[p])) continue;
+    const int j = ci[p];
+    if (st_old[j] != ST_U) continue;
+    const double lj = lam[j];
+    if (lj > li || (lj == li && j > i)) beaten = true;
+  }
+  beaten = __any_sync(0xffffffffu, beaten);
+  if (lane == 0) st_new[i] = beaten ? ST_U : ST_NEWC;
+}
+
+__global__ void k_pmis_update_w(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                const uint8_t *__restrict__ S, const int8_t *__restrict__ st_new,
+                                int8_t *__restrict__ st_next, int *undecided) {
+  __shared__ int und_blk;
+  if (threadIdx.x == 0) und_blk = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i < n) {
+    const int8_t s0 = st_new[i];
+    if (s0 == ST_U) {
+      bool f = false;
+      for (int p = rp[i] + lane; p < rp[i + 1]; p += 32)
+        if (S[p] && st_new[ci[p]] == ST_NEWC) f = true;
+      f = __any_sync(0xffffffffu, f);
+      if (lane == 0) {
+        st_next[i] = f ? ST_F : ST_U;
+        if (!f) atomicAdd(&und_blk, 1);
+      }
+    } else if (lane == 0) {
+      st_next[i] = s0 == ST_NEWC ? ST_C : s0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && und_blk) atomicAdd(undecided, und_blk);
+}
+
+__global__ void k_interp_count_w(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                 const uint8_t *__restrict__ S, const int8_t *__restrict__ cf,
+                                 int *__restrict__ cnt) {
+  WARP_ROW_BEGIN
+  if (cf[i]) {
+    if (lane == 0) cnt[i] = 1;
+    return;
+  }
+  int c = 0;
+  for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+    const int j = ci[p];
+    if (j != i && S[p] && cf[j]) ++c;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) cnt[i] = c;
+}
+
+// Direct interpolation, warp per row: lanes stage a chunk of 32 entries in
+// shared memory, lane 0 adds them in ascending column order (the canonical
+// order of the thread-per-row kernel), then lanes form the weights.
+__global__ void __launch_bounds__(256) k_interp_fill_w(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                       const double *__restrict__ a, const uint8_t *__restrict__ S,
+                                                       const int8_t *__restrict__ cf, const int *__restrict__ cidx,
+                                                       const int *__restrict__ prp, int *__restrict__ pci,
+                                                       double *__restrict__ pv) {
+  __shared__ double sv[8][32];
+  __shared__ uint8_t sk[8][32];  // bit 0: off-diagonal, bit 1: in P_i (strong C neighbour)
+  const int w = threadIdx.x >> 5;
+  WARP_ROW_BEGIN
+  int pos = prp[i];
+  if (cf[i]) {
+    if (lane == 0) {
+      pci[pos] = cidx[i];
+      pv[pos] = 1.0;
+    }
+    return;
+  }
+  const int b = rp[i], e = rp[i + 1];
+  double aii = 0.0, sn_neg = 0.0, sn_pos = 0.0, sp_neg = 0.0, sp_pos = 0.0;
+  int np = 0;
+  for (int c0 = b; c0 < e; c0 += 32) {
+    const int p = c0 + lane;
+    if (p < e) {
+      const int j = ci[p];
+      sv[w][lane] = a[p];
+      sk[w][lane] = (uint8_t)((j != i ? 1 : 0) | ((j != i && S[p] && cf[j]) ? 2 : 0));
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const int cnt = min(32, e - c0);
+      for (int t = 0; t < cnt; ++t) {
+        const double v = sv[w][t];
+        const uint8_t k = sk[w][t];
+        if (!(k & 1)) {
+          aii = v;
+          continue;
+        }
+        if (v < 0.0) sn_neg = __dadd_rn(sn_neg, v);
+        if (v > 0.0) sn_pos = __dadd_rn(sn_pos, v);
+        if (k & 2) {
+          ++np;
+          if (v < 0.0) sp_neg = __dadd_rn(sp_neg, v);
+          if (v > 0.0) sp_pos = __dadd_rn(sp_pos, v);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  np = __shfl_sync(0xffffffffu, np, 0);
+  if (np == 0) return;
+  double alpha = 0.0, beta = 0.0, at = 0.0;
+  if (lane == 0) {
+    alpha = sp_neg != 0.0 ? __ddiv_rn(sn_neg, sp_neg) : 0.0;
+    beta = sp_pos != 0.0 ? __ddiv_rn(sn_pos, sp_pos) : 0.0;
+    at = sp_pos != 0.0 ? aii : __dadd_rn(aii, sn_pos);
+  }
+  alpha = __shfl_sync(0xffffffffu, alpha, 0);
+  beta = __shfl_sync(0xffffffffu, beta, 0);
+  at = __shfl_sync(0xffffffffu, at, 0);
+  for (int c0 = b; c0 < e; c0 += 32) {
+    const int p = c0 + lane;
+    bool sel = false;
+    int j = 0;
+    if (p < e) {
+      j = ci[p];
+      sel = j != i && S[p] && cf[j];
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, sel);
+    if (sel) {
+      const double v = a[p];
+      double wv = 0.0;
+      if (v < 0.0) wv = __ddiv_rn(-__dmul_rn(alpha, v), at);
+      if (v > 0.0) wv = __ddiv_rn(-__dmul_rn(beta, v), at);
+      const int q = pos + __popc(bal & ((1u << lane) - 1u));
+      pci[q] = cidx[j];
+      pv[q] = wv;
+    }
+    pos += __popc(bal);
+  }
+}
+
 // ---------------------------------------------------------- transpose --
 __global__ void k_col_count(int64_t nnz, const int *__restrict__ ci, int *__restrict__ cnt) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -555,6 +767,12 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     const DCsr &A = L.A;
     const int n = A.n;
     bool last = n <= prm.max_coarse || k == prm.max_levels - 1;
+    // Long rows on a level too small to fill the GPU with a thread per row:
+    // the warp-per-row kernels (the interpolation's serial FP64 sums only on
+    // the smallest levels, where FP64 issue slots are not the limit).
+    const bool wide = (double)A.nnz >= 12.0 * n && n < (1 << 18);
+    const bool wide_interp = wide && n < (1 << 15);
+    const int gw = ceil_div((int64_t)n * 32, TPB);
     Buf<uint8_t> S, ST;
     Buf<int> cidx;
     int nc = 0;
@@ -568,12 +786,14 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       const double nz = (double)A.nnz, rows = 4.0 * (n + 1);
       {
         ProfScope ps(s, AMG_K_STRENGTH, rows + 13.0 * nz);
-        k_strength<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
+        if (wide) k_strength_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
+        else k_strength<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
         AMG_CHECK_LAUNCH();
       }
       {
         ProfScope ps(s, AMG_K_STRENGTH, rows + 6.0 * nz + 9.0 * n);
-        k_pmis_init<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
+        if (wide) k_pmis_init_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
+        else k_pmis_init<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
         AMG_CHECK_LAUNCH();
       }
       read_flags(m, fl);
@@ -583,12 +803,14 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
         AMG_CUDA(cudaMemsetAsync(und.p, 0, sizeof(int), s));
         {
           ProfScope ps(s, AMG_K_PMIS, rows + 6.0 * nz + 10.0 * n);
-          k_pmis_select<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, st1.p);
+          if (wide) k_pmis_select_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, st1.p);
+          else k_pmis_select<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, st1.p);
           AMG_CHECK_LAUNCH();
         }
         {
           ProfScope ps(s, AMG_K_PMIS, rows + 5.0 * nz + 2.0 * n);
-          k_pmis_update<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, st1.p, st0.p, und.p);
+          if (wide) k_pmis_update_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, S.p, st1.p, st0.p, und.p);
+          else k_pmis_update<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, st1.p, st0.p, und.p);
           AMG_CHECK_LAUNCH();
         }
         if (read_int(m, und.p) == 0) break;
@@ -638,7 +860,8 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       Buf<int> pcnt(m, n);
       {
         ProfScope ps(s, AMG_K_INTERP, 4.0 * (n + 1) + 5.0 * A.nnz + 5.0 * n);
-        k_interp_count<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, L.cf, pcnt.p);
+        if (wide) k_interp_count_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, S.p, L.cf, pcnt.p);
+        else k_interp_count<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, L.cf, pcnt.p);
         AMG_CHECK_LAUNCH();
       }
       P.n = n;
@@ -649,7 +872,8 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       P.v = m.get_n<double>(std::max<int64_t>(P.nnz, 1));
       {
         ProfScope ps(s, AMG_K_INTERP, 8.0 * (n + 1) + 13.0 * A.nnz + 5.0 * n + 12.0 * P.nnz);
-        k_interp_fill<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, P.rp, P.ci, P.v);
+        if (wide_interp) k_interp_fill_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, P.rp, P.ci, P.v);
+        else k_interp_fill<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, P.rp, P.ci, P.v);
         AMG_CHECK_LAUNCH();
       }
     }
