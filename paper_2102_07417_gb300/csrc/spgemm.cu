@@ -19,7 +19,8 @@
 //                          (lane order = p order, so the sum is canonical);
 //   tier 1-5  ub <= 64 ... 1024   a warp per row, a shared-memory hash set of
 //                          2 ub_max slots (128 ... 2048), keys bitonic-sorted,
-//                          then the values summed p by p into shared memory;
+//                          products staged in shared memory and summed 32 at a
+//                          time, equal columns grouped and added in p order;
 //   tier 6    ub <= 4096   a block per row, 8192-slot table in shared memory;
 //   tier 7    larger       a block per row, table in a global scratch slice.
 #include <cuda_runtime.h>
@@ -171,6 +172,48 @@ __global__ void __launch_bounds__(TPB) k_tier_scatter(int m, const int8_t *__res
   }
 }
 
+// ------------------------------------------------- warp row helpers ----
+// Metadata of one chunk of up to 32 entries of X row [c0, xe): lane l holds
+// entry c0 + l's Y row start and length, the X value, and the exclusive
+// prefix of the lengths; *total is the chunk's number of products.
+struct XChunk {
+  int ys, len, excl;
+  double xv;
+};
+
+__device__ __forceinline__ XChunk x_chunk(int c0, int xe, const int *__restrict__ xci, const double *__restrict__ xv,
+                                          const int *__restrict__ yrp, int lane, int *total) {
+  XChunk c{0, 0, 0, 0.0};
+  const int p = c0 + lane;
+  if (p < xe) {
+    const int k = xci[p];
+    c.ys = yrp[k];
+    c.len = yrp[k + 1] - c.ys;
+    c.xv = xv[p];
+  }
+  int incl = c.len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  c.excl = incl - c.len;
+  *total = __shfl_sync(FULL, incl, 31);
+  return c;
+}
+
+// Source lane (X entry) of product u of a chunk: the last lane whose
+// exclusive prefix is <= u (it always has a nonzero length).  All lanes call.
+__device__ __forceinline__ int x_source(const XChunk &c, int u) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step; step >>= 1) {
+    const int e = __shfl_sync(FULL, c.excl, lo + step);
+    if (e <= u) lo += step;
+  }
+  return lo;
+}
+
 // ---------------------------------------------------------- tier 0 ----
 __global__ void __launch_bounds__(TPB) k_spgemm_reg(const int *__restrict__ rows, int nrows,
                                                     const int *__restrict__ xrp, const int *__restrict__ xci,
@@ -182,18 +225,23 @@ __global__ void __launch_bounds__(TPB) k_spgemm_reg(const int *__restrict__ rows
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (int r = gw; r < nrows; r += nw) {
     const int i = rows[r];
+    const int xb = xrp[i], xe = xrp[i + 1];
     int key = INT_MAX;
     double val = 0.0;
-    int o = 0;
-    for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
-      const int k = xci[p];
-      const int yb = yrp[k], len = yrp[k + 1] - yb;
-      if (lane >= o && lane < o + len) {
-        const int q = yb + lane - o;
+    int o = 0;  // products placed so far (ub <= 32, so product t sits in lane t)
+    for (int c0 = xb; c0 < xe; c0 += 32) {
+      int total;
+      const XChunk c = x_chunk(c0, xe, xci, xv, yrp, lane, &total);
+      const int u = lane - o;
+      const int src = x_source(c, u < 0 ? 0 : u);
+      const int ys = __shfl_sync(FULL, c.ys, src), ex = __shfl_sync(FULL, c.excl, src);
+      const double xs = __shfl_sync(FULL, c.xv, src);
+      if (u >= 0 && u < total) {
+        const int q = ys + u - ex;
         key = yci[q];
-        val = __dmul_rn(xv[p], yv[q]);
+        val = __dmul_rn(xs, yv[q]);
       }
-      o += len;
+      o += total;
     }
     const bool valid = lane < o;
     const unsigned grp = __match_any_sync(FULL, key);
@@ -208,8 +256,8 @@ __global__ void __launch_bounds__(TPB) k_spgemm_reg(const int *__restrict__ rows
     double acc = 0.0;
     unsigned mm = grp;
     for (int it = 0; it < maxg; ++it) {
-      const int src = mm ? __ffs(mm) - 1 : lane;
-      const double v = __shfl_sync(FULL, val, src);
+      const int sl = mm ? __ffs(mm) - 1 : lane;
+      const double v = __shfl_sync(FULL, val, sl);
       if (leader && mm) acc = __dadd_rn(acc, v);
       mm &= mm - 1u;
     }
@@ -223,8 +271,14 @@ __global__ void __launch_bounds__(TPB) k_spgemm_reg(const int *__restrict__ rows
 }
 
 // -------------------------------------------------------- tiers 1-5 ----
-// Shared memory per warp: TAB ints (hash table, then reused as TAB/2 double
-// accumulators) + TAB/2 ints (the row's distinct columns, then sorted).
+// Shared memory per warp (TAB = 2 x the tier's largest ub):
+//   table[TAB] hash set (then TAB/2 double accumulators), keys[TAB/2] the
+//   row's distinct columns (then sorted), pk[TAB/2] / pv[TAB/2] the row's
+//   products in (p, q) order: column and rounded product x_ip * y_qJ.
+// The products are fetched in one flattened pass (all lanes busy), then summed
+// into the accumulators 32 at a time: lanes holding the same column form a
+// group (__match_any_sync) whose lowest lane adds the members in lane order,
+// which is p order -- the canonical order.
 template <int TAB>
 __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ rows, int nrows,
                                                      const int *__restrict__ xrp, const int *__restrict__ xci,
@@ -235,8 +289,10 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
   constexpr int HALF = TAB / 2;
   extern __shared__ __align__(16) int smem_i[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int *table = smem_i + warp * (TAB + HALF);
+  int *table = smem_i + warp * (3 * TAB);
   int *keys = table + TAB;
+  int *pk = keys + HALF;
+  double *pv = reinterpret_cast<double *>(pk + HALF);
   double *acc = reinterpret_cast<double *>(table);
   const int gw = blockIdx.x * WARPS + warp, nw = gridDim.x * WARPS;
   for (int r = gw; r < nrows; r += nw) {
@@ -244,9 +300,24 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
     for (int t = lane; t < TAB; t += 32) table[t] = -1;
     __syncwarp();
     const int xb = xrp[i], xe = xrp[i + 1];
-    for (int p = xb; p < xe; ++p) {
-      const int k = xci[p];
-      for (int q = yrp[k] + lane; q < yrp[k + 1]; q += 32) hash_insert(table, TAB - 1, yci[q], flags);
+    int nprod = 0;
+    for (int c0 = xb; c0 < xe; c0 += 32) {
+      int total;
+      const XChunk c = x_chunk(c0, xe, xci, xv, yrp, lane, &total);
+      for (int u0 = 0; u0 < total; u0 += 32) {
+        const int u = u0 + lane;
+        const int src = x_source(c, u);
+        const int ys = __shfl_sync(FULL, c.ys, src), ex = __shfl_sync(FULL, c.excl, src);
+        const double xs = __shfl_sync(FULL, c.xv, src);
+        if (u < total) {
+          const int q = ys + u - ex;
+          const int key = yci[q];
+          pk[nprod + u] = key;
+          pv[nprod + u] = __dmul_rn(xs, yv[q]);
+          hash_insert(table, TAB - 1, key, flags);
+        }
+      }
+      nprod += total;
     }
     __syncwarp();
     int count = 0;
@@ -275,13 +346,23 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
       }
     for (int e = lane; e < count; e += 32) acc[e] = 0.0;
     __syncwarp();
-    for (int p = xb; p < xe; ++p) {
-      const int k = xci[p];
-      const double x = xv[p];
-      for (int q = yrp[k] + lane; q < yrp[k + 1]; q += 32) {
-        const int pos = lower_bound(keys, count, yci[q]);
-        acc[pos] = __dadd_rn(acc[pos], __dmul_rn(x, yv[q]));
+    for (int t0 = 0; t0 < nprod; t0 += 32) {
+      const int t = t0 + lane;
+      const bool valid = t < nprod;
+      const int pos = valid ? lower_bound(keys, count, pk[t]) : -1 - lane;
+      const double v = valid ? pv[t] : 0.0;
+      const unsigned grp = __match_any_sync(FULL, pos);
+      const bool leader = valid && (__ffs(grp) - 1) == lane;
+      const int maxg = (int)__reduce_max_sync(FULL, leader ? (unsigned)__popc(grp) : 0u);
+      double a = leader ? acc[pos] : 0.0;
+      unsigned mm = grp;
+      for (int it = 0; it < maxg; ++it) {
+        const int sl = mm ? __ffs(mm) - 1 : lane;
+        const double w = __shfl_sync(FULL, v, sl);
+        if (leader && mm) a = __dadd_rn(a, w);
+        mm &= mm - 1u;
       }
+      if (leader) acc[pos] = a;
       __syncwarp();
     }
     const int base = off[i];
@@ -384,7 +465,7 @@ __global__ void __launch_bounds__(TPB) k_compact(int m, const int *__restrict__ 
 
 template <int TAB>
 constexpr size_t hash_smem() {
-  return (size_t)WARPS * (TAB + TAB / 2) * sizeof(int);
+  return (size_t)WARPS * 3 * TAB * sizeof(int);
 }
 constexpr size_t block_smem = (size_t)(BTAB + BTAB / 2) * sizeof(int);
 
