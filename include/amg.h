@@ -237,6 +237,10 @@ void amg_free(amg_hierarchy *h);
 #define AMG_K_SETUP_OTHER 14  /* set-up: scans, dense factor, casts, diagonal */
 #define AMG_K_COUNT 15
 int amg_profile_enable(int32_t on);
+/* Restricts recording to launches of kernel class `kernel` on level `level`
+ * (-1: any level); kernel = -1 records every launch again (the default).
+ * Recording one class keeps the event overhead out of the other launches. */
+int amg_profile_filter(int32_t kernel, int32_t level);
 int amg_profile_read(int32_t kernel, int32_t level, int64_t *launches, double *ms, double *bytes);
 
 /* Number of libamg kernel launches in this process so far. */

@@ -36,7 +36,7 @@ SETUP_KERNELS = KERNEL_NAMES[9:]
 # Names exported by the C ABI (each declared in include/amg.h).
 EXPORTS = ["amg_params_default", "amg_setup", "amg_pcg_solve", "amg_pcg_solve_batch", "amg_vcycle_apply", "amg_spmv", "amg_solve",
            "amg_hierarchy_info", "amg_hierarchy_export", "amg_hierarchy_bytes", "amg_free", "amg_profile_enable",
-           "amg_profile_read", "amg_launch_count", "amg_status_string", "amg_last_error",
+           "amg_profile_read", "amg_profile_filter", "amg_launch_count", "amg_status_string", "amg_last_error",
            "amg_spmv_dot_noalloc"]
 
 
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True):
     L.amg_free.restype = None
     L.amg_profile_enable.argtypes = [i32]
     L.amg_profile_read.argtypes = [i32, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]
+    L.amg_profile_filter.argtypes = [i32, i32]
     L.amg_launch_count.argtypes = []
     L.amg_launch_count.restype = C.c_int64
     L.amg_status_string.argtypes = [C.c_int]
@@ -296,6 +297,12 @@ def profile(on: bool):
     check(load().amg_profile_enable(1 if on else 0), "amg_profile_enable")
 
 
+def profile_filter(kernel: str | None = None, level: int = -1):
+    """Record only launches of one kernel class (name from KERNEL_NAMES) on one level (-1: any); None: all."""
+    k = -1 if kernel is None else KERNEL_NAMES.index(kernel)
+    check(load().amg_profile_filter(k, level), "amg_profile_filter")
+
+
 def profile_read(level: int = -1) -> dict:
     """Per kernel class (on one level, or all with -1): launches, summed event time (ms), algorithmic bytes."""
     out = {}
@@ -314,7 +321,7 @@ def launch_count() -> int:
 def solve(A, b, x0=None, params: Params | None = None, rtol: float = 1e-8, maxit: int = 500, stream=None,
           torch_allocator: bool = True, **kw):
     """One-call set-up + solve (amg_solve).  Host (numpy) or device (torch CUDA) inputs.
-    Returns (x, Result)."""
+    A host x0 (contiguous float64) receives the solution in place.  Returns (x, Result)."""
     import torch
 
     L = load()
@@ -334,7 +341,7 @@ def solve(A, b, x0=None, params: Params | None = None, rtol: float = 1e-8, maxit
         ptrs = (rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
         nnz = int(rp[-1])
         bb = np.ascontiguousarray(b, np.float64)
-        x = np.zeros(A.n) if x0 is None else np.ascontiguousarray(x0, np.float64).copy()
+        x = np.zeros(A.n) if x0 is None else np.ascontiguousarray(x0, np.float64)
         keep.append(bb)
         bp, xp = bb.ctypes.data, x.ctypes.data
     csr = Csr(int(A.n), nnz, *ptrs, 1 if on_dev else 0)

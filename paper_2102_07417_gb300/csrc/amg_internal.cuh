@@ -152,6 +152,7 @@ struct Level {
 // and hierarchy level (index kMaxLevels: launches that belong to no level).
 struct Profile {
   bool on = false;
+  int only_kind = -1, only_level = -1;  // amg_profile_filter
   std::vector<cudaEvent_t> ev;  // pool of events, two per recorded launch
   std::vector<int> kind;        // kernel class * (kMaxLevels + 1) + level slot of each pair
   std::vector<double> bytes;    // algorithmic bytes of each recorded pair

@@ -19,6 +19,7 @@ Profile g_prof;
 ProfScope::ProfScope(cudaStream_t s, int kind, double bytes, int level) : stream(s) {
   Profile &pr = g_prof;
   if (!pr.on) return;
+  if (pr.only_kind >= 0 && (kind != pr.only_kind || (pr.only_level >= 0 && level != pr.only_level))) return;
   if (pr.used * 2 + 2 > pr.ev.size()) {
     const size_t add = std::max<size_t>(2048, pr.ev.size());
     for (size_t t = 0; t < add; ++t) {
@@ -357,6 +358,14 @@ int amg_profile_enable(int32_t on) {
       }
     pr.used = 0;
   }
+  return AMG_OK;
+}
+
+int amg_profile_filter(int32_t kernel, int32_t level) {
+  if (kernel < -1 || kernel >= AMG_K_COUNT) return bad("kernel class out of range");
+  if (level < -1 || level >= amg::kMaxLevels) return bad("level out of range");
+  amg::g_prof.only_kind = kernel;
+  amg::g_prof.only_level = level;
   return AMG_OK;
 }
 
