@@ -152,6 +152,19 @@ class Clocks:
                 "samples": len(rows), "reasons": reasons}
 
 
+def reduce_max(value: float, device=None) -> float:
+    """Maximum of `value` over the ranks of the default process group (the
+    slowest replica sets the time); identity without one."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def gpu_uuid(dev: int):
     try:
         import torch
@@ -309,11 +322,7 @@ def run_gpu(args, rank, world, dist):
     timed = amg.profile_read(-1 if dom_lv is None else dom_lv)[dom]
     if dom_lv is None:  # set-up kernels carry no level
         timed = amg.profile_read()[dom]
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, dev)
 
     peak, peak_src = peaks()
     d = timed
@@ -348,11 +357,7 @@ def run_gpu(args, rank, world, dist):
         for _ in range(reps):
             xh[...] = 0.0
             _, res = amg.solve(A_h, bh, x0=xh, params=params, rtol=args.rtol, maxit=1000, stream=stream)
-        te = (time.perf_counter() - t0) / reps
-        if dist:
-            t = torch.tensor([te], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
+        te = reduce_max((time.perf_counter() - t0) / reps, dev)
         n, nnz = p.A.n, p.A.nnz
         e2e = {"value": te, "unit": "s", "h2d_bytes_per_step": 4 * (n + 1) + 12 * nnz + 16 * n,
                "d2h_bytes_per_step": 8 * n + 8 + 8 * 10}
