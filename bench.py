@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-latency leg")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-capacity", type=int, default=4)
     ap.add_argument("--no-kernel-events", action="store_true",
                     help="do not record per-launch CUDA events in the timed region (roofline fields then null)")
     return ap.parse_args()
@@ -369,6 +372,10 @@ def run_gpu(args, rank, world, dist):
                "sample": f"one full oracle set-up ({tp_o:.2f} s) + PCG solve ({ts_o:.2f} s, {it_o} it) of the workload",
                "iters": it_o}
 
+    serving = None
+    if world == 1 and not args.no_serve:
+        serving = run_serving(args)
+
     if rank != 0:
         return
     info = rec["info"]
@@ -392,8 +399,45 @@ def run_gpu(args, rank, world, dist):
         "profile_pass": {"note": "one extra step with events around every launch (not timed)",
                          "kernels_ms": kernels, "by_level_ms": by_level},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "serving": serving,
     }
     print(json.dumps(out), flush=True)
+
+
+def run_serving(args):
+    """The serving workload: 4 resident FP32-V-cycle hierarchies (diffusion sigma 1 at 48^3, 96^3,
+    128^3, 160^3), a stream of requests (seed 4) with Poisson arrivals at 200 req/s, 70% new
+    right-hand sides served by continuous batching, 30% new operators (m log-uniform in [32, 160])
+    set up and solved on worker streams; rtol 1e-8.  Latency = arrival to solution in HBM."""
+    import torch
+
+    from paper_2102_07417_gb300 import amg, serve
+
+    t0 = time.perf_counter()
+    ops = serve.resident_operators(sizes=(48, 96, 128, 160), sigma=1.0, seed0=40)
+    srv = serve.Server(ops, precision=amg.PREC_FP32, capacity=args.serve_capacity, rtol=1e-8, maxit=200)
+    del ops
+    t_res = time.perf_counter() - t0
+    # warm-up: graphs captured, allocator pools grown (not reported)
+    srv.run(serve.make_requests(24, rate=2000.0, seed=99, m_range=(32, 64)))
+    for k in srv.stats:
+        srv.stats[k] = 0
+    torch.cuda.synchronize()
+    l0 = amg.launch_count()
+    reqs = serve.make_requests(args.serve_requests, rate=200.0, seed=4, frac_matrix=0.3, n_resident=4,
+                               m_range=(32, 160))
+    res = srv.run(reqs)
+    torch.cuda.synchronize()
+    out = serve.summarize(res)
+    out.update({"unit": "ms", "offered_rate_req_s": 200.0, "capacity_per_operator": args.serve_capacity,
+                "precision": "fp32 V-cycle + fp64 flexible PCG", "resident_setup_s": t_res,
+                "iters_rhs_median": statistics.median([r.iters for r in res if r.kind == "rhs"] or [0]),
+                "gpu_launches": amg.launch_count() - l0, "stats": dict(srv.stats),
+                "config": "512 requests (seed 4), Poisson arrivals 200 req/s, 70% rhs on 4 resident operators "
+                          "(48^3, 96^3, 128^3, 160^3 diffusion, sigma 1, seeds 40-43), 30% new operators "
+                          "(m log-uniform [32, 160]); rtol 1e-8"})
+    srv.close()
+    return out
 
 
 def main():

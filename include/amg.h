@@ -139,6 +139,41 @@ int amg_pcg_solve(amg_hierarchy *h, const double *b, double *x, double rtol, int
 int amg_pcg_solve_batch(amg_hierarchy *h, int32_t k, const double *B, double *X, double rtol, int32_t maxit,
                         void *stream, int32_t *iters, int32_t *status, double *res_hist, int32_t hist_cap);
 
+/* Continuous batching (Sec. 3.1's row-wise dense blocks, used as a resident
+ * batch whose columns change while it runs).  A slots object holds an n x
+ * capacity block of CG vectors on hierarchy h (1 <= capacity <= 32, the last
+ * level bounded as for amg_pcg_solve_batch) and runs on `stream`; every call
+ * below is stream-ordered on it.  Each column ("slot") is one request:
+ *   amg_slots_admit  starts PCG on slot `slot` with x0 = 0 and right-hand side
+ *                    b (device, n doubles; read before the call's work ends,
+ *                    i.e. the caller keeps b alive until the next poll);
+ *   amg_slots_step   runs one PCG iteration of every running slot (one SpMM,
+ *                    one update, one V-cycle, one direction update shared by
+ *                    all of them).  A slot admitted since the last step uses
+ *                    it to form z = M r and p = z (alpha = beta = 0), the same
+ *                    arithmetic as the first step of amg_pcg_solve_batch.
+ *                    Converged and free slots are frozen;
+ *   amg_slots_poll   synchronises the stream and reports per slot (host
+ *                    arrays of capacity, either may be NULL): state 0 free,
+ *                    1 running, 2 converged (||r_j|| < rtol ||b_j||), or a
+ *                    negative status (AMG_ERR_NO_CONVERGENCE after maxit
+ *                    iterations, AMG_ERR_BREAKDOWN); iters = CG iterations;
+ *   amg_slots_retire copies the slot's x into `x` (device, n doubles; NULL
+ *                    discards it) and frees the slot;
+ *   amg_slots_free   waits for the stream and releases the object (before
+ *                    amg_free(h)).
+ * Memory comes from h's allocator.  A slots object must be driven from one
+ * host thread; several objects on different streams may share h (the
+ * hierarchy is read only).  AMG_ERR_UNSUPPORTED if the last level is too
+ * large for `capacity` columns. */
+typedef struct amg_slots amg_slots;
+int amg_slots_create(amg_hierarchy *h, int32_t capacity, double rtol, int32_t maxit, void *stream, amg_slots **out);
+int amg_slots_admit(amg_slots *s, int32_t slot, const double *b);
+int amg_slots_step(amg_slots *s);
+int amg_slots_poll(amg_slots *s, int32_t *state, int32_t *iters);
+int amg_slots_retire(amg_slots *s, int32_t slot, double *x);
+void amg_slots_free(amg_slots *s);
+
 /* One application of the preconditioner z = B y (Algorithm 2 on level 0):
  * y, z device arrays of n doubles (FP64 in and out in every precision mode). */
 int amg_vcycle_apply(amg_hierarchy *h, const double *y, double *z, void *stream);

@@ -37,7 +37,8 @@ SETUP_KERNELS = KERNEL_NAMES[9:]
 EXPORTS = ["amg_params_default", "amg_setup", "amg_pcg_solve", "amg_pcg_solve_batch", "amg_vcycle_apply", "amg_spmv", "amg_solve",
            "amg_hierarchy_info", "amg_hierarchy_export", "amg_hierarchy_bytes", "amg_free", "amg_profile_enable",
            "amg_profile_read", "amg_profile_filter", "amg_launch_count", "amg_status_string", "amg_last_error",
-           "amg_spmv_dot_noalloc"]
+           "amg_spmv_dot_noalloc", "amg_slots_create", "amg_slots_admit", "amg_slots_step", "amg_slots_poll",
+           "amg_slots_retire", "amg_slots_free"]
 
 
 class AmgError(RuntimeError):
@@ -94,6 +95,13 @@ def load(build_if_missing: bool = True):
     L.amg_pcg_solve.argtypes = [vp, vp, vp, dbl, i32, vp, C.POINTER(i32), vp, i32]
     L.amg_pcg_solve_batch.argtypes = [vp, i32, vp, vp, dbl, i32, vp, vp, vp, vp, i32]
     L.amg_vcycle_apply.argtypes = [vp, vp, vp, vp]
+    L.amg_slots_create.argtypes = [vp, i32, dbl, i32, vp, C.POINTER(vp)]
+    L.amg_slots_admit.argtypes = [vp, i32, vp]
+    L.amg_slots_step.argtypes = [vp]
+    L.amg_slots_poll.argtypes = [vp, vp, vp]
+    L.amg_slots_retire.argtypes = [vp, i32, vp]
+    L.amg_slots_free.argtypes = [vp]
+    L.amg_slots_free.restype = None
     L.amg_spmv.argtypes = [vp, i32, vp, vp, vp]
     L.amg_solve.argtypes = [C.POINTER(Csr), vp, vp, C.POINTER(Params), dbl, i32, C.POINTER(Allocator), vp,
                             C.POINTER(Result)]
@@ -191,7 +199,10 @@ class Hierarchy:
         self.n = int(A.n)
         self.nnz = int(rp[-1]) if not on_dev else int(rp[-1].item())
         csr = Csr(self.n, self.nnz, *ptrs, 1 if on_dev else 0)
+        self.tstream = stream
         self.stream = _stream_handle(stream)
+        if hasattr(stream, "wait_stream"):  # A may come from work queued on the current stream
+            stream.wait_stream(torch.cuda.current_stream())
         h = C.c_void_p()
         check(L.amg_setup(C.byref(csr), C.byref(self.params), C.byref(self._alloc.struct) if self._alloc else None,
                           self.stream, C.byref(h)), "amg_setup")
@@ -208,6 +219,24 @@ class Hierarchy:
         except Exception:
             pass
 
+    def _on(self, stream) -> int:
+        """Handle of the stream a call runs on (the given one, else the hierarchy's), ordered
+        after the work already queued on the caller's current stream."""
+        import torch
+
+        s = stream if stream is not None else self.tstream
+        if hasattr(s, "wait_stream"):
+            s.wait_stream(torch.cuda.current_stream())
+        return _stream_handle(s) if stream is not None else self.stream
+
+    def _after(self, stream):
+        """Order the caller's current stream after a stream-ordered call."""
+        import torch
+
+        s = stream if stream is not None else self.tstream
+        if hasattr(s, "wait_stream"):
+            torch.cuda.current_stream().wait_stream(s)
+
     # -- solve phase ---------------------------------------------------------
     def solve(self, b, x=None, rtol: float = 1e-8, maxit: int = 500, hist: bool = False, stream=None):
         """PCG to ||r|| < rtol ||b||.  b, x: CUDA float64 tensors (x holds x0; default zeros).
@@ -218,7 +247,7 @@ class Hierarchy:
             x = torch.zeros_like(b)
         hbuf = np.zeros(maxit + 1) if hist else None
         it = C.c_int32(0)
-        st = load().amg_pcg_solve(self.h, _ptr(b), _ptr(x), rtol, maxit, _stream_handle(stream) if stream else self.stream,
+        st = load().amg_pcg_solve(self.h, _ptr(b), _ptr(x), rtol, maxit, self._on(stream),
                                   C.byref(it), hbuf.ctypes.data if hist else None, maxit + 1 if hist else 0)
         if st not in (AMG_OK, AMG_ERR_NO_CONVERGENCE):
             check(st, "amg_pcg_solve")
@@ -237,19 +266,24 @@ class Hierarchy:
         stv = np.zeros(k, np.int32)
         hbuf = np.zeros((maxit + 1, k)) if hist else None
         st = load().amg_pcg_solve_batch(self.h, k, _ptr(B), _ptr(X), rtol, maxit,
-                                        _stream_handle(stream) if stream else self.stream, it.ctypes.data,
+                                        self._on(stream), it.ctypes.data,
                                         stv.ctypes.data, hbuf.ctypes.data if hist else None, maxit + 1 if hist else 0)
         if st not in (AMG_OK, AMG_ERR_NO_CONVERGENCE, AMG_ERR_BREAKDOWN):
             check(st, "amg_pcg_solve_batch")
         return X, it.tolist(), stv.tolist(), st, hbuf
+
+    def slots(self, capacity: int, rtol: float = 1e-8, maxit: int = 500, stream=None) -> "Slots":
+        """A continuous-batching block of ``capacity`` PCG columns on this hierarchy."""
+        return Slots(self, capacity, rtol, maxit, stream)
 
     def vcycle(self, y, z=None, stream=None):
         import torch
 
         if z is None:
             z = torch.empty_like(y)
-        check(load().amg_vcycle_apply(self.h, _ptr(y), _ptr(z), _stream_handle(stream) if stream else self.stream),
+        check(load().amg_vcycle_apply(self.h, _ptr(y), _ptr(z), self._on(stream)),
               "amg_vcycle_apply")
+        self._after(stream)
         return z
 
     def spmv(self, level: int, x, y=None, stream=None):
@@ -257,8 +291,9 @@ class Hierarchy:
 
         if y is None:
             y = torch.empty(self.info()["n"][level], dtype=torch.float64, device=x.device)
-        check(load().amg_spmv(self.h, level, _ptr(x), _ptr(y), _stream_handle(stream) if stream else self.stream),
+        check(load().amg_spmv(self.h, level, _ptr(x), _ptr(y), self._on(stream)),
               "amg_spmv")
+        self._after(stream)
         return y
 
     # -- inspection ----------------------------------------------------------
@@ -291,6 +326,76 @@ class Hierarchy:
         return int(load().amg_hierarchy_bytes(self.h))
 
 
+
+
+SLOT_FREE, SLOT_RUNNING, SLOT_CONVERGED = 0, 1, 2
+
+
+class Slots:
+    """Continuous batching on one hierarchy: up to 32 requests share each SpMM and V-cycle.
+
+    ``admit(j, b)`` starts PCG (x0 = 0) for right-hand side ``b`` in slot j,
+    ``step()`` runs one iteration of every running slot, ``poll()`` returns the
+    per-slot states (0 free, 1 running, 2 converged, < 0 error) and iteration
+    counts, ``retire(j)`` returns slot j's solution and frees the slot.  All
+    calls are ordered on the object's stream; ``poll`` synchronises it.
+    """
+
+    def __init__(self, hier: Hierarchy, capacity: int, rtol: float, maxit: int, stream=None):
+        import torch
+
+        self.hier = hier
+        self.capacity = int(capacity)
+        self.n = hier.n
+        # a stream of its own (steps are captured into a CUDA graph and replayed on it)
+        self.tstream = stream if stream is not None else torch.cuda.Stream()
+        self.stream = _stream_handle(self.tstream)
+        self._state = np.zeros(self.capacity, np.int32)
+        self._iters = np.zeros(self.capacity, np.int32)
+        self._pending = {}  # slot -> right-hand side tensor kept alive until the next poll
+        h = C.c_void_p()
+        check(load().amg_slots_create(hier.h, self.capacity, rtol, maxit, self.stream, C.byref(h)), "amg_slots_create")
+        self.s = h
+        self._torch = torch
+
+    def admit(self, slot: int, b):
+        """Start PCG for right-hand side b (CUDA float64, n) in a free slot."""
+        self.tstream.wait_stream(self._torch.cuda.current_stream())
+        b.record_stream(self.tstream)
+        check(load().amg_slots_admit(self.s, int(slot), _ptr(b)), "amg_slots_admit")
+        self._pending[int(slot)] = b
+
+    def step(self):
+        check(load().amg_slots_step(self.s), "amg_slots_step")
+
+    def poll(self):
+        check(load().amg_slots_poll(self.s, self._state.ctypes.data, self._iters.ctypes.data), "amg_slots_poll")
+        self._pending.clear()
+        return self._state.copy(), self._iters.copy()
+
+    def retire(self, slot: int, x=None):
+        """Slot's solution (into x, or a new tensor) and the slot freed; ordered before later
+        work on the caller's current stream."""
+        torch = self._torch
+        cur = torch.cuda.current_stream()
+        if x is None:
+            x = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        self.tstream.wait_stream(cur)
+        check(load().amg_slots_retire(self.s, int(slot), _ptr(x)), "amg_slots_retire")
+        x.record_stream(self.tstream)
+        cur.wait_stream(self.tstream)
+        return x
+
+    def close(self):
+        if getattr(self, "s", None):
+            load().amg_slots_free(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 def profile(on: bool):
     """Start (clearing totals) or stop process-wide per-launch CUDA-event timing."""

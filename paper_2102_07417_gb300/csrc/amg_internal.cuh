@@ -206,6 +206,21 @@ void prepare_solve(amg_hierarchy *h);
 int pcg_solve(amg_hierarchy *h, const double *b, double *x, double rtol, int maxit, int *iters, double *hist,
               int hist_cap);
 void vcycle_apply(amg_hierarchy *h, const double *y, double *z);
+// continuous batching slots (batch.cu): one resident n x K CG block whose
+// columns are admitted, stepped and retired independently
+struct SlotsBase {
+  virtual ~SlotsBase() = default;
+  virtual void admit(int j, const double *b) = 0;
+  virtual void step() = 0;
+  virtual void poll(int *state, int *iters) = 0;
+  virtual void retire(int j, double *x) = 0;
+};
+SlotsBase *make_slots(amg_hierarchy *h, int K, double rtol, int maxit, cudaStream_t s);
+void slots_admit(SlotsBase *b, int j, const double *rhs);
+void slots_step(SlotsBase *b);
+void slots_poll(SlotsBase *b, int *state, int *iters);
+void slots_retire(SlotsBase *b, int j, double *x);
+void slots_delete(SlotsBase *b);
 // batched right-hand sides (batch.cu)
 int pcg_solve_batch(amg_hierarchy *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
                     int *status, double *hist, int hist_cap);

@@ -226,6 +226,74 @@ int amg_pcg_solve_batch(amg_hierarchy *h, int32_t k, const double *B, double *X,
   AMG_GUARD_END
 }
 
+struct amg_slots {
+  amg_hierarchy *h;
+  amg::SlotsBase *impl;
+  int32_t capacity;
+};
+
+int amg_slots_create(amg_hierarchy *h, int32_t capacity, double rtol, int32_t maxit, void *stream, amg_slots **out) {
+  if (!out) return bad("NULL argument");
+  *out = nullptr;
+  if (!h) return bad("NULL argument");
+  if (capacity < 1 || capacity > 32) return bad("capacity must be in 1..32");
+  if (!(rtol > 0.0) || maxit < 1) return bad("rtol must be > 0 and maxit >= 1");
+  AMG_GUARD_BEGIN
+  amg_slots *s = new amg_slots{h, nullptr, capacity};
+  try {
+    s->impl = amg::make_slots(h, capacity, rtol, maxit, static_cast<cudaStream_t>(stream));
+  } catch (...) {
+    delete s;
+    throw;
+  }
+  *out = s;
+  return AMG_OK;
+  AMG_GUARD_END
+}
+
+int amg_slots_admit(amg_slots *s, int32_t slot, const double *b) {
+  if (!s || !b) return bad("NULL argument");
+  if (slot < 0 || slot >= s->capacity) return bad("slot out of range");
+  AMG_GUARD_BEGIN
+  amg::slots_admit(s->impl, slot, b);
+  return AMG_OK;
+  AMG_GUARD_END
+}
+
+int amg_slots_step(amg_slots *s) {
+  if (!s) return bad("NULL argument");
+  AMG_GUARD_BEGIN
+  amg::slots_step(s->impl);
+  return AMG_OK;
+  AMG_GUARD_END
+}
+
+int amg_slots_poll(amg_slots *s, int32_t *state, int32_t *iters) {
+  if (!s) return bad("NULL argument");
+  AMG_GUARD_BEGIN
+  amg::slots_poll(s->impl, state, iters);
+  return AMG_OK;
+  AMG_GUARD_END
+}
+
+int amg_slots_retire(amg_slots *s, int32_t slot, double *x) {
+  if (!s) return bad("NULL argument");
+  if (slot < 0 || slot >= s->capacity) return bad("slot out of range");
+  AMG_GUARD_BEGIN
+  amg::slots_retire(s->impl, slot, x);
+  return AMG_OK;
+  AMG_GUARD_END
+}
+
+void amg_slots_free(amg_slots *s) {
+  if (!s) return;
+  try {
+    amg::slots_delete(s->impl);
+  } catch (...) {
+  }
+  delete s;
+}
+
 int amg_vcycle_apply(amg_hierarchy *h, const double *y, double *z, void *stream) {
   if (!h || !y || !z) return bad("NULL argument");
   AMG_GUARD_BEGIN

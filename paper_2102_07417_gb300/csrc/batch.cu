@@ -26,6 +26,7 @@ constexpr int KMAX = 32;  // largest block width
 struct BScal {
   double rho[KMAX], alpha[KMAX], beta[KMAX], rr[KMAX], bb[KMAX], tol[KMAX];
   int iters[KMAX], done[KMAX], status[KMAX];
+  int first[KMAX];  // column admitted since the last iteration (continuous batching): no CG step yet
   int all_done, maxit, k;
 };
 
@@ -188,7 +189,9 @@ struct BSpmvDot {
     double tot[1];
     if (col_reduce<K, 1>(acc.v, partials, counter, tot)) {
       const int j = threadIdx.x;
-      if (j < k && !sc->done[j]) {
+      if (j < k && !sc->done[j] && sc->first[j]) {
+        sc->alpha[j] = 0.0;  // p_j = 0: its first step only forms z = M r
+      } else if (j < k && !sc->done[j]) {
         if (!(tot[0] > 0.0)) {
           sc->status[j] = AMG_ERR_BREAKDOWN;
           sc->done[j] = 1;
@@ -319,8 +322,12 @@ struct BPost0 {
     if (col_reduce<K, 2>(acc.v, partials, counter, tot)) {
       const int j = threadIdx.x;
       if (j < k && !sc->done[j]) {
-        if (mode == BPOST_ITER)
+        if (mode == BPOST_ITER && sc->first[j]) {
+          sc->beta[j] = 0.0;  // p_j = 0 + z_j
+          sc->first[j] = 0;
+        } else if (mode == BPOST_ITER) {
           sc->beta[j] = flexible ? -sc->alpha[j] * tot[1] / sc->rho[j] : tot[0] / sc->rho[j];
+        }
         sc->rho[j] = tot[0];
       }
     }
@@ -338,7 +345,7 @@ __global__ void __launch_bounds__(TPB) k_bupdate(int n, int k, double *__restric
   __shared__ double s_alpha[KMAX];
   __shared__ int s_done[KMAX];
   if (threadIdx.x < k) {
-    s_done[threadIdx.x] = sc->done[threadIdx.x];
+    s_done[threadIdx.x] = sc->done[threadIdx.x] | sc->first[threadIdx.x];
     s_alpha[threadIdx.x] = s_done[threadIdx.x] ? 0.0 : sc->alpha[threadIdx.x];
   }
   __syncthreads();
@@ -387,7 +394,7 @@ __global__ void __launch_bounds__(TPB) k_bupdate(int n, int k, double *__restric
     const int c = threadIdx.x;
     double s = 0.0;
     for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(&partials[(b * 3) * KMAX + c]);
-    if (!sc->done[c]) {
+    if (!sc->done[c] && !sc->first[c]) {
       const int it = sc->iters[c] + 1;
       sc->iters[c] = it;
       sc->rr[c] = s;
@@ -490,6 +497,7 @@ struct BWork {
 template <int K, typename T, typename TP>
 struct Batch {
   amg_hierarchy *h;
+  cudaStream_t st;
   int k;
   BWork<T> *wk;
   BScal *sc;
@@ -498,7 +506,7 @@ struct Batch {
   double *r, *zz, *p, *q;  // level-0 CG blocks (FP64)
 
   void cycle(int lv, const int *done) {
-    cudaStream_t s = h->mem.stream;
+    cudaStream_t s = st;
     Level &L = h->lev[lv];
     const DCsr &A = L.A;
     const int n = A.n;
@@ -555,7 +563,7 @@ struct Batch {
   }
 
   void vcycle(int mode, int flexible, const int *done) {
-    cudaStream_t s = h->mem.stream;
+    cudaStream_t s = st;
     Level &L0 = h->lev[0];
     const DCsr &A = L0.A;
     const int n = A.n;
@@ -628,7 +636,7 @@ int batch_impl(amg_hierarchy *h, int k, const double *B, double *X, double rtol,
   }
   T *s0 = wk.s[0].p;
   const bool pre = h->prm.nu1 > 0;
-  Batch<K, T, TP> bt{h, k, &wk, scb.p, partials.p, counter.p, r.p, zz.p, p.p, q.p};
+  Batch<K, T, TP> bt{h, s, k, &wk, scb.p, partials.p, counter.p, r.p, zz.p, p.p, q.p};
   {
     ProfScope ps(s, AMG_K_SOLVE_OTHER, 12.0 * A.nnz + 40.0 * nk, 0);
     launch_b<K>(n, k, A, BInit<K, T>{k, A.v, X, B, r.p, wdv<T>(L0), y0, s0, !fp64, pre, rtol, scb.p, hist.p, maxit + 1,
@@ -688,6 +696,227 @@ int batch_dispatch(amg_hierarchy *h, int k, const double *B, double *X, double r
   return batch_impl<32, T, TP>(h, k, B, X, rtol, maxit, iters, status, hist, hist_cap);
 }
 
+
+// ------------------------------------------------------------------ slots --
+// Continuous batching: a resident n x K block on one hierarchy whose columns
+// ("slots") are admitted, stepped and retired independently.
+
+// Column j of an n x K block: x = 0, r = b, p = 0; tol_j = rtol ||b||.
+__global__ void __launch_bounds__(TPB) k_admit(int n, int K, int j, const double *__restrict__ b, double *__restrict__ x,
+                                               double *__restrict__ r, double *__restrict__ p, double rtol, BScal *sc,
+                                               double *partials, unsigned int *counter) {
+  __shared__ double red[TPB / 32];
+  __shared__ bool last;
+  double v = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    const size_t o = (size_t)i * K + j;
+    x[o] = 0.0;
+    r[o] = bi;
+    p[o] = 0.0;
+    v = fma(bi, bi, v);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < TPB / 32; ++w) t += red[w];
+    partials[blockIdx.x * 3 * KMAX] = t;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double bb = 0.0;
+  for (int g = 0; g < (int)gridDim.x; ++g) bb += __ldcg(&partials[g * 3 * KMAX]);
+  sc->bb[j] = bb;
+  sc->tol[j] = rtol * sqrt(bb);
+  sc->iters[j] = 0;
+  sc->status[j] = AMG_OK;
+  sc->done[j] = bb == 0.0 ? 1 : 0;
+  sc->first[j] = bb == 0.0 ? 0 : 1;
+  sc->alpha[j] = sc->beta[j] = 0.0;
+  sc->rho[j] = 1.0;
+  int all = 1;
+  for (int c = 0; c < sc->k; ++c) all &= sc->done[c];
+  sc->all_done = all;
+  *counter = 0u;
+}
+
+// Frees slot j (frozen, counted as done).
+__global__ void k_release(int j, BScal *sc) {
+  sc->done[j] = 1;
+  sc->first[j] = 0;
+  int all = 1;
+  for (int c = 0; c < sc->k; ++c) all &= sc->done[c];
+  sc->all_done = all;
+}
+
+__global__ void k_take_column(int n, int K, int j, const double *__restrict__ X, double *__restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = X[(size_t)i * K + j];
+}
+
+template <int KP, typename T, typename TP>
+struct SlotsImpl : SlotsBase {
+  amg_hierarchy *h;
+  Mem mem;
+  int K, maxit;
+  double rtol;
+  BWork<T> wk;
+  Buf<double> X, r, zz, p, q, partials;
+  Buf<BScal> scb;
+  Buf<unsigned int> counter;
+  BScal *host = nullptr;  // pinned copy for poll
+  std::vector<int> busy;
+  cudaGraphExec_t exec = nullptr;
+  long long per_step = 0;  // kernels in one step
+
+  SlotsImpl(amg_hierarchy *hh, int cap, double rt, int mi, cudaStream_t s) : h(hh), K(cap), maxit(mi), rtol(rt) {
+    mem.alloc = h->mem.alloc;
+    mem.callbacks = h->mem.callbacks;
+    mem.stream = s;
+    const int n = h->lev[0].A.n;
+    const size_t nk = (size_t)n * K;
+    for (int lv = 0; lv < h->nlevels; ++lv) {
+      const size_t cnt = (size_t)h->lev[lv].A.n * K;
+      const bool work = lv < h->nlevels - 1 || lv == 0;
+      wk.y.emplace_back(mem, (lv == 0 && std::is_same<T, double>::value) ? 1 : cnt);
+      wk.z.emplace_back(mem, cnt);
+      wk.s.emplace_back(mem, work ? cnt : 1);
+      wk.r.emplace_back(mem, work ? cnt : 1);
+      wk.w.emplace_back(mem, work ? cnt : 1);
+    }
+    X = Buf<double>(mem, nk);
+    r = Buf<double>(mem, nk);
+    zz = Buf<double>(mem, nk);
+    p = Buf<double>(mem, nk);
+    q = Buf<double>(mem, nk);
+    partials = Buf<double>(mem, (size_t)MAX_GRID * 3 * KMAX);
+    scb = Buf<BScal>(mem, 1);
+    counter = Buf<unsigned int>(mem, 1);
+    if (std::is_same<T, double>::value) {  // FP64: the V-cycle input is the CG residual block
+      wk.y[0].reset();
+      wk.y[0].p = reinterpret_cast<T *>(r.p);
+      wk.y[0].m = nullptr;
+    }
+    AMG_CUDA(cudaMemsetAsync(X.p, 0, sizeof(double) * nk, s));
+    AMG_CUDA(cudaMemsetAsync(p.p, 0, sizeof(double) * nk, s));
+    AMG_CUDA(cudaMemsetAsync(r.p, 0, sizeof(double) * nk, s));
+    AMG_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
+    BScal init{};
+    init.maxit = maxit;
+    init.k = K;
+    for (int j = 0; j < K; ++j) init.done[j] = 1;
+    init.all_done = 1;
+    AMG_CUDA(cudaMemcpyAsync(scb.p, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    AMG_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&host), sizeof(BScal), cudaHostAllocDefault));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    busy.assign(K, 0);
+  }
+  ~SlotsImpl() override {
+    cudaStreamSynchronize(mem.stream);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (host) cudaFreeHost(host);
+    // Bufs return their memory through mem; free_all catches anything left
+  }
+  void admit(int j, const double *b) override {
+    const int n = h->lev[0].A.n;
+    k_admit<<<grid_for(n), TPB, 0, mem.stream>>>(n, K, j, b, X.p, r.p, p.p, rtol, scb.p, partials.p, counter.p);
+    AMG_CHECK_LAUNCH();
+    busy[j] = 1;
+  }
+  // One PCG iteration of every running column.  Without profiling the
+  // launches are captured once into a CUDA graph and replayed (the launch
+  // sequence never changes: masks live in device memory).
+  void step() override {
+    if (g_prof.on || mem.stream == nullptr) {  // the legacy default stream cannot be captured
+      issue_step();
+      return;
+    }
+    if (!exec) {
+      cudaGraph_t g = nullptr;
+      const long long before = g_launches.load();
+      AMG_CUDA(cudaStreamBeginCapture(mem.stream, cudaStreamCaptureModeThreadLocal));
+      try {
+        issue_step();
+      } catch (...) {
+        cudaStreamEndCapture(mem.stream, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      AMG_CUDA(cudaStreamEndCapture(mem.stream, &g));
+      per_step = g_launches.load() - before;
+      const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      AMG_CUDA(e);
+      g_launches.fetch_sub(per_step);
+    }
+    AMG_CUDA(cudaGraphLaunch(exec, mem.stream));
+    g_launches.fetch_add(per_step);
+  }
+  void issue_step() {
+    cudaStream_t s = mem.stream;
+    const Level &L0 = h->lev[0];
+    const DCsr &A = L0.A;
+    const int n = A.n;
+    const int64_t nk = (int64_t)n * K;
+    const bool fp64 = std::is_same<T, double>::value;
+    const int *done = &scb.p->all_done;
+    T *y0 = fp64 ? reinterpret_cast<T *>(r.p) : wk.y[0].p;
+    Batch<KP, T, TP> bt{h, s, K, &wk, scb.p, partials.p, counter.p, r.p, zz.p, p.p, q.p};
+    {
+      ProfScope ps(s, AMG_K_SPMV_DOT, 12.0 * A.nnz + 4.0 * (n + 1) + 24.0 * nk, 0);
+      launch_b<KP>(n, K, A, BSpmvDot<KP>{K, A.v, p.p, q.p, scb.p, partials.p, counter.p}, s);
+    }
+    {
+      ProfScope ps(s, AMG_K_PCG_UPDATE, (48.0 + 3.0 * sizeof(T)) * nk, 0);
+      k_bupdate<T><<<grid_for(nk), TPB, 0, s>>>(n, K, X.p, r.p, p.p, q.p, wdv<T>(L0), y0, wk.s[0].p, !fp64,
+                                                h->prm.nu1 > 0, scb.p, nullptr, 0, nullptr, partials.p, counter.p);
+      AMG_CHECK_LAUNCH();
+    }
+    bt.vcycle(BPOST_ITER, fp64 ? 0 : 1, done);
+    {
+      ProfScope ps(s, AMG_K_DIRECTION, 24.0 * nk, 0);
+      k_bdirection<<<grid_for(nk), TPB, 0, s>>>(nk, K, zz.p, p.p, scb.p);
+      AMG_CHECK_LAUNCH();
+    }
+  }
+  void poll(int *state, int *iters) override {
+    AMG_CUDA(cudaMemcpyAsync(host, scb.p, sizeof(BScal), cudaMemcpyDeviceToHost, mem.stream));
+    AMG_CUDA(cudaStreamSynchronize(mem.stream));
+    for (int j = 0; j < K; ++j) {
+      int stt = 0;
+      if (busy[j]) stt = !host->done[j] ? 1 : (host->status[j] == AMG_OK ? 2 : host->status[j]);
+      if (state) state[j] = stt;
+      if (iters) iters[j] = host->iters[j];
+    }
+  }
+  void retire(int j, double *x) override {
+    const int n = h->lev[0].A.n;
+    if (x) {
+      k_take_column<<<grid_for(n), TPB, 0, mem.stream>>>(n, K, j, X.p, x);
+      AMG_CHECK_LAUNCH();
+    }
+    k_release<<<1, 1, 0, mem.stream>>>(j, scb.p);
+    AMG_CHECK_LAUNCH();
+    busy[j] = 0;
+  }
+};
+
+template <typename T, typename TP>
+SlotsBase *make_slots_t(amg_hierarchy *h, int K, double rtol, int maxit, cudaStream_t s) {
+  if (K <= 1) return new SlotsImpl<1, T, TP>(h, K, rtol, maxit, s);
+  if (K <= 2) return new SlotsImpl<2, T, TP>(h, K, rtol, maxit, s);
+  if (K <= 4) return new SlotsImpl<4, T, TP>(h, K, rtol, maxit, s);
+  if (K <= 8) return new SlotsImpl<8, T, TP>(h, K, rtol, maxit, s);
+  if (K <= 16) return new SlotsImpl<16, T, TP>(h, K, rtol, maxit, s);
+  return new SlotsImpl<32, T, TP>(h, K, rtol, maxit, s);
+}
+
 }  // namespace
 
 int pcg_solve_batch(amg_hierarchy *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
@@ -711,5 +940,33 @@ int pcg_solve_batch(amg_hierarchy *h, int k, const double *B, double *X, double 
     default: return batch_dispatch<float, __nv_bfloat16>(h, k, B, X, rtol, maxit, iters, status, hist, hist_cap);
   }
 }
+
+}  // namespace amg
+
+namespace amg {
+
+SlotsBase *make_slots(amg_hierarchy *h, int K, double rtol, int maxit, cudaStream_t s) {
+  if ((size_t)2 * sizeof(double) * h->nL * K > 200 * 1024) {
+    set_error("last level of %d rows too large for %d slots", h->nL, K);
+    throw Status{AMG_ERR_UNSUPPORTED};
+  }
+  static bool attr = false;
+  if (!attr) {
+    AMG_CUDA(cudaFuncSetAttribute(k_bcoarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    AMG_CUDA(cudaFuncSetAttribute(k_bcoarse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  switch (h->prm.precision) {
+    case AMG_PREC_FP64: return make_slots_t<double, double>(h, K, rtol, maxit, s);
+    case AMG_PREC_FP32: return make_slots_t<float, float>(h, K, rtol, maxit, s);
+    default: return make_slots_t<float, __nv_bfloat16>(h, K, rtol, maxit, s);
+  }
+}
+
+void slots_admit(SlotsBase *b, int j, const double *rhs) { b->admit(j, rhs); }
+void slots_step(SlotsBase *b) { b->step(); }
+void slots_poll(SlotsBase *b, int *state, int *iters) { b->poll(state, iters); }
+void slots_retire(SlotsBase *b, int j, double *x) { b->retire(j, x); }
+void slots_delete(SlotsBase *b) { delete b; }
 
 }  // namespace amg

@@ -262,3 +262,61 @@ def nnz_poisson2d(N: int) -> int:
 def nnz_poisson3d(N: int) -> int:
     """Closed form: 7n - 6N^2 for the N^3 interior 7-point stencil."""
     return 7 * N ** 3 - 6 * N * N
+
+
+def diffusion3d_device(N: int, sigma: float, seed: int, device="cuda", stream=None) -> CSR:
+    """``diffusion3d``'s recipe generated on the GPU with torch (Philox normals from
+    ``seed``), for request streams where host generation would dominate.  Same
+    operator family (log-normal box-smoothed coefficients, harmonic-mean faces,
+    7-point stencil, row order [z-, y-, x-, diag, x+, y+, z+]); a different random
+    stream than the numpy version, so the matrices differ from ``diffusion3d``'s.
+    Returns a CSR whose arrays are CUDA tensors (int32 / float64)."""
+    import torch
+
+    import contextlib
+
+    ctx = torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext()
+    with ctx:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(int(seed))
+        g = torch.randn((N, N, N), generator=gen, device=device, dtype=torch.float64) * sigma
+        for _ in range(3):
+            for ax in range(3):
+                s = g.clone()
+                cnt = torch.ones(N, device=device, dtype=torch.float64)
+                lo = [slice(None)] * 3
+                hi = [slice(None)] * 3
+                lo[ax], hi[ax] = slice(1, None), slice(None, -1)
+                s[tuple(lo)] += g[tuple(hi)]
+                s[tuple(hi)] += g[tuple(lo)]
+                cnt[1:] += 1
+                cnt[:-1] += 1
+                shape = [1, 1, 1]
+                shape[ax] = -1
+                g = s / cnt.reshape(shape)
+        k = torch.exp(g)
+
+        def hm(a, b):
+            return 2.0 * a * b / (a + b)
+
+        kx_m = k.clone(); kx_m[:, :, 1:] = hm(k[:, :, 1:], k[:, :, :-1])
+        kx_p = k.clone(); kx_p[:, :, :-1] = hm(k[:, :, :-1], k[:, :, 1:])
+        ky_m = k.clone(); ky_m[:, 1:, :] = hm(k[:, 1:, :], k[:, :-1, :])
+        ky_p = k.clone(); ky_p[:, :-1, :] = hm(k[:, :-1, :], k[:, 1:, :])
+        kz_m = k.clone(); kz_m[1:, :, :] = hm(k[1:, :, :], k[:-1, :, :])
+        kz_p = k.clone(); kz_p[:-1, :, :] = hm(k[:-1, :, :], k[1:, :, :])
+        n = N ** 3
+        f = [a.reshape(n) for a in (kx_m, kx_p, ky_m, ky_p, kz_m, kz_p)]
+        diag = ((((f[4] + f[2]) + f[0]) + f[1]) + f[3]) + f[5]
+        p = torch.arange(n, device=device, dtype=torch.int64)
+        ix, iy, iz = p % N, (p // N) % N, p // (N * N)
+        cols = torch.stack([p - N * N, p - N, p - 1, p, p + 1, p + N, p + N * N], dim=1)
+        vals = torch.stack([-f[4], -f[2], -f[0], diag, -f[1], -f[3], -f[5]], dim=1)
+        mask = torch.stack([iz > 0, iy > 0, ix > 0, torch.ones_like(ix, dtype=torch.bool), ix < N - 1, iy < N - 1,
+                            iz < N - 1], dim=1)
+        rowptr = torch.zeros(n + 1, device=device, dtype=torch.int64)
+        torch.cumsum(mask.sum(dim=1), 0, out=rowptr[1:])
+        col = cols[mask].to(torch.int32)
+        val = vals[mask].contiguous()
+        rp = rowptr.to(torch.int32)
+    return CSR(n, rp, col, val, {"kind": "diffusion3d_device", "N": N, "sigma": sigma, "seed": seed})

@@ -1,0 +1,265 @@
+"""Serving AMG-PCG solves with continuous batching.
+
+A request loop keeps several hierarchies resident on the GPU and serves a
+stream of two kinds of request:
+
+* ``rhs``: a new right-hand side for one of the resident operators.  It is
+  admitted into a free column ("slot") of that operator's running PCG batch
+  (``amg.Slots``) at the next iteration boundary, shares every SpMM and
+  V-cycle with the requests already there, and leaves the batch as soon as
+  its own stopping test ``||r_j|| < rtol ||b_j||`` holds.
+* ``matrix``: a new operator (fresh coefficients) that needs set-up and
+  solve.  These run on worker threads, each with its own CUDA stream, and are
+  admitted only when the HBM they are expected to need is free.
+
+Every resident operator has its own stream; one loop iteration issues one
+PCG step (a replayed CUDA graph) on every operator with running slots, then
+polls them, so the steps of different operators overlap on the device.
+Latency is measured from a request's arrival time to the moment its solution
+is back in device memory.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import threading
+import time
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import amg
+from . import problems as pr
+
+
+@dataclass
+class Request:
+    rid: int
+    t_arrival: float  # seconds after the start of the stream
+    kind: str  # "rhs" | "matrix"
+    target: int  # resident operator index (rhs)
+    m: int  # grid size of a new operator (matrix): n = m^3
+    seed: int  # right-hand side / coefficient seed
+
+
+@dataclass
+class Result:
+    rid: int
+    kind: str
+    n: int
+    t_arrival: float
+    t_start: float
+    t_done: float
+    iters: int
+    status: int
+    slot: int = -1
+    x: object = None
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_arrival
+
+
+def make_requests(count: int = 512, rate: float = 200.0, seed: int = 4, frac_matrix: float = 0.3,
+                  n_resident: int = 4, m_range=(32, 160)) -> list[Request]:
+    """Poisson arrivals at ``rate`` req/s; each request is a new matrix with probability
+    ``frac_matrix`` (grid size m log-uniform in ``m_range``), else a new right-hand side for a
+    resident operator drawn uniformly."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, size=count)
+    t = np.cumsum(gaps) - gaps[0]  # the first request arrives at t = 0
+    is_mat = rng.random(count) < frac_matrix
+    target = rng.integers(0, n_resident, size=count)
+    lo, hi = math.log(m_range[0]), math.log(m_range[1])
+    m = np.rint(np.exp(rng.uniform(lo, hi, size=count))).astype(int)
+    seeds = rng.integers(1, 2**62, size=count)
+    return [Request(i, float(t[i]), "matrix" if is_mat[i] else "rhs", int(target[i]), int(m[i]), int(seeds[i]))
+            for i in range(count)]
+
+
+def percentile(v, q: float) -> float:
+    """Nearest-rank percentile (q in [0, 100]) of a non-empty sequence."""
+    s = sorted(v)
+    k = max(1, math.ceil(q / 100.0 * len(s)))
+    return float(s[k - 1])
+
+
+def summarize(results: list[Result]) -> dict:
+    lat = [r.latency for r in results if r.status == amg.AMG_OK]
+    out = {"requests": len(results), "ok": len(lat)}
+    if lat:
+        t0 = min(r.t_arrival for r in results)
+        t1 = max(r.t_done for r in results)
+        out.update({"p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
+                    "mean_ms": 1e3 * float(np.mean(lat)), "makespan_s": t1 - t0,
+                    "throughput_req_s": len(lat) / (t1 - t0) if t1 > t0 else float("nan")})
+        for kind in ("rhs", "matrix"):
+            lk = [r.latency for r in results if r.kind == kind and r.status == amg.AMG_OK]
+            if lk:
+                out[kind] = {"count": len(lk), "p50_ms": 1e3 * percentile(lk, 50), "p99_ms": 1e3 * percentile(lk, 99)}
+    return out
+
+
+def rhs_for(req: Request, n: int, device="cuda"):
+    """The request's right-hand side, b ~ U[-1, 1] from its seed (generated on the device)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(req.seed)
+    return torch.rand(n, generator=g, device=device, dtype=torch.float64) * 2.0 - 1.0
+
+
+class Server:
+    """Resident hierarchies + continuous batching + HBM-gated set-up of new operators."""
+
+    def __init__(self, operators, precision: int = amg.PREC_FP32, capacity: int = 4, rtol: float = 1e-8,
+                 maxit: int = 200, workers: int = 2, sigma: float = 1.0, hbm_budget: int | None = None,
+                 hbm_reserve: int = 2 << 30, keep_x: bool = False):
+        import torch
+
+        self.torch = torch
+        self.precision, self.capacity, self.rtol, self.maxit = precision, capacity, rtol, maxit
+        self.sigma, self.keep_x = sigma, keep_x
+        self.hier, self.slots, self.n = [], [], []
+        for A in operators:
+            st = torch.cuda.Stream()
+            h = amg.Hierarchy(A, stream=st, precision=precision)  # waits for A's producers
+            self.hier.append(h)
+            self.slots.append(h.slots(capacity, rtol=rtol, maxit=maxit, stream=st))
+            self.n.append(h.n)
+        # bytes of hierarchy per unknown, from the resident operators (set-up estimate: x3 for
+        # the temporaries of the Galerkin products and the solve vectors)
+        self.bytes_per_row = max(h.nbytes() / h.n for h in self.hier) * 3.0
+        self.workers = workers
+        self.hbm_budget = hbm_budget
+        self.hbm_reserve = hbm_reserve
+        self._streams = [torch.cuda.Stream() for _ in range(workers)]
+        self._free_streams = collections.deque(range(workers))
+        self._lock = threading.Lock()
+        self.stats = {"max_running_slots": 0, "max_matrix_inflight": 0, "steps": 0, "rejected": 0}
+
+    def close(self):
+        for s in self.slots:
+            s.close()
+        for h in self.hier:
+            h.close()
+
+    # -- new operators (worker threads) --------------------------------------
+    def matrix_bytes(self, m: int) -> int:
+        return int(self.bytes_per_row * m ** 3)
+
+    def _hbm_ok(self, need: int, inflight_bytes: int) -> bool:
+        if self.hbm_budget is not None:
+            return inflight_bytes + need <= self.hbm_budget
+        free, _ = self.torch.cuda.mem_get_info()
+        cached = self.torch.cuda.memory_reserved() - self.torch.cuda.memory_allocated()
+        return need + inflight_bytes + self.hbm_reserve <= free + cached
+
+    def _solve_matrix(self, req: Request, t0: float, clock):
+        torch = self.torch
+        with self._lock:
+            si = self._free_streams.popleft()
+        st = self._streams[si]
+        t_start = clock() - t0
+        try:
+            with torch.cuda.stream(st):
+                A = pr.diffusion3d_device(req.m, self.sigma, req.seed, stream=st)
+                h = amg.Hierarchy(A, stream=st, precision=self.precision)
+                b = rhs_for(req, h.n)
+                x, it, status, _ = h.solve(b, rtol=self.rtol, maxit=self.maxit, stream=st)
+                st.synchronize()
+                h.close()
+            return Result(req.rid, "matrix", req.m ** 3, req.t_arrival, t_start, clock() - t0, it, status,
+                          x=x if self.keep_x else None)
+        finally:
+            with self._lock:
+                self._free_streams.append(si)
+
+    # -- the loop ------------------------------------------------------------
+    def run(self, requests: list[Request], clock=time.perf_counter) -> list[Result]:
+        torch = self.torch
+        reqs = sorted(requests, key=lambda r: r.t_arrival)
+        rhs_q = [collections.deque() for _ in self.hier]
+        mat_q = collections.deque()
+        free = [list(range(self.capacity)) for _ in self.hier]
+        running = [dict() for _ in self.hier]  # slot -> (request, t_start)
+        results: list[Result] = []
+        inflight = {}  # future -> (request, bytes)
+        pool = ThreadPoolExecutor(max_workers=self.workers)
+        nxt = 0
+        t0 = clock()
+        try:
+            while len(results) < len(reqs):
+                now = clock() - t0
+                while nxt < len(reqs) and reqs[nxt].t_arrival <= now:
+                    r = reqs[nxt]
+                    nxt += 1
+                    if r.kind == "rhs":
+                        rhs_q[r.target].append(r)
+                    else:
+                        mat_q.append(r)
+                # new operators: admitted by HBM, at most `workers` at a time
+                inflight_bytes = sum(v[1] for v in inflight.values())
+                while mat_q and len(inflight) < self.workers:
+                    r = mat_q[0]
+                    need = self.matrix_bytes(r.m)
+                    cap = self.hbm_budget if self.hbm_budget is not None else None
+                    if cap is not None and need > cap:
+                        mat_q.popleft()
+                        self.stats["rejected"] += 1
+                        results.append(Result(r.rid, "matrix", r.m ** 3, r.t_arrival, now, clock() - t0, 0,
+                                              amg.AMG_ERR_OOM))
+                        continue
+                    if not self._hbm_ok(need, inflight_bytes):
+                        break
+                    mat_q.popleft()
+                    inflight[pool.submit(self._solve_matrix, r, t0, clock)] = (r, need)
+                    inflight_bytes += need
+                self.stats["max_matrix_inflight"] = max(self.stats["max_matrix_inflight"], len(inflight))
+                for f in [f for f in inflight if f.done()]:
+                    inflight.pop(f)
+                    results.append(f.result())
+                # right-hand sides: admitted into free slots at the iteration boundary
+                for i, sl in enumerate(self.slots):
+                    while rhs_q[i] and free[i]:
+                        r = rhs_q[i].popleft()
+                        s = free[i].pop(0)
+                        with torch.cuda.stream(sl.tstream):
+                            b = rhs_for(r, self.n[i])
+                            sl.admit(s, b)
+                        running[i][s] = (r, clock() - t0)
+                active = [i for i in range(len(self.slots)) if running[i]]
+                self.stats["max_running_slots"] = max(self.stats["max_running_slots"],
+                                                      sum(len(running[i]) for i in active))
+                for i in active:
+                    self.slots[i].step()
+                self.stats["steps"] += len(active)
+                for i in active:
+                    state, iters = self.slots[i].poll()
+                    for s in list(running[i]):
+                        if state[s] == amg.SLOT_RUNNING:
+                            continue
+                        r, t_start = running[i].pop(s)
+                        with torch.cuda.stream(self.slots[i].tstream):
+                            x = self.slots[i].retire(s)
+                        self.slots[i].tstream.synchronize()
+                        st = amg.AMG_OK if state[s] == amg.SLOT_CONVERGED else int(state[s])
+                        results.append(Result(r.rid, "rhs", self.n[i], r.t_arrival, t_start, clock() - t0,
+                                              int(iters[s]), st, slot=s, x=x if self.keep_x else None))
+                        free[i].append(s)
+                        free[i].sort()
+                if not active:
+                    # idle: wait for the next arrival or a finishing set-up
+                    wait = 0.0005
+                    if nxt < len(reqs) and not inflight and not mat_q:
+                        wait = max(0.0, reqs[nxt].t_arrival - (clock() - t0))
+                    time.sleep(min(wait, 0.002))
+        finally:
+            pool.shutdown(wait=True)
+        return sorted(results, key=lambda r: r.rid)
+
+
+def resident_operators(sizes=(48, 96, 128, 160), sigma: float = 1.0, seed0: int = 40):
+    """The resident operators of the serving workload (device-generated diffusion, seeds seed0 + i)."""
+    return [pr.diffusion3d_device(m, sigma, seed0 + i) for i, m in enumerate(sizes)]
