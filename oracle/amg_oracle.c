@@ -143,6 +143,94 @@ int or_strength(int n, const int *rp, const int *ci, const double *a, double the
 }
 
 /* ------------------------------------------------------------------ */
+/* Nodal (block) strength for systems with bs unknowns per node, numbered */
+/* node-major (unknown i belongs to node i / bs, component i % bs).  This */
+/* is the block form of the scaled measure (Eq. sco, Sec. 2.2) with       */
+/* Frobenius norms of the bs x bs blocks A_IJ:                            */
+/*   s_IJ = ||A_IJ||_F / sqrt(||A_II||_F ||A_JJ||_F),                     */
+/*   J strongly influences I iff J != I, m_I = max_{K != I} s_IK > 0 and   */
+/*   s_IJ >= theta * m_I.                                                 */
+/* ||A_IJ||_F^2 sums a^2 over the rows of node I in order and, within a   */
+/* row, over the columns of node J in ascending order.                    */
+/* Outputs: the node graph (Nrp[nn + 1], Nci[<= nnz], node J present iff  */
+/* some row of I has a column of J), its strength SN, and the unknown-    */
+/* wise strength S[p] = 1 iff column ci[p] has the row's component, lies  */
+/* in another node J, and SN(I, J).                                       */
+/* ------------------------------------------------------------------ */
+static int cmp_int(const void *x, const void *y);
+
+static int node_pos(const int *Nrp, const int *Nci, int I, int J) {
+  int lo = Nrp[I], hi = Nrp[I + 1] - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) / 2;
+    if (Nci[mid] == J) return mid;
+    if (Nci[mid] < J) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+int or_block_strength(int n, const int *rp, const int *ci, const double *a, int bs, double theta, int *nn_out,
+                      int *Nrp, int *Nci, unsigned char *SN, unsigned char *S) {
+  if (bs < 1 || n % bs) return OR_ERR_ARG;
+  int nn = n / bs;
+  *nn_out = nn;
+  int *tmp = (int *)malloc(((size_t)rp[n] + 1) * sizeof(int));
+  if (!tmp) return OR_ERR_MEM;
+  Nrp[0] = 0;
+  for (int I = 0; I < nn; ++I) {
+    int cnt = 0;
+    for (int c = 0; c < bs; ++c)
+      for (int p = rp[I * bs + c]; p < rp[I * bs + c + 1]; ++p) tmp[cnt++] = ci[p] / bs;
+    qsort(tmp, (size_t)cnt, sizeof(int), cmp_int);
+    int u = 0;
+    for (int t = 0; t < cnt; ++t)
+      if (u == 0 || tmp[t] != tmp[u - 1]) tmp[u++] = tmp[t];
+    memcpy(Nci + Nrp[I], tmp, (size_t)u * sizeof(int));
+    Nrp[I + 1] = Nrp[I] + u;
+  }
+  free(tmp);
+  int nne = Nrp[nn];
+  double *F = (double *)malloc(((size_t)nne + 1) * sizeof(double));
+  double *dn = (double *)calloc((size_t)nn + 1, sizeof(double));
+  if (!F || !dn) {
+    free(F); free(dn);
+    return OR_ERR_MEM;
+  }
+  for (int I = 0; I < nn; ++I) {
+    for (int e = Nrp[I]; e < Nrp[I + 1]; ++e) {
+      int J = Nci[e];
+      double f2 = 0.0;
+      for (int c = 0; c < bs; ++c)
+        for (int p = rp[I * bs + c]; p < rp[I * bs + c + 1]; ++p)
+          if (ci[p] / bs == J) f2 += a[p] * a[p];
+      F[e] = sqrt(f2);
+      if (J == I) dn[I] = F[e];
+    }
+  }
+  for (int I = 0; I < nn; ++I) {
+    double m = 0.0;
+    for (int e = Nrp[I]; e < Nrp[I + 1]; ++e) {
+      int J = Nci[e];
+      double den = sqrt(dn[I] * dn[J]);
+      F[e] = (den > 0.0) ? F[e] / den : 0.0; /* F now holds s_IJ */
+      if (J != I && F[e] > m) m = F[e];
+    }
+    for (int e = Nrp[I]; e < Nrp[I + 1]; ++e)
+      SN[e] = (Nci[e] != I && m > 0.0 && F[e] >= theta * m) ? 1 : 0;
+  }
+  for (int i = 0; i < n; ++i) {
+    int I = i / bs;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      int j = ci[p], J = j / bs;
+      S[p] = (j % bs == i % bs && J != I && SN[node_pos(Nrp, Nci, I, J)]) ? 1 : 0;
+    }
+  }
+  free(F); free(dn);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* SplitMix64 (Steele, Lea & Flood 2014), used counter-based:             */
 /* output number c (c = 1, 2, ...) of the generator seeded with `seed` is  */
 /* mix(seed + c * 0x9E3779B97F4A7C15).  The PMIS measure of point i on     */
@@ -250,9 +338,29 @@ int or_pmis(int n, const int *rp, const int *ci, const unsigned char *S, uint64_
 /*   w_ij = -(alpha * a_ij) / at  (a_ij < 0),  -(beta * a_ij) / at  (a_ij > 0) */
 /* Empty P_i gives an empty row.  Capacity `cap` bounds nnz(P).           */
 /* ------------------------------------------------------------------ */
+/* Systems (block size bs > 1, unknowns numbered node-major): unknown-wise  */
+/* interpolation.  Row i only sees the columns of its own component        */
+/* (j % bs == i % bs): N_i, the sums and the diagonal come from those.     */
+static int direct_interp(int n, const int *rp, const int *ci, const double *a, const unsigned char *S,
+                         const signed char *cf, int bs, int *cidx, int *nc_out, int *Prp, int *Pci, double *Pv,
+                         long long cap);
+
 int or_direct_interp(int n, const int *rp, const int *ci, const double *a, const unsigned char *S,
                      const signed char *cf, int *cidx, int *nc_out, int *Prp, int *Pci, double *Pv,
                      long long cap) {
+  return direct_interp(n, rp, ci, a, S, cf, 1, cidx, nc_out, Prp, Pci, Pv, cap);
+}
+
+int or_direct_interp_bs(int n, const int *rp, const int *ci, const double *a, const unsigned char *S,
+                        const signed char *cf, int bs, int *cidx, int *nc_out, int *Prp, int *Pci, double *Pv,
+                        long long cap) {
+  if (bs < 1 || n % bs) return OR_ERR_ARG;
+  return direct_interp(n, rp, ci, a, S, cf, bs, cidx, nc_out, Prp, Pci, Pv, cap);
+}
+
+static int direct_interp(int n, const int *rp, const int *ci, const double *a, const unsigned char *S,
+                         const signed char *cf, int bs, int *cidx, int *nc_out, int *Prp, int *Pci, double *Pv,
+                         long long cap) {
   int nc = 0;
   for (int i = 0; i < n; ++i) cidx[i] = cf[i] ? nc++ : -1;
   *nc_out = nc;
@@ -272,6 +380,7 @@ int or_direct_interp(int n, const int *rp, const int *ci, const double *a, const
     for (int p = rp[i]; p < rp[i + 1]; ++p) {
       int j = ci[p];
       double v = a[p];
+      if (j % bs != i % bs) continue; /* another component: not a neighbour here */
       if (j == i) {
         aii = v;
         continue;
@@ -478,11 +587,23 @@ void or_jacobi_sweep(int n, const int *rp, const int *ci, const double *a, doubl
 /* ------------------------------------------------------------------ */
 void or_free(or_hier *h);
 
+int or_setup_bs(int n, const int *rp, const int *ci, const double *a, double theta, uint64_t seed,
+                int max_coarse, int max_levels, double omega, int nu1, int nu2, int bs, or_hier **out);
+
 int or_setup(int n, const int *rp, const int *ci, const double *a, double theta, uint64_t seed,
              int max_coarse, int max_levels, double omega, int nu1, int nu2, or_hier **out) {
+  return or_setup_bs(n, rp, ci, a, theta, seed, max_coarse, max_levels, omega, nu1, nu2, 1, out);
+}
+
+/* Algorithm 1.  bs = 1: scalar strength and PMIS on the unknowns.  bs > 1  */
+/* (systems, node-major unknowns): nodal block strength, PMIS on the node   */
+/* graph (the measure counter runs over node indices), every unknown of a   */
+/* node takes the node's C/F label, and unknown-wise direct interpolation.  */
+int or_setup_bs(int n, const int *rp, const int *ci, const double *a, double theta, uint64_t seed,
+                int max_coarse, int max_levels, double omega, int nu1, int nu2, int bs, or_hier **out) {
   *out = NULL;
   if (!(theta > 0.0 && theta <= 1.0) || max_levels < 1 || max_levels > OR_MAX_LEVELS || nu1 < 0 ||
-      nu2 < 0 || max_coarse < 1)
+      nu2 < 0 || max_coarse < 1 || bs < 1 || n % bs)
     return OR_ERR_ARG;
   int st = or_check_csr(n, rp, ci, a);
   if (st) return st;
@@ -511,8 +632,22 @@ int or_setup(int n, const int *rp, const int *ci, const double *a, double theta,
     if (!last) {
       h->S[k] = (unsigned char *)malloc((size_t)A->nnz + 1);
       h->cf[k] = (signed char *)malloc((size_t)nk);
-      or_strength(nk, A->rp, A->ci, A->v, theta, h->S[k]);
-      st = or_pmis(nk, A->rp, A->ci, h->S[k], seed, k, h->cf[k]);
+      if (bs == 1) {
+        or_strength(nk, A->rp, A->ci, A->v, theta, h->S[k]);
+        st = or_pmis(nk, A->rp, A->ci, h->S[k], seed, k, h->cf[k]);
+      } else {
+        int nn = 0;
+        int *Nrp = (int *)malloc(((size_t)nk / bs + 1) * sizeof(int));
+        int *Nci = (int *)malloc(((size_t)A->nnz + 1) * sizeof(int));
+        unsigned char *SN = (unsigned char *)malloc((size_t)A->nnz + 1);
+        signed char *cfn = (signed char *)malloc((size_t)nk / bs + 1);
+        st = (Nrp && Nci && SN && cfn) ? OR_OK : OR_ERR_MEM;
+        if (!st) st = or_block_strength(nk, A->rp, A->ci, A->v, bs, theta, &nn, Nrp, Nci, SN, h->S[k]);
+        if (!st) st = or_pmis(nn, Nrp, Nci, SN, seed, k, cfn);
+        if (!st)
+          for (int i = 0; i < nk; ++i) h->cf[k][i] = cfn[i / bs];
+        free(Nrp); free(Nci); free(SN); free(cfn);
+      }
       if (st) {
         or_free(h);
         return st;
@@ -530,7 +665,7 @@ int or_setup(int n, const int *rp, const int *ci, const double *a, double theta,
         }
         int *cidx = (int *)malloc((size_t)nk * sizeof(int));
         int ncc = 0;
-        st = or_direct_interp(nk, A->rp, A->ci, A->v, h->S[k], h->cf[k], cidx, &ncc, P->rp, P->ci, P->v, cap);
+        st = direct_interp(nk, A->rp, A->ci, A->v, h->S[k], h->cf[k], bs, cidx, &ncc, P->rp, P->ci, P->v, cap);
         free(cidx);
         if (st) {
           or_free(h);

@@ -51,6 +51,12 @@ def lib():
         L.or_pmis.argtypes = [C.c_int, _i32p, _i32p, _u8p, C.c_uint64, C.c_int, _i8p]
         L.or_direct_interp.argtypes = [C.c_int, _i32p, _i32p, _f64p, _u8p, _i8p, _i32p, C.POINTER(C.c_int),
                                        _i32p, _i32p, _f64p, C.c_longlong]
+        L.or_direct_interp_bs.argtypes = [C.c_int, _i32p, _i32p, _f64p, _u8p, _i8p, C.c_int, _i32p,
+                                          C.POINTER(C.c_int), _i32p, _i32p, _f64p, C.c_longlong]
+        L.or_block_strength.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_int, C.c_double, C.POINTER(C.c_int),
+                                        _i32p, _i32p, _u8p, _u8p]
+        L.or_setup_bs.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_double, C.c_uint64, C.c_int, C.c_int,
+                                  C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]
         L.or_galerkin.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_int, _i32p, _i32p, _f64p,
                                   C.POINTER(C.c_int), C.POINTER(C.POINTER(C.c_int)),
                                   C.POINTER(C.POINTER(C.c_int)), C.POINTER(C.POINTER(C.c_double))]
@@ -110,16 +116,31 @@ def pmis(A, S: np.ndarray, seed: int, level: int = 0) -> np.ndarray:
     return cf
 
 
-def direct_interp(A, S: np.ndarray, cf: np.ndarray):
-    """Returns (P_rowptr, P_col, P_val, nc)."""
+def block_strength(A, bs: int, theta: float):
+    """Nodal block strength: returns (node rowptr, node col, node strength, unknown-wise strength)."""
+    nn = C.c_int(0)
+    Nrp = np.zeros(A.n // bs + 1, np.int32)
+    Nci = np.zeros(max(A.nnz, 1), np.int32)
+    SN = np.zeros(max(A.nnz, 1), np.uint8)
+    S = np.zeros(max(A.nnz, 1), np.uint8)
+    st = lib().or_block_strength(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), bs, theta, C.byref(nn), Nrp, Nci,
+                                 SN, S)
+    if st:
+        raise RuntimeError(f"or_block_strength failed: {st}")
+    e = int(Nrp[-1])
+    return Nrp, Nci[:e].copy(), SN[:e].copy(), S[: A.nnz].copy()
+
+
+def direct_interp(A, S: np.ndarray, cf: np.ndarray, bs: int = 1):
+    """Returns (P_rowptr, P_col, P_val, nc); bs > 1 interpolates unknown-wise."""
     cap = A.nnz + A.n
     rp = np.zeros(A.n + 1, np.int32)
     ci = np.zeros(cap, np.int32)
     v = np.zeros(cap, np.float64)
     cidx = np.zeros(A.n, np.int32)
     nc = C.c_int(0)
-    st = lib().or_direct_interp(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), np.ascontiguousarray(S, np.uint8),
-                                np.ascontiguousarray(cf, np.int8), cidx, C.byref(nc), rp, ci, v, cap)
+    st = lib().or_direct_interp_bs(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), np.ascontiguousarray(S, np.uint8),
+                                   np.ascontiguousarray(cf, np.int8), bs, cidx, C.byref(nc), rp, ci, v, cap)
     if st:
         raise RuntimeError(f"or_direct_interp failed: {st}")
     nnz = int(rp[-1])
@@ -181,10 +202,12 @@ class Level:
 class Hierarchy:
     """Oracle AMG hierarchy (Algorithm 1) with V-cycle and PCG (Algorithm 2, Sec. 4)."""
 
-    def __init__(self, A, theta=0.25, seed=0, max_coarse=64, max_levels=25, omega=2.0 / 3.0, nu1=1, nu2=1):
+    def __init__(self, A, theta=0.25, seed=0, max_coarse=64, max_levels=25, omega=2.0 / 3.0, nu1=1, nu2=1,
+                 block_size=1):
         self._keep = (_i32(A.rowptr), _i32(A.col), _f64(A.val))
         h = C.c_void_p()
-        st = lib().or_setup(A.n, *self._keep, theta, seed, max_coarse, max_levels, omega, nu1, nu2, C.byref(h))
+        st = lib().or_setup_bs(A.n, *self._keep, theta, seed, max_coarse, max_levels, omega, nu1, nu2, block_size,
+                               C.byref(h))
         if st:
             raise RuntimeError(f"or_setup failed: {st}")
         self.h = h

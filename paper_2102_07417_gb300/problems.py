@@ -320,3 +320,126 @@ def diffusion3d_device(N: int, sigma: float, seed: int, device="cuda", stream=No
         val = vals[mask].contiguous()
         rp = rowptr.to(torch.int32)
     return CSR(n, rp, col, val, {"kind": "diffusion3d_device", "N": N, "sigma": sigma, "seed": seed})
+
+
+def q1_hex_stiffness(nu: float) -> np.ndarray:
+    """24 x 24 stiffness of the unit-cube trilinear (Q1) hexahedron for E = 1, by 2x2x2 Gauss
+    quadrature.  Local node l = a + 2b + 4c sits at (a, b, c) in {0, 1}^3; dof 3l + comp."""
+    lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = 1.0 / (2.0 * (1.0 + nu))
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[np.arange(3), np.arange(3)] = lam + 2.0 * mu
+    D[np.arange(3, 6), np.arange(3, 6)] = mu
+    corners = np.array([[a, b, c] for c in (0, 1) for b in (0, 1) for a in (0, 1)], dtype=float)
+    sgn = 2.0 * corners - 1.0  # reference coordinates of the corners in [-1, 1]^3
+    gp = np.array([-1.0, 1.0]) / np.sqrt(3.0)
+    K = np.zeros((24, 24))
+    for xi in gp:
+        for eta in gp:
+            for zeta in gp:
+                q = np.array([xi, eta, zeta])
+                # dN_l/dxi_d = sgn_ld / 8 * prod_{e != d} (1 + sgn_le q_e); x = (xi + 1) / 2 so d/dx = 2 d/dxi
+                dN = np.zeros((8, 3))
+                for d in range(3):
+                    o = [e for e in range(3) if e != d]
+                    dN[:, d] = sgn[:, d] / 8.0 * (1 + sgn[:, o[0]] * q[o[0]]) * (1 + sgn[:, o[1]] * q[o[1]]) * 2.0
+                B = np.zeros((6, 24))
+                for l in range(8):
+                    gx, gy, gz = dN[l]
+                    B[0, 3 * l] = gx
+                    B[1, 3 * l + 1] = gy
+                    B[2, 3 * l + 2] = gz
+                    B[3, 3 * l], B[3, 3 * l + 1] = gy, gx
+                    B[4, 3 * l + 1], B[4, 3 * l + 2] = gz, gy
+                    B[5, 3 * l], B[5, 3 * l + 2] = gz, gx
+                K += B.T @ D @ B * (1.0 / 8.0)  # det(J) = 1/8, Gauss weights 1
+    return 0.5 * (K + K.T)  # exactly symmetric
+
+
+def elasticity3d(ne: int, nu: float = 0.3, layer: int = 8, E=(1.0, 1e3)) -> CSR:
+    """Linear elasticity on an ne^3 grid of unit Q1 hexahedra, Young's modulus E[0] / E[1] in
+    alternating element layers of thickness ``layer`` along z, the z = 0 face clamped (its nodes
+    eliminated).  Unknowns are node-major (x, y, z displacement per node); nodes are
+    lexicographic with x fastest over the (ne+1) x (ne+1) x ne free nodes.  Every coupled node
+    pair stores its full 3x3 block (entries that vanish are kept as explicit zeros), so
+    nnz = 9 * (3(ne+1) - 2)^2 * (3 ne - 2)."""
+    Kr = q1_hex_stiffness(nu).reshape(8, 3, 8, 3)
+    m = ne + 1  # nodes per x / y line
+    nz = ne  # free node layers (k = 1 .. ne)
+    nn = m * m * nz
+    I = np.arange(nn, dtype=np.int64)
+    ix, iy, iz = I % m, (I // m) % m, I // (m * m) + 1  # iz: global layer index 1..ne
+    ez_layer = np.arange(ne) // layer
+    Ee = np.where(ez_layer % 2 == 0, E[0], E[1])  # modulus of element layer ez
+    offs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    blocks = np.zeros((nn, 27, 3, 3))
+    present = np.zeros((nn, 27), dtype=bool)
+    for o, (dx, dy, dz) in enumerate(offs):
+        jx, jy, jz = ix + dx, iy + dy, iz + dz
+        present[:, o] = (jx >= 0) & (jx < m) & (jy >= 0) & (jy < m) & (jz >= 1) & (jz <= ne)
+        for a in (0, 1):
+            for b in (0, 1):
+                for c in (0, 1):
+                    # element with node I at local (a, b, c); J at local (a+dx, b+dy, c+dz)
+                    la, lb, lc = a + dx, b + dy, c + dz
+                    if not (0 <= la <= 1 and 0 <= lb <= 1 and 0 <= lc <= 1):
+                        continue
+                    ex, ey, ez = ix - a, iy - b, iz - c
+                    ok = present[:, o] & (ex >= 0) & (ex < ne) & (ey >= 0) & (ey < ne) & (ez >= 0) & (ez < ne)
+                    li, lj = a + 2 * b + 4 * c, la + 2 * lb + 4 * lc
+                    w = np.where(ok, Ee[np.clip(ez, 0, ne - 1)], 0.0)
+                    blocks[:, o] += w[:, None, None] * Kr[li, :, lj, :][None]
+    J = I[:, None] + np.array([dx + m * dy + m * m * dz for dx, dy, dz in offs])[None, :]
+    # exact symmetry: block (I, o) and the transpose of block (J, 26 - o) summed the same
+    # contributions in different orders; replace both by their mean
+    Jc = np.where(present, J, 0)
+    mirror = blocks[Jc, 26 - np.arange(27)[None, :]].transpose(0, 1, 3, 2)
+    blocks = np.where(present[:, :, None, None], 0.5 * (blocks + mirror), 0.0)
+    n = 3 * nn
+    # row (I, c): for each neighbour o (ascending J), dofs 3J + d
+    cols = (3 * J[:, None, :, None] + np.arange(3)[None, None, None, :])  # (nn, 1, 27, 3)
+    cols = np.broadcast_to(cols, (nn, 3, 27, 3)).reshape(n, 81)
+    vals = blocks.transpose(0, 2, 1, 3).reshape(n, 81)  # [I, c, o, d]
+    mask = np.broadcast_to(present[:, None, :, None], (nn, 3, 27, 3)).reshape(n, 81)
+    return _finish(n, cols, vals, mask, {"kind": "elasticity3d", "ne": ne, "nu": nu, "layer": layer,
+                                         "E": list(E)})
+
+
+def nnz_elasticity3d(ne: int) -> int:
+    """Closed form: 9 (3(ne+1) - 2)^2 (3 ne - 2) for ``elasticity3d``."""
+    return 9 * (3 * (ne + 1) - 2) ** 2 * (3 * ne - 2)
+
+
+def config4(ne: int = 64, k: int = 16) -> tuple[CSR, np.ndarray]:
+    """Q1 elasticity on ne^3 elements (64^3 by default: 811,200 free dofs) with k right-hand
+    sides (uniform[-1, 1] per dof, seed 3), returned as an n x k row-major block."""
+    A = elasticity3d(ne)
+    rng = np.random.Generator(np.random.PCG64(3))
+    return A, rng.uniform(-1.0, 1.0, size=(A.n, k))
+
+
+def kron_identity(A: CSR, bs: int, full_blocks: bool = True) -> CSR:
+    """The operator A (x) I_bs in node-major order: unknown (I, c) = bs I + c couples to (J, c)
+    with a_IJ.  With ``full_blocks`` every coupled node pair stores its whole bs x bs block
+    (the off-component entries as explicit zeros), as block set-up requires."""
+    n = A.n * bs
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    deg = np.diff(A.rowptr)
+    w = (bs if full_blocks else 1)
+    cols = np.zeros((n, int(deg.max()) * w), dtype=np.int64)
+    vals = np.zeros_like(cols, dtype=np.float64)
+    mask = np.zeros_like(cols, dtype=bool)
+    pos = np.arange(A.nnz) - A.rowptr[rows]
+    for c in range(bs):
+        r = rows * bs + c
+        if full_blocks:
+            for d in range(bs):
+                cols[r, pos * bs + d] = A.col * bs + d
+                vals[r, pos * bs + d] = A.val if d == c else 0.0
+                mask[r, pos * bs + d] = True
+        else:
+            cols[r, pos] = A.col * bs + c
+            vals[r, pos] = A.val
+            mask[r, pos] = True
+    return _finish(n, cols, vals, mask, {"kind": "kron_identity", "bs": bs, "full_blocks": full_blocks})

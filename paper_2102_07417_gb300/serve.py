@@ -62,10 +62,11 @@ class Result:
 
 
 def make_requests(count: int = 512, rate: float = 200.0, seed: int = 4, frac_matrix: float = 0.3,
-                  n_resident: int = 4, m_range=(32, 160)) -> list[Request]:
+                  n_resident: int = 4, m_range=(32, 160), seed_base: int = 1000) -> list[Request]:
     """Poisson arrivals at ``rate`` req/s; each request is a new matrix with probability
-    ``frac_matrix`` (grid size m log-uniform in ``m_range``), else a new right-hand side for a
-    resident operator drawn uniformly."""
+    ``frac_matrix`` (grid size m = round(exp(U[ln lo, ln hi]))), else a new right-hand side for a
+    resident operator drawn uniformly.  ``seed`` drives the arrivals and choices; request r
+    draws its coefficients / right-hand side from seed ``seed_base + r``."""
     rng = np.random.Generator(np.random.PCG64(seed))
     gaps = rng.exponential(1.0 / rate, size=count)
     t = np.cumsum(gaps) - gaps[0]  # the first request arrives at t = 0
@@ -73,8 +74,7 @@ def make_requests(count: int = 512, rate: float = 200.0, seed: int = 4, frac_mat
     target = rng.integers(0, n_resident, size=count)
     lo, hi = math.log(m_range[0]), math.log(m_range[1])
     m = np.rint(np.exp(rng.uniform(lo, hi, size=count))).astype(int)
-    seeds = rng.integers(1, 2**62, size=count)
-    return [Request(i, float(t[i]), "matrix" if is_mat[i] else "rhs", int(target[i]), int(m[i]), int(seeds[i]))
+    return [Request(i, float(t[i]), "matrix" if is_mat[i] else "rhs", int(target[i]), int(m[i]), seed_base + i)
             for i in range(count)]
 
 
