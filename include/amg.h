@@ -92,7 +92,15 @@ typedef struct {
   double omega;       /* Jacobi damping of the smoother S = I - omega D^-1 A (Eq. smoother); 2/3 */
   int32_t nu1, nu2;   /* pre- and post-smoothing steps (Eq. twoGridOp), 0..8 each; 1, 1 */
   int32_t precision;  /* AMG_PREC_*; AMG_PREC_FP64 */
-  int32_t block_size; /* unknowns per node for nodal strength; 1 (only 1 is supported) */
+  int32_t block_size; /* unknowns per node, 1..8; 1.  bs > 1 (systems such as elasticity): the
+                       * unknowns are node-major (unknown i is component i % bs of node i / bs),
+                       * every coupled node pair must be stored as a full bs x bs block
+                       * (explicit zeros allowed; else AMG_ERR_INVALID_ARG) and n % bs == 0.
+                       * Strength is nodal: s_IJ = ||A_IJ||_F / sqrt(||A_II||_F ||A_JJ||_F)
+                       * (the block form of Eq. sco), J strong for I iff s_IJ >= theta *
+                       * max_{K != I} s_IK; PMIS runs on the node graph; every unknown takes its
+                       * node's C/F label; interpolation is unknown-wise (direct interpolation
+                       * over the same-component couplings only). */
 } amg_params;
 
 /* Fills *p with the defaults above.  Returns AMG_ERR_INVALID_ARG if p is NULL. */

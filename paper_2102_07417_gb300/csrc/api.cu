@@ -148,10 +148,7 @@ static int check_params(const amg_params &p) {
   if (!(p.omega > 0.0 && p.omega < 2.0)) return bad("omega must be in (0, 2)");
   if (p.nu1 < 0 || p.nu1 > 8 || p.nu2 < 0 || p.nu2 > 8) return bad("nu1, nu2 must be in 0..8");
   if (p.precision < AMG_PREC_FP64 || p.precision > AMG_PREC_FP32_BF16PR) return bad("unknown precision mode");
-  if (p.block_size != 1) {
-    amg::set_error("block_size other than 1 is not supported");
-    return AMG_ERR_UNSUPPORTED;
-  }
+  if (p.block_size < 1 || p.block_size > 8) return bad("block_size must be in 1..8");
   return AMG_OK;
 }
 
@@ -173,6 +170,7 @@ int amg_setup(const amg_csr *A, const amg_params *params, const amg_allocator *a
   else amg_params_default(&prm);
   int st = check_params(prm);
   if (st) return st;
+  if (A->n % prm.block_size) return bad("n must be a multiple of block_size");
   if (alloc && ((alloc->alloc == nullptr) != (alloc->free == nullptr))) return bad("allocator needs both alloc and free");
   amg_hierarchy *h = new amg_hierarchy();
   h->prm = prm;

@@ -269,6 +269,114 @@ __global__ void k_cf_out(int n, const int8_t *__restrict__ st, int8_t *__restric
   isC[i] = c;
 }
 
+// ---------------------------------------------- systems: nodal blocks --
+// Unknowns are node-major: unknown i is component i % bs of node i / bs, and
+// every coupled node pair stores its full bs x bs block (checked by
+// k_block_check), so node I's rows share one column pattern of whole blocks.
+
+// flags[5] = 1 if some node's rows are not whole, aligned bs x bs blocks.
+__global__ void k_block_check(int nn, int bs, const int *__restrict__ rp, const int *__restrict__ ci, int *flags) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nn) return;
+  const int b0 = rp[I * bs], len = rp[I * bs + 1] - b0;
+  bool ok = len % bs == 0;
+  for (int c = 1; c < bs && ok; ++c) ok = rp[I * bs + c + 1] - rp[I * bs + c] == len;
+  for (int t = 0; ok && t < len; t += bs) {
+    const int J = ci[b0 + t] / bs;
+    for (int c = 0; c < bs && ok; ++c)
+      for (int d = 0; d < bs && ok; ++d) ok = ci[rp[I * bs + c] + t + d] == J * bs + d;
+  }
+  if (!ok) flags[5] = 1;
+}
+
+// Node graph: nrp[I] = rp[bs I] / bs^2, nci = the node of each block.
+__global__ void k_node_graph(int nn, int bs, const int *__restrict__ rp, const int *__restrict__ ci,
+                             int *__restrict__ nrp, int *__restrict__ nci) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I > nn) return;
+  const int b0 = rp[I * bs];
+  nrp[I] = b0 / (bs * bs);
+  if (I == nn) return;
+  const int len = rp[I * bs + 1] - b0;
+  for (int t = 0; t < len; t += bs) nci[b0 / (bs * bs) + t / bs] = ci[b0 + t] / bs;
+}
+
+// ||A_IJ||_F of the block at offset t of node I's rows: a^2 summed over the
+// rows in order and the block's columns in ascending order.
+__device__ __forceinline__ double block_fnorm(int I, int bs, int t, const int *__restrict__ rp,
+                                              const double *__restrict__ a) {
+  double f2 = 0.0;
+  for (int c = 0; c < bs; ++c) {
+    const int q = rp[I * bs + c] + t;
+    for (int d = 0; d < bs; ++d) {
+      const double v = a[q + d];
+      f2 = __dadd_rn(f2, __dmul_rn(v, v));
+    }
+  }
+  return __dsqrt_rn(f2);
+}
+
+// dn[I] = ||A_II||_F.
+__global__ void k_block_dnorm(int nn, int bs, const int *__restrict__ rp, const int *__restrict__ ci,
+                              const double *__restrict__ a, double *__restrict__ dn) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nn) return;
+  const int b0 = rp[I * bs], len = rp[I * bs + 1] - b0;
+  double f = 0.0;
+  for (int t = 0; t < len; t += bs)
+    if (ci[b0 + t] / bs == I) f = block_fnorm(I, bs, t, rp, a);
+  dn[I] = f;
+}
+
+// Nodal strength: s_IJ = ||A_IJ||_F / sqrt(||A_II||_F ||A_JJ||_F); J strong
+// for I iff J != I, m_I = max_{K != I} s_IK > 0 and s_IJ >= theta m_I.
+// sv holds s_IJ per node-graph entry (scratch).
+__global__ void k_block_strength(int nn, int bs, const int *__restrict__ rp, const double *__restrict__ a,
+                                 const int *__restrict__ nrp, const int *__restrict__ nci,
+                                 const double *__restrict__ dn, double theta, double *__restrict__ sv,
+                                 uint8_t *__restrict__ SN) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nn) return;
+  const int e0 = nrp[I], e1 = nrp[I + 1];
+  const double dI = dn[I];
+  double m = 0.0;
+  for (int e = e0; e < e1; ++e) {
+    const int J = nci[e];
+    const double f = block_fnorm(I, bs, (e - e0) * bs, rp, a);
+    const double den = __dsqrt_rn(__dmul_rn(dI, dn[J]));
+    const double sIJ = den > 0.0 ? __ddiv_rn(f, den) : 0.0;
+    sv[e] = sIJ;
+    if (J != I && sIJ > m) m = sIJ;
+  }
+  const double thr = __dmul_rn(theta, m);
+  for (int e = e0; e < e1; ++e) SN[e] = (nci[e] != I && m > 0.0 && sv[e] >= thr) ? 1 : 0;
+}
+
+// Every unknown takes its node's C/F label.
+__global__ void k_cf_expand(int nn, int bs, const int8_t *__restrict__ st, int8_t *__restrict__ cf,
+                            int *__restrict__ isC) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nn) return;
+  const int c = st[I] == ST_C;
+  for (int k = 0; k < bs; ++k) {
+    cf[I * bs + k] = (int8_t)c;
+    isC[I * bs + k] = c;
+  }
+}
+
+// Unknown-wise strength: S[p] = 1 iff column ci[p] has row i's component,
+// lies in another node J, and J strongly influences node I.
+__global__ void k_dof_strength(int n, int bs, const int *__restrict__ rp, const int *__restrict__ ci,
+                               const int *__restrict__ nrp, const uint8_t *__restrict__ SN, uint8_t *__restrict__ S) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int I = i / bs, comp = i % bs, b = rp[i];
+  for (int p = b; p < rp[i + 1]; ++p) {
+    const int j = ci[p];
+    S[p] = (j % bs == comp && j / bs != I && SN[nrp[I] + (p - b) / bs]) ? 1 : 0;
+  }
+}
+
 // ------------------------------------------------------ interpolation --
 __global__ void k_interp_count(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                const uint8_t *__restrict__ S, const int8_t *__restrict__ cf,
@@ -291,7 +399,9 @@ __global__ void k_interp_count(int n, const int *__restrict__ rp, const int *__r
 //   alpha = sum_{N_i} a^- / sum_{P_i} a^-,  beta = sum_{N_i} a^+ / sum_{P_i} a^+,
 //   at = a_ii + sum_{N_i} a^+ when P_i holds no positive entry, else a_ii,
 //   w_ij = -(alpha a_ij) / at for a_ij < 0, -(beta a_ij) / at for a_ij > 0.
-__global__ void k_interp_fill(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+// Systems (bs > 1, node-major unknowns): unknown-wise, row i sees only the
+// columns of its own component (j % bs == i % bs).
+__global__ void k_interp_fill(int n, int bs, const int *__restrict__ rp, const int *__restrict__ ci,
                               const double *__restrict__ a, const uint8_t *__restrict__ S,
                               const int8_t *__restrict__ cf, const int *__restrict__ cidx,
                               const int *__restrict__ prp, int *__restrict__ pci, double *__restrict__ pv) {
@@ -306,9 +416,11 @@ __global__ void k_interp_fill(int n, const int *__restrict__ rp, const int *__re
   double aii = 0.0, sn_neg = 0.0, sn_pos = 0.0, sp_neg = 0.0, sp_pos = 0.0;
   int np = 0;
   const int b = rp[i], e = rp[i + 1];
+  const int comp = i % bs;
   for (int p = b; p < e; ++p) {
     const int j = ci[p];
     const double v = a[p];
+    if (j % bs != comp) continue;
     if (j == i) {
       aii = v;
       continue;
@@ -469,13 +581,13 @@ __global__ void k_interp_count_w(int n, const int *__restrict__ rp, const int *_
 // Direct interpolation, warp per row: lanes stage a chunk of 32 entries in
 // shared memory, lane 0 adds them in ascending column order (the canonical
 // order of the thread-per-row kernel), then lanes form the weights.
-__global__ void __launch_bounds__(256) k_interp_fill_w(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+__global__ void __launch_bounds__(256) k_interp_fill_w(int n, int bs, const int *__restrict__ rp, const int *__restrict__ ci,
                                                        const double *__restrict__ a, const uint8_t *__restrict__ S,
                                                        const int8_t *__restrict__ cf, const int *__restrict__ cidx,
                                                        const int *__restrict__ prp, int *__restrict__ pci,
                                                        double *__restrict__ pv) {
   __shared__ double sv[8][32];
-  __shared__ uint8_t sk[8][32];  // bit 0: off-diagonal, bit 1: in P_i (strong C neighbour)
+  __shared__ uint8_t sk[8][32];  // bit 0: off-diagonal, bit 1: in P_i (strong C neighbour), bit 2: other component
   const int w = threadIdx.x >> 5;
   WARP_ROW_BEGIN
   int pos = prp[i];
@@ -494,7 +606,7 @@ __global__ void __launch_bounds__(256) k_interp_fill_w(int n, const int *__restr
     if (p < e) {
       const int j = ci[p];
       sv[w][lane] = a[p];
-      sk[w][lane] = (uint8_t)((j != i ? 1 : 0) | ((j != i && S[p] && cf[j]) ? 2 : 0));
+      sk[w][lane] = (uint8_t)((j != i ? 1 : 0) | ((j != i && S[p] && cf[j]) ? 2 : 0) | (j % bs != i % bs ? 4 : 0));
     }
     __syncwarp();
     if (lane == 0) {
@@ -502,6 +614,7 @@ __global__ void __launch_bounds__(256) k_interp_fill_w(int n, const int *__restr
       for (int t = 0; t < cnt; ++t) {
         const double v = sv[w][t];
         const uint8_t k = sk[w][t];
+        if (k & 4) continue;
         if (!(k & 1)) {
           aii = v;
           continue;
@@ -777,40 +890,84 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     Buf<int> cidx;
     int nc = 0;
     if (!last) {
+      const int bs = prm.block_size;
       S = Buf<uint8_t>(m, std::max<int64_t>(A.nnz, 1));
-      ST = Buf<uint8_t>(m, std::max<int64_t>(A.nnz, 1));
-      Buf<double> lam(m, n);
-      Buf<int8_t> st0(m, n), st1(m, n);
-      Buf<int> und(m, 1);
       const int g = ceil_div(n, TPB);
-      const double nz = (double)A.nnz, rows = 4.0 * (n + 1);
-      {
-        ProfScope ps(s, AMG_K_STRENGTH, rows + 13.0 * nz);
+      // The graph PMIS runs on: the unknowns (bs = 1) or the nodes (bs > 1).
+      int gn = n;
+      int64_t gnnz = A.nnz;
+      const int *grp = A.rp, *gci = A.ci;
+      const uint8_t *gS = S.p;
+      Buf<int> nrp, nci;
+      Buf<uint8_t> SN;
+      if (bs == 1) {
+        ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n + 1) + 13.0 * A.nnz);
         if (wide) k_strength_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
         else k_strength<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
         AMG_CHECK_LAUNCH();
+      } else {
+        const int nn = n / bs;
+        const int gnn = ceil_div(nn, TPB);
+        {
+          ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n + 1) + 4.0 * A.nnz);
+          k_block_check<<<gnn, TPB, 0, s>>>(nn, bs, A.rp, A.ci, fl.d);
+          AMG_CHECK_LAUNCH();
+        }
+        read_flags(m, fl);
+        if (fl.h[5]) {
+          if (k == 0) fail(AMG_ERR_INVALID_ARG, "block_size > 1 needs every coupled node pair stored as a full block");
+          fail(AMG_ERR_SETUP, "a coarse operator lost its block structure");
+        }
+        const int64_t nne = A.nnz / ((int64_t)bs * bs);
+        nrp = Buf<int>(m, (size_t)nn + 1);
+        nci = Buf<int>(m, std::max<int64_t>(nne, 1));
+        SN = Buf<uint8_t>(m, std::max<int64_t>(nne, 1));
+        Buf<double> dn(m, nn), sv(m, std::max<int64_t>(nne, 1));
+        {
+          ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n + 1) + 12.0 * A.nnz + 8.0 * nn + 13.0 * nne);
+          k_node_graph<<<ceil_div(nn + 1, TPB), TPB, 0, s>>>(nn, bs, A.rp, A.ci, nrp.p, nci.p);
+          AMG_CHECK_LAUNCH();
+          k_block_dnorm<<<gnn, TPB, 0, s>>>(nn, bs, A.rp, A.ci, A.v, dn.p);
+          AMG_CHECK_LAUNCH();
+          k_block_strength<<<gnn, TPB, 0, s>>>(nn, bs, A.rp, A.v, nrp.p, nci.p, dn.p, prm.theta, sv.p, SN.p);
+          AMG_CHECK_LAUNCH();
+          k_dof_strength<<<g, TPB, 0, s>>>(n, bs, A.rp, A.ci, nrp.p, SN.p, S.p);
+          AMG_CHECK_LAUNCH();
+        }
+        gn = nn;
+        gnnz = nne;
+        grp = nrp.p;
+        gci = nci.p;
+        gS = SN.p;
       }
+      const bool gwide = (double)gnnz >= 12.0 * gn && gn < (1 << 18);
+      const int gg = ceil_div(gn, TPB), ggw = ceil_div((int64_t)gn * 32, TPB);
+      const double nz = (double)gnnz, rows = 4.0 * (gn + 1);
+      ST = Buf<uint8_t>(m, std::max<int64_t>(gnnz, 1));
+      Buf<double> lam(m, gn);
+      Buf<int8_t> st0(m, gn), st1(m, gn);
+      Buf<int> und(m, 1);
       {
-        ProfScope ps(s, AMG_K_STRENGTH, rows + 6.0 * nz + 9.0 * n);
-        if (wide) k_pmis_init_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
-        else k_pmis_init<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
+        ProfScope ps(s, AMG_K_STRENGTH, rows + 6.0 * nz + 9.0 * gn);
+        if (gwide) k_pmis_init_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
+        else k_pmis_init<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
         AMG_CHECK_LAUNCH();
       }
       read_flags(m, fl);
       if (fl.h[2]) fail(AMG_ERR_INVALID_ARG, "matrix pattern is not structurally symmetric");
       for (int round = 0;; ++round) {
-        if (round > n + 1) fail(AMG_ERR_SETUP, "PMIS did not terminate");
+        if (round > gn + 1) fail(AMG_ERR_SETUP, "PMIS did not terminate");
         AMG_CUDA(cudaMemsetAsync(und.p, 0, sizeof(int), s));
         {
-          ProfScope ps(s, AMG_K_PMIS, rows + 6.0 * nz + 10.0 * n);
-          if (wide) k_pmis_select_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, st1.p);
-          else k_pmis_select<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, ST.p, lam.p, st0.p, st1.p);
+          ProfScope ps(s, AMG_K_PMIS, rows + 6.0 * nz + 10.0 * gn);
+          if (gwide) k_pmis_select_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, st1.p);
+          else k_pmis_select<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, st1.p);
           AMG_CHECK_LAUNCH();
         }
         {
-          ProfScope ps(s, AMG_K_PMIS, rows + 5.0 * nz + 2.0 * n);
-          if (wide) k_pmis_update_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, S.p, st1.p, st0.p, und.p);
-          else k_pmis_update<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, st1.p, st0.p, und.p);
+          ProfScope ps(s, AMG_K_PMIS, rows + 5.0 * nz + 2.0 * gn);
+          if (gwide) k_pmis_update_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, st1.p, st0.p, und.p);
+          else k_pmis_update<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, st1.p, st0.p, und.p);
           AMG_CHECK_LAUNCH();
         }
         if (read_int(m, und.p) == 0) break;
@@ -819,7 +976,8 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       Buf<int> isC(m, n);
       {
         ProfScope ps(s, AMG_K_PMIS, 6.0 * n);
-        k_cf_out<<<g, TPB, 0, s>>>(n, st0.p, L.cf, isC.p);
+        if (bs == 1) k_cf_out<<<g, TPB, 0, s>>>(n, st0.p, L.cf, isC.p);
+        else k_cf_expand<<<gg, TPB, 0, s>>>(gn, bs, st0.p, L.cf, isC.p);
         AMG_CHECK_LAUNCH();
       }
       cidx = Buf<int>(m, (size_t)n + 1);
@@ -872,8 +1030,10 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       P.v = m.get_n<double>(std::max<int64_t>(P.nnz, 1));
       {
         ProfScope ps(s, AMG_K_INTERP, 8.0 * (n + 1) + 13.0 * A.nnz + 5.0 * n + 12.0 * P.nnz);
-        if (wide_interp) k_interp_fill_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, P.rp, P.ci, P.v);
-        else k_interp_fill<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, P.rp, P.ci, P.v);
+        if (wide_interp)
+          k_interp_fill_w<<<gw, TPB, 0, s>>>(n, prm.block_size, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, P.rp, P.ci, P.v);
+        else
+          k_interp_fill<<<g, TPB, 0, s>>>(n, prm.block_size, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, P.rp, P.ci, P.v);
         AMG_CHECK_LAUNCH();
       }
     }
