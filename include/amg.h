@@ -166,6 +166,15 @@ int amg_pcg_solve_batch(amg_hierarchy *h, int32_t k, const double *B, double *X,
  *                    1 running, 2 converged (||r_j|| < rtol ||b_j||), or a
  *                    negative status (AMG_ERR_NO_CONVERGENCE after maxit
  *                    iterations, AMG_ERR_BREAKDOWN); iters = CG iterations;
+ *   amg_slots_query  the same report without waiting, from the newest step
+ *                    that has finished on the device (a snapshot of the state
+ *                    is copied to pinned host memory at the end of every
+ *                    step); a slot admitted after that step reads as running.
+ *                    steps_done / steps_issued (may be NULL) count the steps
+ *                    finished and launched, so a caller can keep a bounded
+ *                    number in flight;
+ *   amg_slots_wait   blocks until the oldest step still in flight finishes
+ *                    (returns at once when none is);
  *   amg_slots_retire copies the slot's x into `x` (device, n doubles; NULL
  *                    discards it) and frees the slot;
  *   amg_slots_free   waits for the stream and releases the object (before
@@ -179,6 +188,8 @@ int amg_slots_create(amg_hierarchy *h, int32_t capacity, double rtol, int32_t ma
 int amg_slots_admit(amg_slots *s, int32_t slot, const double *b);
 int amg_slots_step(amg_slots *s);
 int amg_slots_poll(amg_slots *s, int32_t *state, int32_t *iters);
+int amg_slots_query(amg_slots *s, int32_t *state, int32_t *iters, int64_t *steps_done, int64_t *steps_issued);
+int amg_slots_wait(amg_slots *s);
 int amg_slots_retire(amg_slots *s, int32_t slot, double *x);
 void amg_slots_free(amg_slots *s);
 

@@ -38,7 +38,7 @@ EXPORTS = ["amg_params_default", "amg_setup", "amg_pcg_solve", "amg_pcg_solve_ba
            "amg_hierarchy_info", "amg_hierarchy_export", "amg_hierarchy_bytes", "amg_free", "amg_profile_enable",
            "amg_profile_read", "amg_profile_filter", "amg_launch_count", "amg_status_string", "amg_last_error",
            "amg_spmv_dot_noalloc", "amg_slots_create", "amg_slots_admit", "amg_slots_step", "amg_slots_poll",
-           "amg_slots_retire", "amg_slots_free"]
+           "amg_slots_query", "amg_slots_wait", "amg_slots_retire", "amg_slots_free"]
 
 
 class AmgError(RuntimeError):
@@ -100,6 +100,8 @@ def load(build_if_missing: bool = True):
     L.amg_slots_step.argtypes = [vp]
     L.amg_slots_poll.argtypes = [vp, vp, vp]
     L.amg_slots_retire.argtypes = [vp, i32, vp]
+    L.amg_slots_query.argtypes = [vp, vp, vp, C.POINTER(i64), C.POINTER(i64)]
+    L.amg_slots_wait.argtypes = [vp]
     L.amg_slots_free.argtypes = [vp]
     L.amg_slots_free.restype = None
     L.amg_spmv.argtypes = [vp, i32, vp, vp, vp]
@@ -352,7 +354,6 @@ class Slots:
         self.stream = _stream_handle(self.tstream)
         self._state = np.zeros(self.capacity, np.int32)
         self._iters = np.zeros(self.capacity, np.int32)
-        self._pending = {}  # slot -> right-hand side tensor kept alive until the next poll
         h = C.c_void_p()
         check(load().amg_slots_create(hier.h, self.capacity, rtol, maxit, self.stream, C.byref(h)), "amg_slots_create")
         self.s = h
@@ -363,15 +364,25 @@ class Slots:
         self.tstream.wait_stream(self._torch.cuda.current_stream())
         b.record_stream(self.tstream)
         check(load().amg_slots_admit(self.s, int(slot), _ptr(b)), "amg_slots_admit")
-        self._pending[int(slot)] = b
 
     def step(self):
         check(load().amg_slots_step(self.s), "amg_slots_step")
 
     def poll(self):
         check(load().amg_slots_poll(self.s, self._state.ctypes.data, self._iters.ctypes.data), "amg_slots_poll")
-        self._pending.clear()
         return self._state.copy(), self._iters.copy()
+
+    def query(self):
+        """(state, iters, steps finished, steps launched) from the newest finished step, without
+        waiting; a slot admitted after that step reads as running."""
+        d, i = C.c_int64(0), C.c_int64(0)
+        check(load().amg_slots_query(self.s, self._state.ctypes.data, self._iters.ctypes.data, C.byref(d),
+                                     C.byref(i)), "amg_slots_query")
+        return self._state.copy(), self._iters.copy(), d.value, i.value
+
+    def wait(self):
+        """Block until the oldest step in flight has finished."""
+        check(load().amg_slots_wait(self.s), "amg_slots_wait")
 
     def retire(self, slot: int, x=None):
         """Slot's solution (into x, or a new tensor) and the slot freed; ordered before later

@@ -213,12 +213,16 @@ struct SlotsBase {
   virtual void admit(int j, const double *b) = 0;
   virtual void step() = 0;
   virtual void poll(int *state, int *iters) = 0;
+  virtual void query(int *state, int *iters, long long *done, long long *issued) = 0;
+  virtual void wait() = 0;
   virtual void retire(int j, double *x) = 0;
 };
 SlotsBase *make_slots(amg_hierarchy *h, int K, double rtol, int maxit, cudaStream_t s);
 void slots_admit(SlotsBase *b, int j, const double *rhs);
 void slots_step(SlotsBase *b);
 void slots_poll(SlotsBase *b, int *state, int *iters);
+void slots_query(SlotsBase *b, int *state, int *iters, long long *done, long long *issued);
+void slots_wait(SlotsBase *b);
 void slots_retire(SlotsBase *b, int j, double *x);
 void slots_delete(SlotsBase *b);
 // batched right-hand sides (batch.cu)

@@ -274,6 +274,25 @@ int amg_slots_poll(amg_slots *s, int32_t *state, int32_t *iters) {
   AMG_GUARD_END
 }
 
+int amg_slots_query(amg_slots *s, int32_t *state, int32_t *iters, int64_t *steps_done, int64_t *steps_issued) {
+  if (!s) return bad("NULL argument");
+  AMG_GUARD_BEGIN
+  long long d = 0, i = 0;
+  amg::slots_query(s->impl, state, iters, &d, &i);
+  if (steps_done) *steps_done = d;
+  if (steps_issued) *steps_issued = i;
+  return AMG_OK;
+  AMG_GUARD_END
+}
+
+int amg_slots_wait(amg_slots *s) {
+  if (!s) return bad("NULL argument");
+  AMG_GUARD_BEGIN
+  amg::slots_wait(s->impl);
+  return AMG_OK;
+  AMG_GUARD_END
+}
+
 int amg_slots_retire(amg_slots *s, int32_t slot, double *x) {
   if (!s) return bad("NULL argument");
   if (slot < 0 || slot >= s->capacity) return bad("slot out of range");

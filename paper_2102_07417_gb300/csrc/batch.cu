@@ -27,6 +27,7 @@ struct BScal {
   double rho[KMAX], alpha[KMAX], beta[KMAX], rr[KMAX], bb[KMAX], tol[KMAX];
   int iters[KMAX], done[KMAX], status[KMAX];
   int first[KMAX];  // column admitted since the last iteration (continuous batching): no CG step yet
+  unsigned int ticket[KMAX];  // admission number of the request in each column (continuous batching)
   int all_done, maxit, k;
 };
 
@@ -702,9 +703,9 @@ int batch_dispatch(amg_hierarchy *h, int k, const double *B, double *X, double r
 // ("slots") are admitted, stepped and retired independently.
 
 // Column j of an n x K block: x = 0, r = b, p = 0; tol_j = rtol ||b||.
-__global__ void __launch_bounds__(TPB) k_admit(int n, int K, int j, const double *__restrict__ b, double *__restrict__ x,
-                                               double *__restrict__ r, double *__restrict__ p, double rtol, BScal *sc,
-                                               double *partials, unsigned int *counter) {
+__global__ void __launch_bounds__(TPB) k_admit(int n, int K, int j, unsigned int ticket, const double *__restrict__ b,
+                                               double *__restrict__ x, double *__restrict__ r, double *__restrict__ p,
+                                               double rtol, BScal *sc, double *partials, unsigned int *counter) {
   __shared__ double red[TPB / 32];
   __shared__ bool last;
   double v = 0.0;
@@ -733,6 +734,7 @@ __global__ void __launch_bounds__(TPB) k_admit(int n, int K, int j, const double
   double bb = 0.0;
   for (int g = 0; g < (int)gridDim.x; ++g) bb += __ldcg(&partials[g * 3 * KMAX]);
   sc->bb[j] = bb;
+  sc->ticket[j] = ticket;
   sc->tol[j] = rtol * sqrt(bb);
   sc->iters[j] = 0;
   sc->status[j] = AMG_OK;
@@ -772,8 +774,15 @@ struct SlotsImpl : SlotsBase {
   Buf<unsigned int> counter;
   BScal *host = nullptr;  // pinned copy for poll
   std::vector<int> busy;
+  std::vector<unsigned int> ticket;  // admission number of each slot's current request
+  unsigned int admitted = 0;
   cudaGraphExec_t exec = nullptr;
   long long per_step = 0;  // kernels in one step
+  // snapshots of the per-column state taken at the end of each step (pinned ring)
+  static constexpr int kRing = 8;
+  BScal *ring = nullptr;
+  cudaEvent_t ring_ev[kRing] = {};
+  long long issued = 0, completed = 0;
 
   SlotsImpl(amg_hierarchy *hh, int cap, double rt, int mi, cudaStream_t s) : h(hh), K(cap), maxit(mi), rtol(rt) {
     mem.alloc = h->mem.alloc;
@@ -814,18 +823,26 @@ struct SlotsImpl : SlotsBase {
     init.all_done = 1;
     AMG_CUDA(cudaMemcpyAsync(scb.p, &init, sizeof(init), cudaMemcpyHostToDevice, s));
     AMG_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&host), sizeof(BScal), cudaHostAllocDefault));
+    AMG_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&ring), sizeof(BScal) * kRing, cudaHostAllocDefault));
+    for (int e = 0; e < kRing; ++e) AMG_CUDA(cudaEventCreateWithFlags(&ring_ev[e], cudaEventDisableTiming));
     AMG_CUDA(cudaStreamSynchronize(s));
     busy.assign(K, 0);
+    ticket.assign(K, 0);
   }
   ~SlotsImpl() override {
     cudaStreamSynchronize(mem.stream);
     if (exec) cudaGraphExecDestroy(exec);
     if (host) cudaFreeHost(host);
+    if (ring) cudaFreeHost(ring);
+    for (int e = 0; e < kRing; ++e)
+      if (ring_ev[e]) cudaEventDestroy(ring_ev[e]);
     // Bufs return their memory through mem; free_all catches anything left
   }
   void admit(int j, const double *b) override {
     const int n = h->lev[0].A.n;
-    k_admit<<<grid_for(n), TPB, 0, mem.stream>>>(n, K, j, b, X.p, r.p, p.p, rtol, scb.p, partials.p, counter.p);
+    ticket[j] = ++admitted;
+    k_admit<<<grid_for(n), TPB, 0, mem.stream>>>(n, K, j, ticket[j], b, X.p, r.p, p.p, rtol, scb.p, partials.p,
+                                                 counter.p);
     AMG_CHECK_LAUNCH();
     busy[j] = 1;
   }
@@ -833,6 +850,47 @@ struct SlotsImpl : SlotsBase {
   // launches are captured once into a CUDA graph and replayed (the launch
   // sequence never changes: masks live in device memory).
   void step() override {
+    if (issued - completed >= kRing) {  // every snapshot slot is in flight: wait for the oldest
+      AMG_CUDA(cudaEventSynchronize(ring_ev[completed % kRing]));
+      ++completed;
+    }
+    run_step();
+    const int e = (int)(issued % kRing);
+    AMG_CUDA(cudaMemcpyAsync(ring + e, scb.p, sizeof(BScal), cudaMemcpyDeviceToHost, mem.stream));
+    AMG_CUDA(cudaEventRecord(ring_ev[e], mem.stream));
+    ++issued;
+  }
+  // Per-slot states from the newest finished step, without waiting.
+  void query(int *state, int *iters, long long *done_steps, long long *issued_steps) override {
+    while (completed < issued && cudaEventQuery(ring_ev[completed % kRing]) == cudaSuccess) ++completed;
+    const BScal *snap = completed > 0 ? ring + (completed - 1) % kRing : nullptr;
+    report(snap, state, iters);
+    if (done_steps) *done_steps = completed;
+    if (issued_steps) *issued_steps = issued;
+  }
+  void wait() override {
+    if (completed < issued) {
+      AMG_CUDA(cudaEventSynchronize(ring_ev[completed % kRing]));
+      ++completed;
+    }
+  }
+  // A slot whose request was admitted after the snapshot was taken reads as running.
+  void report(const BScal *snap, int *state, int *iters) {
+    for (int j = 0; j < K; ++j) {
+      int stt = 0, it = 0;
+      if (busy[j]) {
+        if (snap && snap->ticket[j] == ticket[j]) {
+          stt = !snap->done[j] ? 1 : (snap->status[j] == AMG_OK ? 2 : snap->status[j]);
+          it = snap->iters[j];
+        } else {
+          stt = 1;
+        }
+      }
+      if (state) state[j] = stt;
+      if (iters) iters[j] = it;
+    }
+  }
+  void run_step() {
     if (g_prof.on || mem.stream == nullptr) {  // the legacy default stream cannot be captured
       issue_step();
       return;
@@ -888,12 +946,8 @@ struct SlotsImpl : SlotsBase {
   void poll(int *state, int *iters) override {
     AMG_CUDA(cudaMemcpyAsync(host, scb.p, sizeof(BScal), cudaMemcpyDeviceToHost, mem.stream));
     AMG_CUDA(cudaStreamSynchronize(mem.stream));
-    for (int j = 0; j < K; ++j) {
-      int stt = 0;
-      if (busy[j]) stt = !host->done[j] ? 1 : (host->status[j] == AMG_OK ? 2 : host->status[j]);
-      if (state) state[j] = stt;
-      if (iters) iters[j] = host->iters[j];
-    }
+    completed = issued;
+    report(host, state, iters);
   }
   void retire(int j, double *x) override {
     const int n = h->lev[0].A.n;
@@ -966,6 +1020,10 @@ SlotsBase *make_slots(amg_hierarchy *h, int K, double rtol, int maxit, cudaStrea
 void slots_admit(SlotsBase *b, int j, const double *rhs) { b->admit(j, rhs); }
 void slots_step(SlotsBase *b) { b->step(); }
 void slots_poll(SlotsBase *b, int *state, int *iters) { b->poll(state, iters); }
+void slots_query(SlotsBase *b, int *state, int *iters, long long *done, long long *issued) {
+  b->query(state, iters, done, issued);
+}
+void slots_wait(SlotsBase *b) { b->wait(); }
 void slots_retire(SlotsBase *b, int j, double *x) { b->retire(j, x); }
 void slots_delete(SlotsBase *b) { delete b; }
 

@@ -12,11 +12,13 @@ stream of two kinds of request:
   solve.  These run on worker threads, each with its own CUDA stream, and are
   admitted only when the HBM they are expected to need is free.
 
-Every resident operator has its own stream; one loop iteration issues one
-PCG step (a replayed CUDA graph) on every operator with running slots, then
-polls them, so the steps of different operators overlap on the device.
-Latency is measured from a request's arrival time to the moment its solution
-is back in device memory.
+Every resident operator has its own stream and keeps up to ``depth`` PCG
+steps (replayed CUDA graphs) in flight; the loop reads each step's per-slot
+state from a pinned snapshot without waiting, so the steps of different
+operators overlap on the device and the host never stalls the GPU between
+steps.  Latency is measured from a request's arrival time to the moment the
+host sees its column converged (its solution is then final in device
+memory; a converged column is frozen).
 """
 from __future__ import annotations
 
@@ -114,8 +116,8 @@ class Server:
     """Resident hierarchies + continuous batching + HBM-gated set-up of new operators."""
 
     def __init__(self, operators, precision: int = amg.PREC_FP32, capacity: int = 4, rtol: float = 1e-8,
-                 maxit: int = 200, workers: int = 2, sigma: float = 1.0, hbm_budget: int | None = None,
-                 hbm_reserve: int = 2 << 30, keep_x: bool = False):
+                 maxit: int = 200, workers: int = 4, sigma: float = 1.0, hbm_budget: int | None = None,
+                 hbm_reserve: int = 2 << 30, keep_x: bool = False, depth: int = 2):
         import torch
 
         self.torch = torch
@@ -134,6 +136,8 @@ class Server:
         self.workers = workers
         self.hbm_budget = hbm_budget
         self.hbm_reserve = hbm_reserve
+        self.depth = depth
+        self._x_scratch = [None] * len(self.hier)
         self._streams = [torch.cuda.Stream() for _ in range(workers)]
         self._free_streams = collections.deque(range(workers))
         self._lock = threading.Lock()
@@ -144,6 +148,12 @@ class Server:
             s.close()
         for h in self.hier:
             h.close()
+
+    def _scratch(self, i: int):
+        """A device buffer the solution of operator i is copied to when results are not kept."""
+        if self._x_scratch[i] is None:
+            self._x_scratch[i] = self.torch.empty(self.n[i], dtype=self.torch.float64, device="cuda")
+        return self._x_scratch[i]
 
     # -- new operators (worker threads) --------------------------------------
     def matrix_bytes(self, m: int) -> int:
@@ -232,31 +242,45 @@ class Server:
                 active = [i for i in range(len(self.slots)) if running[i]]
                 self.stats["max_running_slots"] = max(self.stats["max_running_slots"],
                                                       sum(len(running[i]) for i in active))
+                # steps stay `depth` deep in flight on every operator; results are read from the
+                # snapshots of finished steps without waiting (a converged column is frozen, so
+                # the steps behind it leave its solution unchanged)
+                progressed = False
+                blocked = []
                 for i in active:
-                    self.slots[i].step()
-                self.stats["steps"] += len(active)
-                for i in active:
-                    state, iters = self.slots[i].poll()
+                    sl = self.slots[i]
+                    state, iters, done, issued = sl.query()
                     for s in list(running[i]):
                         if state[s] == amg.SLOT_RUNNING:
                             continue
                         r, t_start = running[i].pop(s)
-                        with torch.cuda.stream(self.slots[i].tstream):
-                            x = self.slots[i].retire(s)
-                        self.slots[i].tstream.synchronize()
+                        t_done = clock() - t0
+                        with torch.cuda.stream(sl.tstream):
+                            x = sl.retire(s) if self.keep_x else sl.retire(s, self._scratch(i))
                         st = amg.AMG_OK if state[s] == amg.SLOT_CONVERGED else int(state[s])
-                        results.append(Result(r.rid, "rhs", self.n[i], r.t_arrival, t_start, clock() - t0,
+                        results.append(Result(r.rid, "rhs", self.n[i], r.t_arrival, t_start, t_done,
                                               int(iters[s]), st, slot=s, x=x if self.keep_x else None))
                         free[i].append(s)
                         free[i].sort()
+                        progressed = True
+                    if running[i] and issued - done < self.depth:
+                        sl.step()
+                        self.stats["steps"] += 1
+                        progressed = True
+                    elif running[i]:
+                        blocked.append(i)
                 if not active:
                     # idle: wait for the next arrival or a finishing set-up
                     wait = 0.0005
                     if nxt < len(reqs) and not inflight and not mat_q:
                         wait = max(0.0, reqs[nxt].t_arrival - (clock() - t0))
                     time.sleep(min(wait, 0.002))
+                elif not progressed and blocked:
+                    self.slots[blocked[0]].wait()
         finally:
             pool.shutdown(wait=True)
+            for sl in self.slots:
+                sl.tstream.synchronize()
         return sorted(results, key=lambda r: r.rid)
 
 

@@ -27,9 +27,10 @@ def _rhs(n, count, seed):
     return [rng.uniform(-1.0, 1.0, n) for _ in range(count)]
 
 
-def _run_schedule(hg, cap, bs, arrivals, rtol, maxit=500):
+def _run_schedule(hg, cap, bs, arrivals, rtol, maxit=500, pipelined=False):
     """Admit bs[r] at step arrivals[r] (into the lowest free slot, queueing when full);
-    retire converged slots after every step.  Returns {r: (slot, iters, state, x)}."""
+    retire converged slots after every step (pipelined: read the state of finished steps
+    without waiting, two steps in flight).  Returns {r: (slot, iters, state, x)}."""
     sl = hg.slots(cap, rtol=rtol, maxit=maxit)
     free = list(range(cap))
     queue, running, out = [], {}, {}
@@ -42,8 +43,14 @@ def _run_schedule(hg, cap, bs, arrivals, rtol, maxit=500):
             s = free.pop(0)
             sl.admit(s, bdev[r])
             running[s] = r
-        sl.step()
-        state, iters = sl.poll()
+        if pipelined:
+            sl.step()
+            state, iters, done, issued = sl.query()
+            if issued - done >= 2:
+                sl.wait()
+        else:
+            sl.step()
+            state, iters = sl.poll()
         for s in list(running):
             if state[s] != amg.SLOT_RUNNING:
                 r = running.pop(s)
@@ -57,14 +64,15 @@ def _run_schedule(hg, cap, bs, arrivals, rtol, maxit=500):
     return out
 
 
-@pytest.mark.parametrize("prec", [amg.PREC_FP64, amg.PREC_FP32])
-def test_slots_match_batch_columns(prec):
+@pytest.mark.parametrize("prec,pipelined", [(amg.PREC_FP64, False), (amg.PREC_FP32, False),
+                                             (amg.PREC_FP32, True)])
+def test_slots_match_batch_columns(prec, pipelined):
     A, _ = pr.diffusion3d(20, 1.0, 7)
     hg = amg.Hierarchy(A, seed=0, precision=prec)
     cap = 4
     bs = _rhs(A.n, 9, 11)
     arrivals = [0, 0, 2, 3, 3, 3, 7, 12, 12]
-    out = _run_schedule(hg, cap, bs, arrivals, 1e-8)
+    out = _run_schedule(hg, cap, bs, arrivals, 1e-8, pipelined=pipelined)
     for r, (s, it, state, x) in out.items():
         assert state == amg.SLOT_CONVERGED
         B = np.repeat(bs[r][:, None], cap, axis=1)
