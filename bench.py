@@ -87,6 +87,7 @@ def make_problem(name: str):
 # and iteration counts equal the oracle's at every size the oracle can finish); used to scale the
 # oracle's bounded sample on that workload
 ELASTICITY64_FP64_ITERS = 3400
+FP64_TFLOPS = 1.25  # GB300 nominal dense FP64 (no measured FP64 peak is recorded)
 
 
 def peaks():
@@ -103,17 +104,18 @@ KERNEL_SOURCE = {"spgemm": "spgemm.cu", "strength": "setup.cu", "pmis": "setup.c
                  "transpose": "setup.cu", "setup_other": "setup.cu"}
 
 
-def traffic_for(kernel_class: str, level):
-    """DRAM bytes per launch of a kernel class (on a level) from the committed ncu
+def traffic_for(workload: str, kernel_class: str, level, batch: bool = False):
+    """DRAM bytes per launch of a kernel class (on a level) of a workload from the committed ncu
     summary, if it was captured on the current source of that kernel (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.md")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_2102_07417_gb300", "csrc", KERNEL_SOURCE.get(kernel_class, "solve.cu"))
+    default = "batch.cu" if batch else "solve.cu"
+    src = os.path.join(ROOT, "paper_2102_07417_gb300", "csrc", KERNEL_SOURCE.get(kernel_class, default))
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    want = f"{kernel_class}@{level}" if level is not None else kernel_class
+    want = f"{workload}/{kernel_class}" + (f"@{level}" if level is not None else "")
     for line in open(path):
-        m = re.match(r"^\|\s*`?([\w@]+)`?\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]{16})\s*\|", line)
+        m = re.match(r"^\|\s*`?([\w@/]+)`?\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]{16})\s*\|", line)
         if m and m.group(1) == want and m.group(3) == sha:
             return float(m.group(2))
     return None
@@ -367,7 +369,17 @@ def run_gpu(args, rank, world, dist):
             "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
             "launches_timed": d["launches"], "avg_launch_us": d["ms"] * 1e3 / max(d["launches"], 1),
             "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
-            "traffic": traffic_for(dom, dom_lv)}
+            "traffic": traffic_for(args.workload, dom, dom_lv, batch)}
+    if batch and dom == "spmv_dot" and d["ms"] > 0:
+        # k columns share each matrix entry: the FP64 SpMM is bound by FP64 arithmetic, not HBM
+        # (2 nnz k flops per launch; peak: GB300's nominal FP64 rate, 152 SMs x ~2 DFMA/clk x 2.07 GHz)
+        flops = 2.0 * p.A.nnz * p.b.shape[1] * d["launches"]
+        tf = flops / (d["ms"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "level": dom_lv, "achieved": tf, "peak": FP64_TFLOPS,
+                "unit": "TFLOP/s", "frac": tf / FP64_TFLOPS, "peak_source": "nominal FP64 (recipe table)",
+                "launches_timed": d["launches"], "avg_launch_us": d["ms"] * 1e3 / max(d["launches"], 1),
+                "hbm_gbs": achieved, "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
+                "traffic": traffic_for(args.workload, dom, dom_lv, batch)}
 
     x_err = None
     if p.xstar is not None:

@@ -194,6 +194,12 @@ struct amg_hierarchy {
   int *h_done = nullptr;           // mapped pinned host flag (written by the device)
   int *d_done = nullptr;           // its device alias
   cudaEvent_t iter_ev[2] = {nullptr, nullptr};
+  // one PCG iteration captured as a CUDA graph (replayed on the solve's stream);
+  // valid for the x and history buffers it was captured with
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t iter_exec = nullptr;
+  const void *iter_x = nullptr, *iter_hist = nullptr;
+  long long iter_launches = 0;
   size_t bytes = 0;
 };
 

@@ -35,6 +35,35 @@ __device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(
 __device__ __forceinline__ float tof(float v) { return v; }
 __device__ __forceinline__ double tof(double v) { return v; }
 
+// Totals over the grid's block partials, run by every thread of the last
+// block: pair (c, j) of the NV x kc (value, column) pairs is summed by
+// TPB / P threads over interleaved blocks, then by one thread over those in
+// order (a fixed order, so the totals are deterministic).  tot[c][j] in
+// shared memory on return.
+template <int NV>
+__device__ void grid_totals(const double *partials, int nblocks, int kc, double (*tot)[KMAX]) {
+  __shared__ double red[TPB];
+  const int npairs = NV * kc;
+  int P = 1;
+  while (P < npairs) P <<= 1;
+  const int S = TPB / P;
+  const int pair = threadIdx.x % P, sub = threadIdx.x / P;
+  double t = 0.0;
+  if (pair < npairs) {
+    const int c = pair / kc, j = pair % kc;
+#pragma unroll 4
+    for (int b = sub; b < nblocks; b += S) t += __ldcg(&partials[(b * 3 + c) * KMAX + j]);
+  }
+  red[threadIdx.x] = t;
+  __syncthreads();
+  if (threadIdx.x < npairs) {
+    double v = 0.0;
+    for (int u = 0; u < S; ++u) v += red[u * P + threadIdx.x];
+    tot[threadIdx.x / kc][threadIdx.x % kc] = v;
+  }
+  __syncthreads();
+}
+
 // Per-column sums of NV values: v[c] is this thread's partial for column
 // (lane % K).  Block partials go to partials[(block * 3 + c) * KMAX + j]; the
 // last block to finish gets the totals out[c] for its column j = lane % K
@@ -62,13 +91,11 @@ __device__ bool col_reduce(const double (&v)[NV], double *partials, unsigned int
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  __shared__ double tot[NV][KMAX];
+  grid_totals<NV>(partials, gridDim.x, K, tot);
   if (threadIdx.x < K) {
 #pragma unroll
-    for (int c = 0; c < NV; ++c) {
-      double s = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(&partials[(b * 3 + c) * KMAX + threadIdx.x]);
-      out[c] = s;
-    }
+    for (int c = 0; c < NV; ++c) out[c] = tot[c][threadIdx.x];
   }
   if (threadIdx.x == 0) *counter = 0u;
   return true;
@@ -108,6 +135,135 @@ __global__ void __launch_bounds__(TPB) k_brows(int n, int k, const int *__restri
   op.finish(acc);
 }
 
+// Per-column sums of NV values when each thread holds all K columns of its
+// rows (acc[j].v[c]): warp butterflies, then warps in order, then blocks in
+// order (deterministic).  Same partials layout and return convention as
+// col_reduce: in the last block thread j < K gets column j's totals.
+template <int K, int NV>
+__device__ bool rows_reduce(const BAcc<NV> (&acc)[K], double *partials, unsigned int *counter,
+                            double (&out)[NV]) {
+  __shared__ double red[NV][K][TPB / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      double v = acc[j].v[c];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[c][j][w] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      double t = 0.0;
+      for (int ww = 0; ww < TPB / 32; ++ww) t += red[c][threadIdx.x][ww];
+      partials[(blockIdx.x * 3 + c) * KMAX + threadIdx.x] = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  __shared__ double tot[NV][KMAX];
+  grid_totals<NV>(partials, gridDim.x, K, tot);
+  if (threadIdx.x < K) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) out[c] = tot[c][threadIdx.x];
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// sum[j] += a * p[j] for the K values of one block row, loaded with 16-byte
+// vector loads (K * sizeof(T) a multiple of 16), else in 8- or 4-byte pieces.
+template <int K, typename T>
+__device__ __forceinline__ void fma_row(const T *__restrict__ p, T a, T (&sum)[K]) {
+  if constexpr (sizeof(T) * K % 16 == 0) {
+#pragma unroll
+    for (int v = 0; v < (int)(K * sizeof(T) / 16); ++v) {
+      if constexpr (sizeof(T) == 8) {
+        const double2 d = __ldg(reinterpret_cast<const double2 *>(p) + v);
+        sum[2 * v] = fma(a, d.x, sum[2 * v]);
+        sum[2 * v + 1] = fma(a, d.y, sum[2 * v + 1]);
+      } else {
+        const float4 f = __ldg(reinterpret_cast<const float4 *>(p) + v);
+        sum[4 * v] = fma(a, f.x, sum[4 * v]);
+        sum[4 * v + 1] = fma(a, f.y, sum[4 * v + 1]);
+        sum[4 * v + 2] = fma(a, f.z, sum[4 * v + 2]);
+        sum[4 * v + 3] = fma(a, f.w, sum[4 * v + 3]);
+      }
+    }
+  } else if constexpr (sizeof(T) == 4 && K == 2) {
+    const float2 f = __ldg(reinterpret_cast<const float2 *>(p));
+    sum[0] = fma(a, f.x, sum[0]);
+    sum[1] = fma(a, f.y, sum[1]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < K; ++j) sum[j] = fma(a, __ldg(p + j), sum[j]);
+  }
+}
+
+// SpMM on the sliced-ELLPACK copy: a thread per row holding all K columns
+// (the matrix entry is loaded once, the block row of the gathered vector with
+// vector loads).  vec (k == K and a 16-byte aligned vector) uses the vector
+// loads; otherwise k values are loaded one by one.
+template <int K, class Op>
+__global__ void __launch_bounds__(TPB) k_bsell(int n, int k, bool vec, int nslices, const int *__restrict__ off,
+                                               const int *__restrict__ col, const int *__restrict__ perm, Op op) {
+  using T = typename Op::T;
+  constexpr int NA = Op::NV > 0 ? Op::NV : 1;
+  if (op.skip()) return;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5, nw = (gridDim.x * TPB) >> 5;
+  BAcc<NA> acc[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+#pragma unroll
+    for (int c = 0; c < NA; ++c) acc[j].v[c] = 0.0;
+  for (int sl = gw; sl < nslices; sl += nw) {
+    const int q = sl * 32 + lane;
+    const bool valid = q < n;
+    const int row = valid ? (perm ? perm[q] : q) : 0;
+    T sum[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) sum[j] = T(0);
+    if constexpr (Op::kMatrix) {
+      const int b = off[sl] + lane, len = (off[sl + 1] - off[sl]) >> 5;
+#pragma unroll(K <= 4 ? 4 : 2)
+      for (int t = 0; t < len; ++t) {
+        const int idx = b + 32 * t;
+        const int c = __ldg(col + idx);
+        const T a = op.mat(idx);
+        const T *xr = op.vrow(c);
+        if (vec) {
+          fma_row<K, T>(xr, a, sum);
+        } else {
+#pragma unroll
+          for (int j = 0; j < K; ++j)
+            if (j < k) sum[j] = fma(a, __ldg(xr + j), sum[j]);
+        }
+      }
+    }
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (j < k) op.out(row, j, sum[j], acc[j]);
+    }
+  }
+  if constexpr (Op::NV > 0) {
+    double tot[Op::NV];
+    if (rows_reduce<K, Op::NV>(acc, op.partials, op.counter, tot)) op.finish_col(tot);
+  }
+}
+
 // ------------------------------------------------------------------ ops --
 // Block vectors are row-major with leading dimension k: v[i * k + j].
 
@@ -132,6 +288,8 @@ struct BInit {
   __device__ bool skip() const { return false; }
   __device__ double mat(int p) const { return __ldg(a + p); }
   __device__ double vec(int c, int j) const { return __ldg(x + (size_t)c * k + j); }
+  __device__ const double *vrow(int c) const { return x + (size_t)c * k; }
+  __host__ __device__ const double *vbase() const { return x; }
   __device__ void out(int i, int j, double sum, BAcc<NV> &acc) const {
     const size_t o = (size_t)i * k + j;
     const double bi = b[o], ri = bi - sum;
@@ -144,7 +302,11 @@ struct BInit {
   }
   __device__ void finish(BAcc<NV> &acc) const {
     double tot[2];
-    if (col_reduce<K, 2>(acc.v, partials, counter, tot)) {
+    if (col_reduce<K, 2>(acc.v, partials, counter, tot)) finish_col(tot);
+  }
+  // Run by every thread of the last block; thread j < k holds column j's totals.
+  __device__ void finish_col(const double (&tot)[NV]) const {
+    {
       const int j = threadIdx.x;
       if (j < k) {
         sc->bb[j] = tot[0];
@@ -181,6 +343,8 @@ struct BSpmvDot {
   __device__ bool skip() const { return sc->all_done; }
   __device__ double mat(int t) const { return __ldg(a + t); }
   __device__ double vec(int c, int j) const { return __ldg(p + (size_t)c * k + j); }
+  __device__ const double *vrow(int c) const { return p + (size_t)c * k; }
+  __host__ __device__ const double *vbase() const { return p; }
   __device__ void out(int i, int j, double sum, BAcc<NV> &acc) const {
     const size_t o = (size_t)i * k + j;
     q[o] = sum;
@@ -188,7 +352,10 @@ struct BSpmvDot {
   }
   __device__ void finish(BAcc<NV> &acc) const {
     double tot[1];
-    if (col_reduce<K, 1>(acc.v, partials, counter, tot)) {
+    if (col_reduce<K, 1>(acc.v, partials, counter, tot)) finish_col(tot);
+  }
+  __device__ void finish_col(const double (&tot)[NV]) const {
+    {
       const int j = threadIdx.x;
       if (j < k && !sc->done[j] && sc->first[j]) {
         sc->alpha[j] = 0.0;  // p_j = 0: its first step only forms z = M r
@@ -217,6 +384,8 @@ struct BResid {  // r = y - A s
   __device__ bool skip() const { return *done; }
   __device__ T mat(int p) const { return __ldg(a + p); }
   __device__ T vec(int c, int j) const { return __ldg(s + (size_t)c * k + j); }
+  __device__ const T *vrow(int c) const { return s + (size_t)c * k; }
+  __host__ __device__ const T *vbase() const { return s; }
   __device__ void out(int i, int j, T sum, BAcc<1> &) const {
     const size_t o = (size_t)i * k + j;
     r[o] = y[o] - sum;
@@ -238,6 +407,8 @@ struct BRestrict {  // y_c = R r;  s_c = wd_c y_c (pre = 1), 0 (pre = 0), not wr
   __device__ bool skip() const { return *done; }
   __device__ T mat(int p) const { return static_cast<T>(tof(rv[p])); }
   __device__ T vec(int c, int j) const { return __ldg(r + (size_t)c * k + j); }
+  __device__ const T *vrow(int c) const { return r + (size_t)c * k; }
+  __host__ __device__ const T *vbase() const { return r; }
   __device__ void out(int i, int j, T sum, BAcc<1> &) const {
     const size_t o = (size_t)i * k + j;
     yc[o] = sum;
@@ -259,6 +430,8 @@ struct BProlong {  // t = s + P z_c
   __device__ bool skip() const { return *done; }
   __device__ T mat(int p) const { return static_cast<T>(tof(pv[p])); }
   __device__ T vec(int c, int j) const { return __ldg(zc + (size_t)c * k + j); }
+  __device__ const T *vrow(int c) const { return zc + (size_t)c * k; }
+  __host__ __device__ const T *vbase() const { return zc; }
   __device__ void out(int i, int j, T sum, BAcc<1> &) const {
     const size_t o = (size_t)i * k + j;
     t[o] = s[o] + sum;
@@ -278,6 +451,8 @@ struct BJacobi {  // z = t + wd (y - A t)
   __device__ bool skip() const { return *done; }
   __device__ T mat(int p) const { return __ldg(a + p); }
   __device__ T vec(int c, int j) const { return __ldg(t + (size_t)c * k + j); }
+  __device__ const T *vrow(int c) const { return t + (size_t)c * k; }
+  __host__ __device__ const T *vbase() const { return t; }
   __device__ void out(int i, int j, T sum, BAcc<1> &) const {
     const size_t o = (size_t)i * k + j;
     z[o] = fma(wd[i], y[o] - sum, t[o]);
@@ -306,6 +481,8 @@ struct BPost0 {
   __device__ bool skip() const { return *done; }
   __device__ T mat(int pp) const { return __ldg(a + pp); }
   __device__ T vec(int c, int j) const { return __ldg(t + (size_t)c * k + j); }
+  __device__ const T *vrow(int c) const { return t + (size_t)c * k; }
+  __host__ __device__ const T *vbase() const { return t; }
   __device__ void out(int i, int j, T sum, BAcc<NV> &acc) const {
     const size_t o = (size_t)i * k + j;
     const T zi = SWEEP ? fma(wd[i], y[o] - sum, t[o]) : t[o];
@@ -320,7 +497,11 @@ struct BPost0 {
   __device__ void finish(BAcc<NV> &acc) const {
     if (mode == BPOST_APPLY) return;
     double tot[2];
-    if (col_reduce<K, 2>(acc.v, partials, counter, tot)) {
+    if (col_reduce<K, 2>(acc.v, partials, counter, tot)) finish_col(tot);
+  }
+  __device__ void finish_col(const double (&tot)[NV]) const {
+    if (mode == BPOST_APPLY) return;
+    {
       const int j = threadIdx.x;
       if (j < k && !sc->done[j]) {
         if (mode == BPOST_ITER && sc->first[j]) {
@@ -336,8 +517,120 @@ struct BPost0 {
 };
 
 // x += alpha_j p;  r -= alpha_j q (columns not done);  ||r_j||;  convergence;  V-cycle input.
+// A thread per row holding its k <= K columns (16-byte vector loads when
+// k == K); frozen columns (converged, or admitted since the last step) keep
+// x and r bit for bit.
+template <int K>
+__device__ __forceinline__ void load_dr(const double *__restrict__ p, int k, bool vec, double (&v)[K]) {
+  if (vec && K % 2 == 0) {
+#pragma unroll
+    for (int u = 0; u < K / 2; ++u) {
+      const double2 d = reinterpret_cast<const double2 *>(p)[u];
+      v[2 * u] = d.x;
+      v[2 * u + 1] = d.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = j < k ? p[j] : 0.0;
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void store_dr(double *__restrict__ p, int k, bool vec, const double (&v)[K]) {
+  if (vec && K % 2 == 0) {
+#pragma unroll
+    for (int u = 0; u < K / 2; ++u) reinterpret_cast<double2 *>(p)[u] = make_double2(v[2 * u], v[2 * u + 1]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j < k) p[j] = v[j];
+  }
+}
+
+template <int K, typename T>
+__global__ void __launch_bounds__(TPB) k_bupdate(int n, int k, bool vec, double *__restrict__ x, double *__restrict__ r,
+                                                 const double *__restrict__ p, const double *__restrict__ q,
+                                                 const T *__restrict__ wd, T *__restrict__ y0, T *__restrict__ s0,
+                                                 bool write_y, bool pre, BScal *sc, double *hist, int hist_cap,
+                                                 int *host_done, double *partials, unsigned int *counter) {
+  if (sc->all_done) return;
+  __shared__ double s_alpha[KMAX];
+  __shared__ int s_frozen[KMAX];
+  if (threadIdx.x < KMAX) {
+    const int c = threadIdx.x;
+    const int fz = c < k ? (sc->done[c] | sc->first[c]) : 1;
+    s_frozen[c] = fz;
+    s_alpha[c] = fz ? 0.0 : sc->alpha[c];
+  }
+  __syncthreads();
+  double alpha[K];
+  bool frozen[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    alpha[j] = s_alpha[j];
+    frozen[j] = s_frozen[j];
+  }
+  BAcc<1> acc[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) acc[j].v[0] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const size_t o = (size_t)i * k;
+    double xr[K], rr[K], pr[K], qr[K];
+    load_dr<K>(r + o, k, vec, rr);
+    load_dr<K>(x + o, k, vec, xr);
+    load_dr<K>(p + o, k, vec, pr);
+    load_dr<K>(q + o, k, vec, qr);
+    const T w = pre ? wd[i] : T(0);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (!frozen[j]) {
+        xr[j] = fma(alpha[j], pr[j], xr[j]);
+        rr[j] = fma(-alpha[j], qr[j], rr[j]);
+      }
+      acc[j].v[0] = fma(rr[j], rr[j], acc[j].v[0]);
+    }
+    store_dr<K>(x + o, k, vec, xr);
+    store_dr<K>(r + o, k, vec, rr);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (j < k) {
+        const T yi = static_cast<T>(rr[j]);
+        if (write_y) y0[o + j] = yi;
+        s0[o + j] = pre ? w * yi : T(0);
+      }
+    }
+  }
+  double tot[1];
+  if (!rows_reduce<K, 1>(acc, partials, counter, tot)) return;
+  if (threadIdx.x < k) {
+    const int c = threadIdx.x;
+    if (!sc->done[c] && !sc->first[c]) {
+      const int it = sc->iters[c] + 1;
+      sc->iters[c] = it;
+      sc->rr[c] = tot[0];
+      const double res = sqrt(tot[0]);
+      if (it < hist_cap) hist[(size_t)it * k + c] = res;
+      if (res < sc->tol[c]) {
+        sc->done[c] = 1;
+      } else if (it >= sc->maxit) {
+        sc->status[c] = AMG_ERR_NO_CONVERGENCE;
+        sc->done[c] = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int all = 1;
+    for (int c = 0; c < k; ++c) all &= sc->done[c];
+    sc->all_done = all;
+    if (all && host_done) *(volatile int *)host_done = 1;
+  }
+}
+
+// The same for wide batches (K > 8, where a row's columns do not fit in one
+// thread's registers): consecutive threads take consecutive columns.
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_bupdate(int n, int k, double *__restrict__ x, double *__restrict__ r,
+__global__ void __launch_bounds__(TPB) k_bupdate_cols(int n, int k, double *__restrict__ x, double *__restrict__ r,
                                                  const double *__restrict__ p, const double *__restrict__ q,
                                                  const T *__restrict__ wd, T *__restrict__ y0, T *__restrict__ s0,
                                                  bool write_y, bool pre, BScal *sc, double *hist, int hist_cap,
@@ -391,10 +684,11 @@ __global__ void __launch_bounds__(TPB) k_bupdate(int n, int k, double *__restric
   __syncthreads();
   if (!last) return;
   __threadfence();
+  __shared__ double tot[1][KMAX];
+  grid_totals<1>(partials, gridDim.x, kk, tot);
   if (threadIdx.x < k) {
     const int c = threadIdx.x;
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(&partials[(b * 3) * KMAX + c]);
+    const double s = tot[0][c];
     if (!sc->done[c] && !sc->first[c]) {
       const int it = sc->iters[c] + 1;
       sc->iters[c] = it;
@@ -461,27 +755,69 @@ __global__ void k_bcopy(int64_t total, const T *__restrict__ a, T *__restrict__ 
 
 inline int grid_for(int64_t work) { return std::max(1, std::min<int>(ceil_div(work, TPB), MAX_GRID)); }
 
+// Batches of up to 16 columns run on a matrix's sliced-ELLPACK copy when it
+// has one (the op's value pointer must then point into it: bv below).
+template <int K>
+bool bsell(const DCsr &M) {
+  return M.use_sell && K <= 16;
+}
+
+template <typename V>
+struct VSel;
+template <>
+struct VSel<double> {
+  static const double *csr(const DCsr &M) { return M.v; }
+  static const double *sell(const DCsr &M) { return M.sell.v; }
+};
+template <>
+struct VSel<float> {
+  static const float *csr(const DCsr &M) { return M.v32; }
+  static const float *sell(const DCsr &M) { return M.sell.v32; }
+};
+template <>
+struct VSel<__nv_bfloat16> {
+  static const __nv_bfloat16 *csr(const DCsr &M) { return M.v16; }
+  static const __nv_bfloat16 *sell(const DCsr &M) { return M.sell.v16; }
+};
+
+// Values of M in storage type V, laid out for the kernel launch_b<K> runs.
+template <int K, typename V>
+const V *bv(const DCsr &M) {
+  return bsell<K>(M) ? VSel<V>::sell(M) : VSel<V>::csr(M);
+}
+
 template <int K, class Op>
 void launch_b(int n, int k, const DCsr &M, const Op &op, cudaStream_t s) {
-  k_brows<K, Op><<<grid_for((int64_t)n * K), TPB, 0, s>>>(n, k, M.rp, M.ci, op);
+  bool done = false;
+  if constexpr (K <= 16) {
+    if (bsell<K>(M)) {
+      const int grid = std::max(1, std::min(ceil_div(M.sell.nslices, TPB / 32), MAX_GRID));
+      const bool vec = k == K && (reinterpret_cast<uintptr_t>(op.vbase()) & 15) == 0;
+      k_bsell<K, Op><<<grid, TPB, 0, s>>>(n, k, vec, M.sell.nslices, M.sell.off, M.sell.col, M.sell.perm, op);
+      done = true;
+    }
+  }
+  if (!done) k_brows<K, Op><<<grid_for((int64_t)n * K), TPB, 0, s>>>(n, k, M.rp, M.ci, op);
+  AMG_CHECK_LAUNCH();
+}
+
+template <int K, typename T>
+void launch_bupdate(int n, int k, double *x, double *r, const double *p, const double *q, const T *wd, T *y0, T *s0,
+                    bool write_y, bool pre, BScal *sc, double *hist, int hist_cap, int *host_done, double *partials,
+                    unsigned int *counter, cudaStream_t s) {
+  if constexpr (K <= 8) {
+    auto al = [](const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) == 0; };
+    const bool vec = k == K && al(x) && al(r) && al(p) && al(q);
+    k_bupdate<K, T><<<grid_for(n), TPB, 0, s>>>(n, k, vec, x, r, p, q, wd, y0, s0, write_y, pre, sc, hist, hist_cap,
+                                                 host_done, partials, counter);
+  } else {
+    k_bupdate_cols<T><<<grid_for((int64_t)n * k), TPB, 0, s>>>(n, k, x, r, p, q, wd, y0, s0, write_y, pre, sc, hist,
+                                                               hist_cap, host_done, partials, counter);
+  }
   AMG_CHECK_LAUNCH();
 }
 
 // --------------------------------------------------------------- driver --
-template <typename T>
-const T *csr_vals(const DCsr &M);
-template <>
-const double *csr_vals<double>(const DCsr &M) { return M.v; }
-template <>
-const float *csr_vals<float>(const DCsr &M) { return M.v32; }
-template <typename TP>
-const TP *pr_vals(const DCsr &M);
-template <>
-const double *pr_vals<double>(const DCsr &M) { return M.v; }
-template <>
-const float *pr_vals<float>(const DCsr &M) { return M.v32; }
-template <>
-const __nv_bfloat16 *pr_vals<__nv_bfloat16>(const DCsr &M) { return M.v16; }
 template <typename T>
 const T *wdv(const Level &l);
 template <>
@@ -525,12 +861,12 @@ struct Batch {
     const double abytes = (4.0 + bt) * (double)A.nnz + 4.0 * (n + 1);
     for (int it = 1; it < prm.nu1; ++it) {
       ProfScope ps(s, AMG_K_SOLVE_OTHER, abytes + 4.0 * bt * nk, lv);
-      launch_b<K>(n, k, A, BJacobi<T>{k, csr_vals<T>(A), wdv<T>(L), y, sv, w, done}, s);
+      launch_b<K>(n, k, A, BJacobi<T>{k, bv<K, T>(A), wdv<T>(L), y, sv, w, done}, s);
       std::swap(sv, w);
     }
     {
       ProfScope ps(s, AMG_K_SMOOTH_RESID, abytes + 3.0 * bt * nk, lv);
-      launch_b<K>(n, k, A, BResid<T>{k, csr_vals<T>(A), sv, y, r, done}, s);
+      launch_b<K>(n, k, A, BResid<T>{k, bv<K, T>(A), sv, y, r, done}, s);
     }
     Level &C = h->lev[lv + 1];
     const int nc = C.A.n;
@@ -538,14 +874,14 @@ struct Batch {
     {
       ProfScope ps(s, AMG_K_RESTRICT, (4.0 + bp) * (double)L.R.nnz + 4.0 * (nc + 1) + bt * nk + 3.0 * bt * nc * k, lv);
       launch_b<K>(nc, k, L.R,
-                  BRestrict<T, TP>{k, pr_vals<TP>(L.R), r, c_last ? nullptr : wdv<T>(C), wk->y[lv + 1].p,
+                  BRestrict<T, TP>{k, bv<K, TP>(L.R), r, c_last ? nullptr : wdv<T>(C), wk->y[lv + 1].p,
                                    c_last ? nullptr : wk->s[lv + 1].p, c_last ? -1 : (prm.nu1 > 0 ? 1 : 0), done},
                   s);
     }
     cycle(lv + 1, done);
     {
       ProfScope ps(s, AMG_K_PROLONG, (4.0 + bp) * (double)L.P.nnz + 4.0 * (n + 1) + 2.0 * bt * nk + bt * nc * k, lv);
-      launch_b<K>(n, k, L.P, BProlong<T, TP>{k, pr_vals<TP>(L.P), sv, wk->z[lv + 1].p, r, done}, s);
+      launch_b<K>(n, k, L.P, BProlong<T, TP>{k, bv<K, TP>(L.P), sv, wk->z[lv + 1].p, r, done}, s);
     }
     if (lv == 0) return;
     T *t = r;
@@ -558,7 +894,7 @@ struct Batch {
       const bool lastp = it == prm.nu2 - 1;
       T *dst = lastp ? wk->z[lv].p : (t == r ? w : r);
       ProfScope ps(s, lastp ? AMG_K_SMOOTH_POST : AMG_K_SOLVE_OTHER, abytes + 4.0 * bt * nk, lv);
-      launch_b<K>(n, k, A, BJacobi<T>{k, csr_vals<T>(A), wdv<T>(L), y, t, dst, done}, s);
+      launch_b<K>(n, k, A, BJacobi<T>{k, bv<K, T>(A), wdv<T>(L), y, t, dst, done}, s);
       t = dst;
     }
   }
@@ -580,7 +916,7 @@ struct Batch {
       cycle(0, done);
       T *tt = wk->r[0].p, *w = wk->w[0].p;
       for (int it = 0; it + 1 < h->prm.nu2; ++it) {
-        launch_b<K>(n, k, A, BJacobi<T>{k, csr_vals<T>(A), wdv<T>(L0), y, tt, w, done}, s);
+        launch_b<K>(n, k, A, BJacobi<T>{k, bv<K, T>(A), wdv<T>(L0), y, tt, w, done}, s);
         std::swap(tt, w);
       }
       t = tt;
@@ -588,10 +924,10 @@ struct Batch {
     }
     ProfScope ps(s, AMG_K_SMOOTH_POST, (sweep ? 12.0 * A.nnz : 0.0) + 40.0 * nk, 0);
     if (sweep)
-      launch_b<K>(n, k, A, BPost0<K, T, true>{k, csr_vals<T>(A), wdv<T>(L0), y, t, zz, r, q, p, mode, flexible, sc,
+      launch_b<K>(n, k, A, BPost0<K, T, true>{k, bv<K, T>(A), wdv<T>(L0), y, t, zz, r, q, p, mode, flexible, sc,
                                                 done, partials, counter}, s);
     else
-      launch_b<K>(n, k, A, BPost0<K, T, false>{k, csr_vals<T>(A), wdv<T>(L0), y, t, zz, r, q, p, mode, flexible, sc,
+      launch_b<K>(n, k, A, BPost0<K, T, false>{k, bv<K, T>(A), wdv<T>(L0), y, t, zz, r, q, p, mode, flexible, sc,
                                                  done, partials, counter}, s);
   }
 };
@@ -640,7 +976,7 @@ int batch_impl(amg_hierarchy *h, int k, const double *B, double *X, double rtol,
   Batch<K, T, TP> bt{h, s, k, &wk, scb.p, partials.p, counter.p, r.p, zz.p, p.p, q.p};
   {
     ProfScope ps(s, AMG_K_SOLVE_OTHER, 12.0 * A.nnz + 40.0 * nk, 0);
-    launch_b<K>(n, k, A, BInit<K, T>{k, A.v, X, B, r.p, wdv<T>(L0), y0, s0, !fp64, pre, rtol, scb.p, hist.p, maxit + 1,
+    launch_b<K>(n, k, A, BInit<K, T>{k, bv<K, double>(A), X, B, r.p, wdv<T>(L0), y0, s0, !fp64, pre, rtol, scb.p, hist.p, maxit + 1,
                                      partials.p, counter.p}, s);
   }
   const int flexible = fp64 ? 0 : 1;
@@ -648,13 +984,12 @@ int batch_impl(amg_hierarchy *h, int k, const double *B, double *X, double rtol,
   for (int it = 1; it <= maxit; ++it) {
     {
       ProfScope ps(s, AMG_K_SPMV_DOT, 12.0 * A.nnz + 4.0 * (n + 1) + 24.0 * nk, 0);
-      launch_b<K>(n, k, A, BSpmvDot<K>{k, A.v, p.p, q.p, scb.p, partials.p, counter.p}, s);
+      launch_b<K>(n, k, A, BSpmvDot<K>{k, bv<K, double>(A), p.p, q.p, scb.p, partials.p, counter.p}, s);
     }
     {
       ProfScope ps(s, AMG_K_PCG_UPDATE, (48.0 + 3.0 * sizeof(T)) * nk, 0);
-      k_bupdate<T><<<grid_for(nk), TPB, 0, s>>>(n, k, X, r.p, p.p, q.p, wdv<T>(L0), y0, s0, !fp64, pre, scb.p, hist.p,
-                                                maxit + 1, h->d_done, partials.p, counter.p);
-      AMG_CHECK_LAUNCH();
+      launch_bupdate<K, T>(n, k, X, r.p, p.p, q.p, wdv<T>(L0), y0, s0, !fp64, pre, scb.p, hist.p, maxit + 1,
+                           h->d_done, partials.p, counter.p, s);
     }
     bt.vcycle(BPOST_ITER, flexible, done);
     {
@@ -729,10 +1064,12 @@ __global__ void __launch_bounds__(TPB) k_admit(int n, int K, int j, unsigned int
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
-  double bb = 0.0;
-  for (int g = 0; g < (int)gridDim.x; ++g) bb += __ldcg(&partials[g * 3 * KMAX]);
+  __shared__ double tot[1][KMAX];
+  grid_totals<1>(partials, gridDim.x, 1, tot);
+  if (threadIdx.x != 0) return;
+  const double bb = tot[0][0];
   sc->bb[j] = bb;
   sc->ticket[j] = ticket;
   sc->tol[j] = rtol * sqrt(bb);
@@ -928,13 +1265,12 @@ struct SlotsImpl : SlotsBase {
     Batch<KP, T, TP> bt{h, s, K, &wk, scb.p, partials.p, counter.p, r.p, zz.p, p.p, q.p};
     {
       ProfScope ps(s, AMG_K_SPMV_DOT, 12.0 * A.nnz + 4.0 * (n + 1) + 24.0 * nk, 0);
-      launch_b<KP>(n, K, A, BSpmvDot<KP>{K, A.v, p.p, q.p, scb.p, partials.p, counter.p}, s);
+      launch_b<KP>(n, K, A, BSpmvDot<KP>{K, bv<KP, double>(A), p.p, q.p, scb.p, partials.p, counter.p}, s);
     }
     {
       ProfScope ps(s, AMG_K_PCG_UPDATE, (48.0 + 3.0 * sizeof(T)) * nk, 0);
-      k_bupdate<T><<<grid_for(nk), TPB, 0, s>>>(n, K, X.p, r.p, p.p, q.p, wdv<T>(L0), y0, wk.s[0].p, !fp64,
-                                                h->prm.nu1 > 0, scb.p, nullptr, 0, nullptr, partials.p, counter.p);
-      AMG_CHECK_LAUNCH();
+      launch_bupdate<KP, T>(n, K, X.p, r.p, p.p, q.p, wdv<T>(L0), y0, wk.s[0].p, !fp64, h->prm.nu1 > 0, scb.p,
+                            nullptr, 0, nullptr, partials.p, counter.p, s);
     }
     bt.vcycle(BPOST_ITER, fp64 ? 0 : 1, done);
     {

@@ -108,6 +108,35 @@ __global__ void k_scan_apply(const int *__restrict__ in, int n, const long long 
 
 __global__ void k_set_last(int *out, int n, const long long *total) { out[n] = static_cast<int>(*total); }
 
+// Whole exclusive scan in one block (small n): tiles in order with a carry;
+// out[n] and *total receive the sum.
+__global__ void k_scan_single(const int *__restrict__ in, int n, int *__restrict__ out, long long *total) {
+  long long carry = 0;
+  for (int64_t base0 = 0; base0 < n; base0 += SCAN_TILE) {
+    const int64_t base = base0 + (int64_t)threadIdx.x * SCAN_ITEMS;
+    long long v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int t = 0; t < SCAN_ITEMS; ++t) {
+      const int64_t i = base + t;
+      v[t] = i < n ? in[i] : 0;
+      s += v[t];
+    }
+    long long tot;
+    long long ex = block_excl_scan(s, &tot) + carry;
+#pragma unroll
+    for (int t = 0; t < SCAN_ITEMS; ++t) {
+      const int64_t i = base + t;
+      if (i < n) out[i] = static_cast<int>(ex);
+      ex += v[t];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    out[n] = static_cast<int>(carry);
+    *total = carry;
+  }
+}
+
 // ------------------------------------------------------- validation --
 // flags[0]: malformed CSR, flags[1]: non-positive or missing diagonal,
 // flags[2]: pattern not structurally symmetric, flags[3]: hash table overflow,
@@ -765,12 +794,6 @@ void read_flags(Mem &m, Flags &f) {
   AMG_CUDA(cudaStreamSynchronize(m.stream));
 }
 
-int read_int(Mem &m, const int *d) {
-  int v = 0;
-  AMG_CUDA(cudaMemcpyAsync(&v, d, sizeof(int), cudaMemcpyDeviceToHost, m.stream));
-  AMG_CUDA(cudaStreamSynchronize(m.stream));
-  return v;
-}
 
 void fail(int code, const char *msg) {
   set_error("%s", msg);
@@ -820,23 +843,34 @@ void free_csr(Mem &m, DCsr &c) {
 
 }  // namespace
 
+// Exclusive scan of n counts into out[0..n] (out[n] = total); returns the
+// total, read back after the scan has been written (one synchronisation).
+// Totals of 2^31 - 1 or more fail (the offsets are int32); out is then
+// incomplete and must not be used.
 int64_t scan_counts(Mem &m, const int *in, int *out, int n) {
   cudaStream_t s = m.stream;
   const int nb = std::max(1, ceil_div(n, SCAN_TILE));
   Buf<long long> bsum(m, (size_t)nb + 1);
-  ProfScope ps(s, AMG_K_SETUP_OTHER, 8.0 * n + 8.0 * nb);
-  k_scan_reduce<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p);
-  AMG_CHECK_LAUNCH();
-  k_scan_blocks<<<1, SCAN_T, 0, s>>>(bsum.p, nb);
-  AMG_CHECK_LAUNCH();
+  {
+    ProfScope ps(s, AMG_K_SETUP_OTHER, 8.0 * n + 8.0 * nb);
+    if (n <= 16 * SCAN_TILE) {
+      k_scan_single<<<1, SCAN_T, 0, s>>>(in, n, out, bsum.p + nb);
+      AMG_CHECK_LAUNCH();
+    } else {
+      k_scan_reduce<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p);
+      AMG_CHECK_LAUNCH();
+      k_scan_blocks<<<1, SCAN_T, 0, s>>>(bsum.p, nb);
+      AMG_CHECK_LAUNCH();
+      k_scan_apply<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p, out);
+      AMG_CHECK_LAUNCH();
+      k_set_last<<<1, 1, 0, s>>>(out, n, bsum.p + nb);
+      AMG_CHECK_LAUNCH();
+    }
+  }
   long long total = 0;
   AMG_CUDA(cudaMemcpyAsync(&total, bsum.p + nb, sizeof(total), cudaMemcpyDeviceToHost, s));
   AMG_CUDA(cudaStreamSynchronize(s));
   if (total >= (1LL << 31) - 1) fail(AMG_ERR_UNSUPPORTED, "more than 2^31-1 nonzeros in one matrix");
-  k_scan_apply<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p, out);
-  AMG_CHECK_LAUNCH();
-  k_set_last<<<1, 1, 0, s>>>(out, n, bsum.p + nb);
-  AMG_CHECK_LAUNCH();
   return total;
 }
 
@@ -946,31 +980,36 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       ST = Buf<uint8_t>(m, std::max<int64_t>(gnnz, 1));
       Buf<double> lam(m, gn);
       Buf<int8_t> st0(m, gn), st1(m, gn);
-      Buf<int> und(m, 1);
       {
         ProfScope ps(s, AMG_K_STRENGTH, rows + 6.0 * nz + 9.0 * gn);
         if (gwide) k_pmis_init_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
         else k_pmis_init<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
         AMG_CHECK_LAUNCH();
       }
-      read_flags(m, fl);
-      if (fl.h[2]) fail(AMG_ERR_INVALID_ARG, "matrix pattern is not structurally symmetric");
-      for (int round = 0;; ++round) {
+      // Rounds run two at a time between host checks: a round after the last
+      // undecided point is gone changes nothing, so the second one is free to
+      // run past the end.  flags[6] / flags[7] count the points each of the
+      // two rounds leaves undecided (read with the error flags, one sync).
+      for (int round = 0;; round += 2) {
         if (round > gn + 1) fail(AMG_ERR_SETUP, "PMIS did not terminate");
-        AMG_CUDA(cudaMemsetAsync(und.p, 0, sizeof(int), s));
-        {
-          ProfScope ps(s, AMG_K_PMIS, rows + 6.0 * nz + 10.0 * gn);
-          if (gwide) k_pmis_select_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, st1.p);
-          else k_pmis_select<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, st1.p);
-          AMG_CHECK_LAUNCH();
+        AMG_CUDA(cudaMemsetAsync(fl.d + 6, 0, 2 * sizeof(int), s));
+        for (int sub = 0; sub < 2; ++sub) {
+          {
+            ProfScope ps(s, AMG_K_PMIS, rows + 6.0 * nz + 10.0 * gn);
+            if (gwide) k_pmis_select_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, st1.p);
+            else k_pmis_select<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, st1.p);
+            AMG_CHECK_LAUNCH();
+          }
+          {
+            ProfScope ps(s, AMG_K_PMIS, rows + 5.0 * nz + 2.0 * gn);
+            if (gwide) k_pmis_update_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, st1.p, st0.p, fl.d + 6 + sub);
+            else k_pmis_update<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, st1.p, st0.p, fl.d + 6 + sub);
+            AMG_CHECK_LAUNCH();
+          }
         }
-        {
-          ProfScope ps(s, AMG_K_PMIS, rows + 5.0 * nz + 2.0 * gn);
-          if (gwide) k_pmis_update_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, st1.p, st0.p, und.p);
-          else k_pmis_update<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, st1.p, st0.p, und.p);
-          AMG_CHECK_LAUNCH();
-        }
-        if (read_int(m, und.p) == 0) break;
+        read_flags(m, fl);
+        if (fl.h[2]) fail(AMG_ERR_INVALID_ARG, "matrix pattern is not structurally symmetric");
+        if (fl.h[7] == 0) break;
       }
       L.cf = m.get_n<int8_t>(n);
       Buf<int> isC(m, n);

@@ -984,29 +984,69 @@ int pcg_impl(amg_hierarchy *h, const double *b, double *x, double rtol, int maxi
   const double upd_bytes = 48.0 + 2.0 * bt + (fp64 ? 0.0 : bt);
   const bool vec_ok = aligned16(x) && aligned16(h->r) && aligned16(h->p) && aligned16(h->q) && aligned16(wd0) &&
                       aligned16(s0) && aligned16(y0) && aligned16(h->z);
-  for (int it = 1; it <= maxit; ++it) {
+  // one iteration: q = A p and (p, q); x, r update; z = M r; p = z + beta p
+  auto iteration = [&]() {
+    cudaStream_t st = h->mem.stream;
     {
-      ProfScope ps(s, AMG_K_SPMV_DOT, spmv_bytes, 0);
+      ProfScope ps(st, AMG_K_SPMV_DOT, spmv_bytes, 0);
       OpSpmvDot op{a64, h->p, h->q, h->sc, h->partials, h->counter};
-      launch_mat(A, A.map64, op, s);
+      launch_mat(A, A.map64, op, st);
     }
     {
-      ProfScope ps(s, AMG_K_PCG_UPDATE, upd_bytes * n, 0);
+      ProfScope ps(st, AMG_K_PCG_UPDATE, upd_bytes * n, 0);
       if (vec_ok)
-        k_pcg_update<T, true><<<grid_for((n + 1) / 2), TPB, 0, s>>>(n, x, h->r, h->p, h->q, wd0, y0, s0, !fp64, pre,
-                                                                    h->sc, h->hist, h->hist_cap, h->d_done,
-                                                                    h->partials, h->counter);
+        k_pcg_update<T, true><<<grid_for((n + 1) / 2), TPB, 0, st>>>(n, x, h->r, h->p, h->q, wd0, y0, s0, !fp64,
+                                                                     pre, h->sc, h->hist, h->hist_cap, h->d_done,
+                                                                     h->partials, h->counter);
       else
-        k_pcg_update<T, false><<<grid_for(n), TPB, 0, s>>>(n, x, h->r, h->p, h->q, wd0, y0, s0, !fp64, pre, h->sc,
-                                                           h->hist, h->hist_cap, h->d_done, h->partials, h->counter);
+        k_pcg_update<T, false><<<grid_for(n), TPB, 0, st>>>(n, x, h->r, h->p, h->q, wd0, y0, s0, !fp64, pre, h->sc,
+                                                            h->hist, h->hist_cap, h->d_done, h->partials, h->counter);
       AMG_CHECK_LAUNCH();
     }
     vcycle<T, TP>(h, h->z, cc);
     {
-      ProfScope ps(s, AMG_K_DIRECTION, 24.0 * n, 0);
-      if (vec_ok) k_direction<true><<<grid_for((n + 1) / 2), TPB, 0, s>>>(n, h->z, h->p, h->sc);
-      else k_direction<false><<<grid_for(n), TPB, 0, s>>>(n, h->z, h->p, h->sc);
+      ProfScope ps(st, AMG_K_DIRECTION, 24.0 * n, 0);
+      if (vec_ok) k_direction<true><<<grid_for((n + 1) / 2), TPB, 0, st>>>(n, h->z, h->p, h->sc);
+      else k_direction<false><<<grid_for(n), TPB, 0, st>>>(n, h->z, h->p, h->sc);
       AMG_CHECK_LAUNCH();
+    }
+  };
+  // Without profiling the iteration is captured once (on a stream of the
+  // hierarchy's own; capture does not run it) and replayed on the solve's
+  // stream: one launch per iteration instead of one per kernel.
+  if (!g_prof.on && (h->iter_exec == nullptr || h->iter_x != x || h->iter_hist != h->hist)) {
+    if (h->iter_exec) AMG_CUDA(cudaGraphExecDestroy(h->iter_exec));
+    h->iter_exec = nullptr;
+    if (!h->cap_stream) AMG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    const long long before = g_launches.load();
+    h->mem.stream = h->cap_stream;
+    AMG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      iteration();
+    } catch (...) {
+      cudaStreamEndCapture(h->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      h->mem.stream = s;
+      throw;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &g);
+    h->mem.stream = s;
+    AMG_CUDA(ec);
+    h->iter_launches = g_launches.load() - before;
+    g_launches.fetch_sub(h->iter_launches);
+    const cudaError_t ei = cudaGraphInstantiate(&h->iter_exec, g, 0);
+    cudaGraphDestroy(g);
+    AMG_CUDA(ei);
+    h->iter_x = x;
+    h->iter_hist = h->hist;
+  }
+  for (int it = 1; it <= maxit; ++it) {
+    if (!g_prof.on) {
+      AMG_CUDA(cudaGraphLaunch(h->iter_exec, s));
+      g_launches.fetch_add(h->iter_launches);
+    } else {
+      iteration();
     }
     AMG_CUDA(cudaEventRecord(h->iter_ev[it & 1], s));
     // keep one iteration in flight: wait for the previous one, then test the flag
@@ -1131,6 +1171,10 @@ void prepare_solve(amg_hierarchy *h) {
 }
 
 void release_solve(amg_hierarchy *h) {
+  if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
+  h->iter_exec = nullptr;
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  h->cap_stream = nullptr;
   if (h->h_done) cudaFreeHost(h->h_done);
   h->h_done = nullptr;
   for (auto &e : h->iter_ev)

@@ -22,7 +22,9 @@
 //                          products staged in shared memory and summed 32 at a
 //                          time, equal columns grouped and added in p order;
 //   tier 6    ub <= 4096   a block per row, 8192-slot table in shared memory;
-//   tier 7    larger       a block per row, table in a global scratch slice.
+//   tier 7    larger       a block per row, table in a global scratch slice;
+//   tier 8    X row <= 8 entries and ub <= 64 (taken first): a thread per
+//                          row merging the row's sorted Y rows.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,13 +39,17 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int TPB = 256;
 constexpr int WARPS = TPB / 32;
-constexpr int NTIER = 8;
+constexpr int NTIER = 9;
+constexpr int T_GLOBAL = 7;  // block per row, table in global scratch
+constexpr int T_THREAD = 8;  // thread per row, k-way merge
+constexpr int MERGE_L = 8;   // longest X row of the merge tier
 constexpr int BTAB = 8192;  // tier-6 table slots
 constexpr int TILE = 1024;  // rows per binning tile
 
-__device__ __forceinline__ int tier_of(int64_t ub) {
+__device__ __forceinline__ int tier_of(int64_t ub, int xlen) {
+  if (xlen <= MERGE_L && ub <= 64) return T_THREAD;
   return ub <= 32 ? 0 : ub <= 64 ? 1 : ub <= 128 ? 2 : ub <= 256 ? 3 : ub <= 512 ? 4 : ub <= 1024 ? 5
-         : ub <= 4096 ? 6 : 7;
+         : ub <= 4096 ? 6 : T_GLOBAL;
 }
 
 // flags[3] is set on a full hash table (cannot happen while ub <= slots / 2).
@@ -94,11 +100,11 @@ __global__ void __launch_bounds__(TPB) k_bin_rows(int m, const int *__restrict__
       flags[3] = 1;
       ub = 1 << 30;
     }
-    const int c = tier_of(ub);
+    const int c = tier_of(ub, xrp[i + 1] - xrp[i]);
     ub_out[i] = (int)ub;
     tier[i] = (int8_t)c;
     atomicAdd(&cnt[c], 1);
-    if (c == NTIER - 1) atomicMax(max_ub, (int)ub);
+    if (c == T_GLOBAL) atomicMax(max_ub, (int)ub);
   }
   __syncthreads();
   if (threadIdx.x < NTIER) tile_cnt[blockIdx.x * NTIER + threadIdx.x] = cnt[threadIdx.x];
@@ -212,6 +218,59 @@ __device__ __forceinline__ int x_source(const XChunk &c, int u) {
     if (e <= u) lo += step;
   }
   return lo;
+}
+
+// ------------------------------------------------------ merge tier ----
+// A thread per row for short X rows (<= MERGE_L entries, ub <= 64): a k-way
+// merge of the row's Y rows, which are sorted.  Each step takes the smallest
+// head column c and adds the products of the heads at c in ascending p, so
+// every sum is in the canonical order and the output comes out sorted.
+__global__ void __launch_bounds__(TPB) k_spgemm_merge(const int *__restrict__ rows, int nrows,
+                                                      const int *__restrict__ xrp, const int *__restrict__ xci,
+                                                      const double *__restrict__ xv, const int *__restrict__ yrp,
+                                                      const int *__restrict__ yci, const double *__restrict__ yv,
+                                                      const int *__restrict__ off, int *__restrict__ tci,
+                                                      double *__restrict__ tcv, int *__restrict__ cnt) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
+    const int i = rows[r];
+    const int xb = xrp[i], len = xrp[i + 1] - xb;
+    int hp[MERGE_L], he[MERGE_L], hc[MERGE_L];
+    double xa[MERGE_L];
+#pragma unroll
+    for (int t = 0; t < MERGE_L; ++t) {
+      hp[t] = he[t] = 0;
+      hc[t] = INT_MAX;
+      xa[t] = 0.0;
+      if (t < len) {
+        const int k = xci[xb + t];
+        xa[t] = xv[xb + t];
+        hp[t] = yrp[k];
+        he[t] = yrp[k + 1];
+        if (hp[t] < he[t]) hc[t] = yci[hp[t]];
+      }
+    }
+    const int base = off[i];
+    int count = 0;
+    for (;;) {
+      int c = hc[0];
+#pragma unroll
+      for (int t = 1; t < MERGE_L; ++t) c = min(c, hc[t]);
+      if (c == INT_MAX) break;
+      double acc = 0.0;
+#pragma unroll
+      for (int t = 0; t < MERGE_L; ++t) {
+        if (hc[t] == c) {
+          acc = __dadd_rn(acc, __dmul_rn(xa[t], yv[hp[t]]));
+          ++hp[t];
+          hc[t] = hp[t] < he[t] ? yci[hp[t]] : INT_MAX;
+        }
+      }
+      tci[base + count] = c;
+      tcv[base + count] = acc;
+      ++count;
+    }
+    cnt[i] = count;
+  }
 }
 
 // ---------------------------------------------------------- tier 0 ----
@@ -523,9 +582,9 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
   }
   int gcap = 2;
   while (gcap < 2 * std::max(hm[NTIER], 1)) gcap <<= 1;
-  const int gblocks = std::min(hm[7], kNumSMs * 2);
+  const int gblocks = std::min(hm[T_GLOBAL], kNumSMs * 2);
   Buf<int> gscr;
-  if (hm[7] > 0) gscr = Buf<int>(m, (size_t)gblocks * ((size_t)gcap + gcap / 2));
+  if (hm[T_GLOBAL] > 0) gscr = Buf<int>(m, (size_t)gblocks * ((size_t)gcap + gcap / 2));
   static bool attr = false;
   if (!attr) {
     AMG_CUDA(cudaFuncSetAttribute(k_spgemm_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem));
@@ -541,6 +600,12 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
   const Args a{&X, &Y, off.p, tci.p, tcv.p, cnt.p, flags, s};
   {
     ProfScope ps(s, AMG_K_SPGEMM, xy_bytes + 12.0 * total_ub);
+    if (hm[T_THREAD] > 0) {
+      const int grid = std::max(1, std::min(ceil_div(hm[T_THREAD], TPB), kNumSMs * 16));
+      k_spgemm_merge<<<grid, TPB, 0, s>>>(list(T_THREAD), hm[T_THREAD], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off.p,
+                                          tci.p, tcv.p, cnt.p);
+      AMG_CHECK_LAUNCH();
+    }
     if (hm[0] > 0) {
       const int grid = std::max(1, std::min(ceil_div(hm[0], WARPS), kNumSMs * 32));
       k_spgemm_reg<<<grid, TPB, 0, s>>>(list(0), hm[0], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off.p, tci.p, tcv.p, cnt.p);
@@ -557,8 +622,8 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
                                                           tci.p, tcv.p, cnt.p, flags, nullptr, 0);
       AMG_CHECK_LAUNCH();
     }
-    if (hm[7] > 0) {
-      k_spgemm_block<true><<<gblocks, TPB, 0, s>>>(list(7), hm[7], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off.p, tci.p,
+    if (hm[T_GLOBAL] > 0) {
+      k_spgemm_block<true><<<gblocks, TPB, 0, s>>>(list(T_GLOBAL), hm[T_GLOBAL], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off.p, tci.p,
                                                    tcv.p, cnt.p, flags, gscr.p, gcap);
       AMG_CHECK_LAUNCH();
     }
