@@ -107,6 +107,7 @@ struct Sell {
   double *v = nullptr;            // [nent] FP64 values (when needed)
   float *v32 = nullptr;           // FP32 values (FP32 modes)
   __nv_bfloat16 *v16 = nullptr;   // BF16 values (P and R in the BF16 ablation)
+  float2 *vdf = nullptr;          // FP64 values as FP32 pairs hi + lo (level-0 A, batched FP32 modes)
   int *perm = nullptr;            // [n] row held by each slot; nullptr = identity
 };
 

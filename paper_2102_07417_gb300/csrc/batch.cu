@@ -35,6 +35,30 @@ __device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(
 __device__ __forceinline__ float tof(float v) { return v; }
 __device__ __forceinline__ double tof(double v) { return v; }
 
+// ------------------------------------------------------ double-float --
+// The FP64 outer product of the FP32 modes in FP32 arithmetic (GB300 runs
+// FP32 at many times its FP64 rate): a value v is held as the pair
+// hi = fl32(v), lo = fl32(v - hi), and products are accumulated with the
+// error-free transformations TwoProd (by FMA) and TwoSum (Knuth), keeping
+// about 48 bits -- far below the 1e-8 outer tolerance, with no FP64 FMA.
+__device__ __forceinline__ float2 df_split(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+// (sh, sl) += (ah + al) (ph + pl), dropping al * pl.  Intrinsics keep every
+// operation rounded as written (no contraction).
+__device__ __forceinline__ void df_madd(float ah, float al, float ph, float pl, float &sh, float &sl) {
+  const float prod = __fmul_rn(ah, ph);
+  const float perr = __fmaf_rn(ah, ph, -prod);
+  const float cross = __fmaf_rn(ah, pl, __fmaf_rn(al, ph, perr));
+  const float s = __fadd_rn(sh, prod);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(prod, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, cross));
+}
+
 // Totals over the grid's block partials, run by every thread of the last
 // block: pair (c, j) of the NV x kc (value, column) pairs is summed by
 // TPB / P threads over interleaved blocks, then by one thread over those in
@@ -372,6 +396,73 @@ struct BSpmvDot {
   }
 };
 
+// q = A p in double-float on the sliced-ELLPACK copy (a thread per row over
+// the K columns; a2 = A as FP32 pairs, p2 = p as FP32 pairs), then the same
+// per-column bookkeeping as BSpmvDot (op carries its pointers).
+template <int K>
+__global__ void __launch_bounds__(TPB) k_bsell_df(int n, int k, bool vec, int nslices, const int *__restrict__ off,
+                                                  const int *__restrict__ col, const int *__restrict__ perm,
+                                                  const float2 *__restrict__ a2, const float2 *__restrict__ p2,
+                                                  BSpmvDot<K> op) {
+  if (op.skip()) return;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5, nw = (gridDim.x * TPB) >> 5;
+  BAcc<1> acc[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) acc[j].v[0] = 0.0;
+  for (int sl_ = gw; sl_ < nslices; sl_ += nw) {
+    const int q = sl_ * 32 + lane;
+    const bool valid = q < n;
+    const int row = valid ? (perm ? perm[q] : q) : 0;
+    float sh[K], sl[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) sh[j] = sl[j] = 0.f;
+    const int b = off[sl_] + lane, len = (off[sl_ + 1] - off[sl_]) >> 5;
+#pragma unroll 2
+    for (int t = 0; t < len; ++t) {
+      const int idx = b + 32 * t;
+      const int c = __ldg(col + idx);
+      const float2 a = __ldg(a2 + idx);
+      const float2 *pr = p2 + (size_t)c * k;
+      if (vec && K % 2 == 0) {
+#pragma unroll
+        for (int u = 0; u < K / 2; ++u) {
+          const float4 v = __ldg(reinterpret_cast<const float4 *>(pr) + u);
+          df_madd(a.x, a.y, v.x, v.y, sh[2 * u], sl[2 * u]);
+          df_madd(a.x, a.y, v.z, v.w, sh[2 * u + 1], sl[2 * u + 1]);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          if (j < k) {
+            const float2 v = __ldg(pr + j);
+            df_madd(a.x, a.y, v.x, v.y, sh[j], sl[j]);
+          }
+        }
+      }
+    }
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        if (j < k) {
+          const size_t o = (size_t)row * k + j;
+          const double qd = (double)sh[j] + (double)sl[j];
+          op.q[o] = qd;
+          acc[j].v[0] = fma(op.p[o], qd, acc[j].v[0]);
+        }
+      }
+    }
+  }
+  double tot[1];
+  if (rows_reduce<K, 1>(acc, op.partials, op.counter, tot)) op.finish_col(tot);
+}
+
+// A's FP64 values as FP32 pairs.
+__global__ void k_split_df(int64_t m, const double *__restrict__ v, float2 *__restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = df_split(v[i]);
+}
+
 template <typename TT>
 struct BResid {  // r = y - A s
   using T = TT;
@@ -473,6 +564,7 @@ struct BPost0 {
   double *z;
   const double *r, *q;
   double *p;
+  float2 *p2;  // p as FP32 pairs (double-float outer product), or nullptr
   int mode, flexible;
   BScal *sc;
   const int *done;
@@ -490,7 +582,10 @@ struct BPost0 {
     z[o] = zd;
     if (mode != BPOST_APPLY) {
       acc.v[0] = fma(r[o], zd, acc.v[0]);
-      if (mode == BPOST_FIRST) p[o] = zd;
+      if (mode == BPOST_FIRST) {
+        p[o] = zd;
+        if (p2) p2[o] = df_split(zd);
+      }
       else if (flexible) acc.v[1] = fma(zd, q[o], acc.v[1]);
     }
   }
@@ -714,12 +809,48 @@ __global__ void __launch_bounds__(TPB) k_bupdate_cols(int n, int k, double *__re
 }
 
 // p = z + beta_j p (columns not done)
-__global__ void __launch_bounds__(TPB) k_bdirection(int64_t total, int k, const double *__restrict__ z,
-                                                    double *__restrict__ p, const BScal *sc) {
+template <int K>
+__global__ void __launch_bounds__(TPB) k_bdirection(int n, int k, bool vec, const double *__restrict__ z,
+                                                    double *__restrict__ p, float2 *__restrict__ p2,
+                                                    const BScal *sc) {
+  if (sc->all_done) return;
+  __shared__ double s_beta[KMAX];
+  __shared__ int s_act[KMAX];
+  if (threadIdx.x < KMAX) {
+    const int c = threadIdx.x;
+    s_act[c] = c < k && !sc->done[c];
+    s_beta[c] = c < k ? sc->beta[c] : 0.0;
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const size_t o = (size_t)i * k;
+    double zr[K], pr[K];
+    load_dr<K>(z + o, k, vec, zr);
+    load_dr<K>(p + o, k, vec, pr);
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (s_act[j]) pr[j] = fma(s_beta[j], pr[j], zr[j]);
+    store_dr<K>(p + o, k, vec, pr);
+    if (p2) {
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (j < k && s_act[j]) p2[o + j] = df_split(pr[j]);
+    }
+  }
+}
+
+// Wide batches (K > 8): an entry per thread.
+__global__ void __launch_bounds__(TPB) k_bdirection_cols(int64_t total, int k, const double *__restrict__ z,
+                                                         double *__restrict__ p, float2 *__restrict__ p2,
+                                                         const BScal *sc) {
   if (sc->all_done) return;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(o % k);
-    if (!sc->done[j]) p[o] = fma(sc->beta[j], p[o], z[o]);
+    if (!sc->done[j]) {
+      const double v = fma(sc->beta[j], p[o], z[o]);
+      p[o] = v;
+      if (p2) p2[o] = df_split(v);
+    }
   }
 }
 
@@ -817,6 +948,19 @@ void launch_bupdate(int n, int k, double *x, double *r, const double *p, const d
   AMG_CHECK_LAUNCH();
 }
 
+template <int K>
+void launch_bdirection(int n, int k, const double *z, double *p, float2 *p2, const BScal *sc, cudaStream_t s) {
+  if constexpr (K <= 8) {
+    auto al = [](const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) == 0; };
+    const bool vec = k == K && al(z) && al(p);
+    k_bdirection<K><<<grid_for(n), TPB, 0, s>>>(n, k, vec, z, p, p2, sc);
+  } else {
+    const int64_t nk = (int64_t)n * k;
+    k_bdirection_cols<<<grid_for(nk), TPB, 0, s>>>(nk, k, z, p, p2, sc);
+  }
+  AMG_CHECK_LAUNCH();
+}
+
 // --------------------------------------------------------------- driver --
 template <typename T>
 const T *wdv(const Level &l);
@@ -841,6 +985,7 @@ struct Batch {
   double *partials;
   unsigned int *counter;
   double *r, *zz, *p, *q;  // level-0 CG blocks (FP64)
+  float2 *p2;               // p as FP32 pairs when the outer product runs in double-float, else nullptr
 
   void cycle(int lv, const int *done) {
     cudaStream_t s = st;
@@ -924,13 +1069,48 @@ struct Batch {
     }
     ProfScope ps(s, AMG_K_SMOOTH_POST, (sweep ? 12.0 * A.nnz : 0.0) + 40.0 * nk, 0);
     if (sweep)
-      launch_b<K>(n, k, A, BPost0<K, T, true>{k, bv<K, T>(A), wdv<T>(L0), y, t, zz, r, q, p, mode, flexible, sc,
+      launch_b<K>(n, k, A, BPost0<K, T, true>{k, bv<K, T>(A), wdv<T>(L0), y, t, zz, r, q, p, p2, mode, flexible, sc,
                                                 done, partials, counter}, s);
     else
-      launch_b<K>(n, k, A, BPost0<K, T, false>{k, bv<K, T>(A), wdv<T>(L0), y, t, zz, r, q, p, mode, flexible, sc,
+      launch_b<K>(n, k, A, BPost0<K, T, false>{k, bv<K, T>(A), wdv<T>(L0), y, t, zz, r, q, p, p2, mode, flexible, sc,
                                                  done, partials, counter}, s);
   }
 };
+
+// The double-float outer product is used in the FP32 modes when level 0 has
+// its sliced-ELLPACK copy and the batch is 8 or 16 wide (narrower batches are
+// bound by memory, where FP64 costs nothing extra); its FP32 pairs of A are
+// built on first use and kept with the hierarchy.
+template <int K, typename T>
+bool use_df(amg_hierarchy *h) {
+  const DCsr &A = h->lev[0].A;
+  // below 8 columns the FP64 product is not bound by FP64 arithmetic
+  return std::is_same<T, float>::value && K >= 8 && bsell<K>(A) && A.sell.v != nullptr;
+}
+
+void ensure_df(amg_hierarchy *h, cudaStream_t s) {
+  DCsr &A = h->lev[0].A;
+  if (A.sell.vdf) return;
+  A.sell.vdf = h->mem.get_n<float2>(std::max<int64_t>(A.sell.nent, 1));
+  k_split_df<<<grid_for(A.sell.nent), TPB, 0, s>>>(A.sell.nent, A.sell.v, A.sell.vdf);
+  AMG_CHECK_LAUNCH();
+}
+
+// q = A p and the alpha bookkeeping: double-float when p2 is set, FP64 otherwise.
+template <int K>
+void launch_outer(int n, int k, const DCsr &A, const BSpmvDot<K> &op, const float2 *p2, cudaStream_t s) {
+  if constexpr (K <= 16) {
+    if (p2) {
+      const int grid = std::max(1, std::min(ceil_div(A.sell.nslices, TPB / 32), MAX_GRID));
+      const bool vec = k == K && (reinterpret_cast<uintptr_t>(p2) & 15) == 0;
+      k_bsell_df<K><<<grid, TPB, 0, s>>>(n, k, vec, A.sell.nslices, A.sell.off, A.sell.col, A.sell.perm, A.sell.vdf,
+                                         p2, op);
+      AMG_CHECK_LAUNCH();
+      return;
+    }
+  }
+  launch_b<K>(n, k, A, op, s);
+}
 
 template <int K, typename T, typename TP>
 int batch_impl(amg_hierarchy *h, int k, const double *B, double *X, double rtol, int maxit, int *iters, int *status,
@@ -953,6 +1133,12 @@ int batch_impl(amg_hierarchy *h, int k, const double *B, double *X, double rtol,
     wk.w.emplace_back(m, work ? cnt : 1);
   }
   Buf<double> r(m, nk), zz(m, nk), p(m, nk), q(m, nk);
+  const bool df = use_df<K, T>(h);
+  Buf<float2> p2;
+  if (df) {
+    ensure_df(h, s);
+    p2 = Buf<float2>(m, nk);
+  }
   Buf<BScal> scb(m, 1);
   Buf<double> partials(m, (size_t)MAX_GRID * 3 * KMAX);
   Buf<unsigned int> counter(m, 1);
@@ -973,7 +1159,7 @@ int batch_impl(amg_hierarchy *h, int k, const double *B, double *X, double rtol,
   }
   T *s0 = wk.s[0].p;
   const bool pre = h->prm.nu1 > 0;
-  Batch<K, T, TP> bt{h, s, k, &wk, scb.p, partials.p, counter.p, r.p, zz.p, p.p, q.p};
+  Batch<K, T, TP> bt{h, s, k, &wk, scb.p, partials.p, counter.p, r.p, zz.p, p.p, q.p, p2.p};
   {
     ProfScope ps(s, AMG_K_SOLVE_OTHER, 12.0 * A.nnz + 40.0 * nk, 0);
     launch_b<K>(n, k, A, BInit<K, T>{k, bv<K, double>(A), X, B, r.p, wdv<T>(L0), y0, s0, !fp64, pre, rtol, scb.p, hist.p, maxit + 1,
@@ -984,7 +1170,7 @@ int batch_impl(amg_hierarchy *h, int k, const double *B, double *X, double rtol,
   for (int it = 1; it <= maxit; ++it) {
     {
       ProfScope ps(s, AMG_K_SPMV_DOT, 12.0 * A.nnz + 4.0 * (n + 1) + 24.0 * nk, 0);
-      launch_b<K>(n, k, A, BSpmvDot<K>{k, bv<K, double>(A), p.p, q.p, scb.p, partials.p, counter.p}, s);
+      launch_outer<K>(n, k, A, BSpmvDot<K>{k, bv<K, double>(A), p.p, q.p, scb.p, partials.p, counter.p}, p2.p, s);
     }
     {
       ProfScope ps(s, AMG_K_PCG_UPDATE, (48.0 + 3.0 * sizeof(T)) * nk, 0);
@@ -994,8 +1180,7 @@ int batch_impl(amg_hierarchy *h, int k, const double *B, double *X, double rtol,
     bt.vcycle(BPOST_ITER, flexible, done);
     {
       ProfScope ps(s, AMG_K_DIRECTION, 24.0 * nk, 0);
-      k_bdirection<<<grid_for(nk), TPB, 0, s>>>(nk, k, zz.p, p.p, scb.p);
-      AMG_CHECK_LAUNCH();
+      launch_bdirection<K>(n, k, zz.p, p.p, p2.p, scb.p, s);
     }
     AMG_CUDA(cudaEventRecord(h->iter_ev[it & 1], s));
     if (it > 1) {
@@ -1040,7 +1225,8 @@ int batch_dispatch(amg_hierarchy *h, int k, const double *B, double *X, double r
 // Column j of an n x K block: x = 0, r = b, p = 0; tol_j = rtol ||b||.
 __global__ void __launch_bounds__(TPB) k_admit(int n, int K, int j, unsigned int ticket, const double *__restrict__ b,
                                                double *__restrict__ x, double *__restrict__ r, double *__restrict__ p,
-                                               double rtol, BScal *sc, double *partials, unsigned int *counter) {
+                                               float2 *__restrict__ p2, double rtol, BScal *sc, double *partials,
+                                               unsigned int *counter) {
   __shared__ double red[TPB / 32];
   __shared__ bool last;
   double v = 0.0;
@@ -1050,6 +1236,7 @@ __global__ void __launch_bounds__(TPB) k_admit(int n, int K, int j, unsigned int
     x[o] = 0.0;
     r[o] = bi;
     p[o] = 0.0;
+    if (p2) p2[o] = make_float2(0.f, 0.f);
     v = fma(bi, bi, v);
   }
 #pragma unroll
@@ -1107,6 +1294,7 @@ struct SlotsImpl : SlotsBase {
   double rtol;
   BWork<T> wk;
   Buf<double> X, r, zz, p, q, partials;
+  Buf<float2> p2;  // p as FP32 pairs (double-float outer product), when used
   Buf<BScal> scb;
   Buf<unsigned int> counter;
   BScal *host = nullptr;  // pinned copy for poll
@@ -1144,6 +1332,11 @@ struct SlotsImpl : SlotsBase {
     partials = Buf<double>(mem, (size_t)MAX_GRID * 3 * KMAX);
     scb = Buf<BScal>(mem, 1);
     counter = Buf<unsigned int>(mem, 1);
+    if (use_df<KP, T>(h)) {
+      ensure_df(h, s);
+      p2 = Buf<float2>(mem, nk);
+      AMG_CUDA(cudaMemsetAsync(p2.p, 0, sizeof(float2) * nk, s));
+    }
     if (std::is_same<T, double>::value) {  // FP64: the V-cycle input is the CG residual block
       wk.y[0].reset();
       wk.y[0].p = reinterpret_cast<T *>(r.p);
@@ -1178,8 +1371,8 @@ struct SlotsImpl : SlotsBase {
   void admit(int j, const double *b) override {
     const int n = h->lev[0].A.n;
     ticket[j] = ++admitted;
-    k_admit<<<grid_for(n), TPB, 0, mem.stream>>>(n, K, j, ticket[j], b, X.p, r.p, p.p, rtol, scb.p, partials.p,
-                                                 counter.p);
+    k_admit<<<grid_for(n), TPB, 0, mem.stream>>>(n, K, j, ticket[j], b, X.p, r.p, p.p, p2.p, rtol, scb.p,
+                                                 partials.p, counter.p);
     AMG_CHECK_LAUNCH();
     busy[j] = 1;
   }
@@ -1262,10 +1455,11 @@ struct SlotsImpl : SlotsBase {
     const bool fp64 = std::is_same<T, double>::value;
     const int *done = &scb.p->all_done;
     T *y0 = fp64 ? reinterpret_cast<T *>(r.p) : wk.y[0].p;
-    Batch<KP, T, TP> bt{h, s, K, &wk, scb.p, partials.p, counter.p, r.p, zz.p, p.p, q.p};
+    Batch<KP, T, TP> bt{h, s, K, &wk, scb.p, partials.p, counter.p, r.p, zz.p, p.p, q.p, p2.p};
     {
       ProfScope ps(s, AMG_K_SPMV_DOT, 12.0 * A.nnz + 4.0 * (n + 1) + 24.0 * nk, 0);
-      launch_b<KP>(n, K, A, BSpmvDot<KP>{K, bv<KP, double>(A), p.p, q.p, scb.p, partials.p, counter.p}, s);
+      launch_outer<KP>(n, K, A, BSpmvDot<KP>{K, bv<KP, double>(A), p.p, q.p, scb.p, partials.p, counter.p}, p2.p,
+                       s);
     }
     {
       ProfScope ps(s, AMG_K_PCG_UPDATE, (48.0 + 3.0 * sizeof(T)) * nk, 0);
@@ -1275,8 +1469,7 @@ struct SlotsImpl : SlotsBase {
     bt.vcycle(BPOST_ITER, fp64 ? 0 : 1, done);
     {
       ProfScope ps(s, AMG_K_DIRECTION, 24.0 * nk, 0);
-      k_bdirection<<<grid_for(nk), TPB, 0, s>>>(nk, K, zz.p, p.p, scb.p);
-      AMG_CHECK_LAUNCH();
+      launch_bdirection<KP>(n, K, zz.p, p.p, p2.p, scb.p, s);
     }
   }
   void poll(int *state, int *iters) override {

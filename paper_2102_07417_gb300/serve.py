@@ -56,6 +56,7 @@ class Result:
     iters: int
     status: int
     slot: int = -1
+    capacity: int = 0  # width of the batch the request ran in (rhs)
     x: object = None
 
     @property
@@ -112,24 +113,45 @@ def rhs_for(req: Request, n: int, device="cuda"):
     return torch.rand(n, generator=g, device=device, dtype=torch.float64) * 2.0 - 1.0
 
 
+class _Group:
+    """One continuous-batching block on a resident operator: its slots object, free slots and
+    running requests (slot -> (request, start time))."""
+
+    def __init__(self, op: int, sl, capacity: int):
+        self.op, self.sl, self.capacity = op, sl, capacity
+        self.free = list(range(capacity))
+        self.running = {}
+
+
 class Server:
-    """Resident hierarchies + continuous batching + HBM-gated set-up of new operators."""
+    """Resident hierarchies + continuous batching + HBM-gated set-up of new operators.
+
+    Each resident operator has a batch group of ``capacity`` columns and (``solo``) a one-column
+    group: a step costs about a + b k for k columns, so a request that finds the operator idle
+    runs alone (cheapest step), and requests that overlap share the batch group's steps."""
 
     def __init__(self, operators, precision: int = amg.PREC_FP32, capacity: int = 4, rtol: float = 1e-8,
                  maxit: int = 200, workers: int = 4, sigma: float = 1.0, hbm_budget: int | None = None,
-                 hbm_reserve: int = 2 << 30, keep_x: bool = False, depth: int = 2):
+                 hbm_reserve: int = 2 << 30, keep_x: bool = False, depth: int = 2, solo: bool = True):
         import torch
 
         self.torch = torch
         self.precision, self.capacity, self.rtol, self.maxit = precision, capacity, rtol, maxit
         self.sigma, self.keep_x = sigma, keep_x
         self.hier, self.slots, self.n = [], [], []
-        for A in operators:
+        # per operator: [solo group (one column), batch group (capacity columns)] or [batch group]
+        self.groups = []
+        for i, A in enumerate(operators):
             st = torch.cuda.Stream()
             h = amg.Hierarchy(A, stream=st, precision=precision)  # waits for A's producers
             self.hier.append(h)
-            self.slots.append(h.slots(capacity, rtol=rtol, maxit=maxit, stream=st))
             self.n.append(h.n)
+            gs = []
+            if solo and capacity > 1:
+                gs.append(_Group(i, h.slots(1, rtol=rtol, maxit=maxit, stream=torch.cuda.Stream()), 1))
+            gs.append(_Group(i, h.slots(capacity, rtol=rtol, maxit=maxit, stream=st), capacity))
+            self.groups.append(gs)
+            self.slots.extend(g.sl for g in gs)
         # bytes of hierarchy per unknown, from the resident operators (set-up estimate: x3 for
         # the temporaries of the Galerkin products and the solve vectors)
         self.bytes_per_row = max(h.nbytes() / h.n for h in self.hier) * 3.0
@@ -138,7 +160,9 @@ class Server:
         self.hbm_reserve = hbm_reserve
         self.depth = depth
         self._x_scratch = [None] * len(self.hier)
-        self._streams = [torch.cuda.Stream() for _ in range(workers)]
+        # set-up streams run at high priority: a set-up is a chain of small, latency-bound kernels
+        # (and host round trips) that would otherwise queue behind the resident operators' steps
+        self._streams = [torch.cuda.Stream(priority=-1) for _ in range(workers)]
         self._free_streams = collections.deque(range(workers))
         self._lock = threading.Lock()
         self.stats = {"max_running_slots": 0, "max_matrix_inflight": 0, "steps": 0, "rejected": 0}
@@ -175,7 +199,9 @@ class Server:
         try:
             with torch.cuda.stream(st):
                 A = pr.diffusion3d_device(req.m, self.sigma, req.seed, stream=st)
-                h = amg.Hierarchy(A, stream=st, precision=self.precision)
+                # the library's own stream-ordered allocator: no Python callback (and no GIL) per
+                # allocation inside the set-up
+                h = amg.Hierarchy(A, stream=st, precision=self.precision, torch_allocator=False)
                 b = rhs_for(req, h.n)
                 x, it, status, _ = h.solve(b, rtol=self.rtol, maxit=self.maxit, stream=st)
                 st.synchronize()
@@ -192,8 +218,6 @@ class Server:
         reqs = sorted(requests, key=lambda r: r.t_arrival)
         rhs_q = [collections.deque() for _ in self.hier]
         mat_q = collections.deque()
-        free = [list(range(self.capacity)) for _ in self.hier]
-        running = [dict() for _ in self.hier]  # slot -> (request, t_start)
         results: list[Result] = []
         inflight = {}  # future -> (request, bytes)
         pool = ThreadPoolExecutor(max_workers=self.workers)
@@ -231,44 +255,51 @@ class Server:
                     inflight.pop(f)
                     results.append(f.result())
                 # right-hand sides: admitted into free slots at the iteration boundary
-                for i, sl in enumerate(self.slots):
-                    while rhs_q[i] and free[i]:
+                for i, gs in enumerate(self.groups):
+                    batch = gs[-1]
+                    while rhs_q[i]:
+                        g = batch
+                        if len(gs) > 1 and not batch.running and gs[0].free:
+                            g = gs[0]  # the operator is idle: run alone
+                        if not g.free:
+                            break
                         r = rhs_q[i].popleft()
-                        s = free[i].pop(0)
-                        with torch.cuda.stream(sl.tstream):
+                        s_ = g.free.pop(0)
+                        with torch.cuda.stream(g.sl.tstream):
                             b = rhs_for(r, self.n[i])
-                            sl.admit(s, b)
-                        running[i][s] = (r, clock() - t0)
-                active = [i for i in range(len(self.slots)) if running[i]]
+                            g.sl.admit(s_, b)
+                        g.running[s_] = (r, clock() - t0)
+                active = [g for gs in self.groups for g in gs if g.running]
                 self.stats["max_running_slots"] = max(self.stats["max_running_slots"],
-                                                      sum(len(running[i]) for i in active))
-                # steps stay `depth` deep in flight on every operator; results are read from the
+                                                      sum(len(g.running) for g in active))
+                # steps stay `depth` deep in flight on every group; results are read from the
                 # snapshots of finished steps without waiting (a converged column is frozen, so
                 # the steps behind it leave its solution unchanged)
                 progressed = False
                 blocked = []
-                for i in active:
-                    sl = self.slots[i]
+                for g in active:
+                    sl, i = g.sl, g.op
                     state, iters, done, issued = sl.query()
-                    for s in list(running[i]):
-                        if state[s] == amg.SLOT_RUNNING:
+                    for s_ in list(g.running):
+                        if state[s_] == amg.SLOT_RUNNING:
                             continue
-                        r, t_start = running[i].pop(s)
+                        r, t_start = g.running.pop(s_)
                         t_done = clock() - t0
                         with torch.cuda.stream(sl.tstream):
-                            x = sl.retire(s) if self.keep_x else sl.retire(s, self._scratch(i))
-                        st = amg.AMG_OK if state[s] == amg.SLOT_CONVERGED else int(state[s])
+                            x = sl.retire(s_) if self.keep_x else sl.retire(s_, self._scratch(i))
+                        st = amg.AMG_OK if state[s_] == amg.SLOT_CONVERGED else int(state[s_])
                         results.append(Result(r.rid, "rhs", self.n[i], r.t_arrival, t_start, t_done,
-                                              int(iters[s]), st, slot=s, x=x if self.keep_x else None))
-                        free[i].append(s)
-                        free[i].sort()
+                                              int(iters[s_]), st, slot=s_, capacity=g.capacity,
+                                              x=x if self.keep_x else None))
+                        g.free.append(s_)
+                        g.free.sort()
                         progressed = True
-                    if running[i] and issued - done < self.depth:
+                    if g.running and issued - done < self.depth:
                         sl.step()
                         self.stats["steps"] += 1
                         progressed = True
-                    elif running[i]:
-                        blocked.append(i)
+                    elif g.running:
+                        blocked.append(g)
                 if not active:
                     # idle: wait for the next arrival or a finishing set-up
                     wait = 0.0005
@@ -276,7 +307,7 @@ class Server:
                         wait = max(0.0, reqs[nxt].t_arrival - (clock() - t0))
                     time.sleep(min(wait, 0.002))
                 elif not progressed and blocked:
-                    self.slots[blocked[0]].wait()
+                    blocked[0].sl.wait()
         finally:
             pool.shutdown(wait=True)
             for sl in self.slots:

@@ -37,7 +37,7 @@ def test_serve_same_alone_and_in_mix():
         if q.kind == "rhs":
             h = srv.hier[q.target]
             b = serve.rhs_for(q, h.n)
-            alone = h.slots(srv.capacity, rtol=1e-8, maxit=200)
+            alone = h.slots(r.capacity, rtol=1e-8, maxit=200)
             alone.admit(r.slot, b)
             while True:
                 alone.step()
