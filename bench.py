@@ -492,6 +492,10 @@ def run_serving(args):
     res = srv.run(reqs)
     torch.cuda.synchronize()
     out = serve.summarize(res)
+    # the same stream mix at a rate the server sustains, for the latency below saturation
+    low = serve.summarize(srv.run(serve.make_requests(args.serve_requests, rate=150.0, seed=4, frac_matrix=0.3,
+                                                      n_resident=4, m_range=(32, 160))))
+    out["at_150_req_s"] = {k: low[k] for k in ("p50_ms", "p99_ms", "throughput_req_s", "makespan_s") if k in low}
     out.update({"unit": "ms", "offered_rate_req_s": 200.0, "capacity_per_operator": args.serve_capacity,
                 "precision": "fp32 V-cycle + fp64 flexible PCG", "resident_setup_s": t_res,
                 "iters_rhs_median": statistics.median([r.iters for r in res if r.kind == "rhs"] or [0]),

@@ -131,7 +131,7 @@ class Server:
     runs alone (cheapest step), and requests that overlap share the batch group's steps."""
 
     def __init__(self, operators, precision: int = amg.PREC_FP32, capacity: int = 4, rtol: float = 1e-8,
-                 maxit: int = 200, workers: int = 4, sigma: float = 1.0, hbm_budget: int | None = None,
+                 maxit: int = 200, workers: int = 8, sigma: float = 1.0, hbm_budget: int | None = None,
                  hbm_reserve: int = 2 << 30, keep_x: bool = False, depth: int = 2, solo: bool = True):
         import torch
 

@@ -383,6 +383,25 @@ def test_batch_mixed_precision_16_columns(prec):
         assert res < 1.01e-8 * np.linalg.norm(Bm[:, j]) * 10  # true residual near the recursive one
 
 
+@pytest.mark.parametrize("k", [8, 16, 5])
+def test_batch_fp32_sell_double_float(k):
+    """FP32 modes on a matrix with a sliced-ELLPACK copy (64,000 rows): 8- and 16-wide batches take
+    the double-float outer product, a 5-wide batch the FP64 one; every column matches the oracle's
+    FP64 solve (x to 1e-6), reaches rtol 1e-8, and its true residual (FP64, host) is within 10x."""
+    A = LARGE["diffusion3d_40"]()
+    Bm = _batch_rhs(A.n, k, 60)
+    hg = amg.Hierarchy(A, seed=1, precision=amg.PREC_FP32)
+    X, iters, stats, st, _ = hg.solve_batch(dev(Bm), rtol=1e-8)
+    assert st == amg.AMG_OK
+    Xg = X.cpu().numpy()
+    ho = O.Hierarchy(A, seed=1)
+    for j in sorted({0, k // 2, k - 1}):
+        _, xo, ito, _, _ = ho.pcg(Bm[:, j], rtol=1e-8)
+        assert np.linalg.norm(Xg[:, j] - xo) <= 1e-6 * np.linalg.norm(xo)
+        assert abs(iters[j] - ito) <= max(3, ito // 5)
+        assert np.linalg.norm(Bm[:, j] - A.matvec(Xg[:, j])) < 1e-7 * np.linalg.norm(Bm[:, j])
+
+
 def test_batch_column_masks():
     """A zero column converges at iteration 0 and stays zero; the others keep going."""
     A = CASES["poisson2d_64"]()

@@ -64,12 +64,12 @@ def _run_schedule(hg, cap, bs, arrivals, rtol, maxit=500, pipelined=False):
     return out
 
 
-@pytest.mark.parametrize("prec,pipelined", [(amg.PREC_FP64, False), (amg.PREC_FP32, False),
-                                             (amg.PREC_FP32, True)])
-def test_slots_match_batch_columns(prec, pipelined):
-    A, _ = pr.diffusion3d(20, 1.0, 7)
+@pytest.mark.parametrize("prec,pipelined,cap,N", [(amg.PREC_FP64, False, 4, 20), (amg.PREC_FP32, False, 4, 20),
+                                                   (amg.PREC_FP32, True, 4, 20), (amg.PREC_FP32, True, 8, 34)])
+def test_slots_match_batch_columns(prec, pipelined, cap, N):
+    """(8 columns on 39,304 rows: the sliced-ELLPACK kernels and the double-float outer product.)"""
+    A, _ = pr.diffusion3d(N, 1.0, 7)
     hg = amg.Hierarchy(A, seed=0, precision=prec)
-    cap = 4
     bs = _rhs(A.n, 9, 11)
     arrivals = [0, 0, 2, 3, 3, 3, 7, 12, 12]
     out = _run_schedule(hg, cap, bs, arrivals, 1e-8, pipelined=pipelined)
