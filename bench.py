@@ -492,6 +492,7 @@ def run_serving(args):
     res = srv.run(reqs)
     torch.cuda.synchronize()
     launches = amg.launch_count() - l0
+    stats = dict(srv.stats)
     out = serve.summarize(res)
     # the same stream mix at a rate the server sustains, for the latency below saturation
     low = serve.summarize(srv.run(serve.make_requests(args.serve_requests, rate=150.0, seed=4, frac_matrix=0.3,
@@ -500,7 +501,7 @@ def run_serving(args):
     out.update({"unit": "ms", "offered_rate_req_s": 200.0, "capacity_per_operator": args.serve_capacity,
                 "precision": "fp32 V-cycle + fp64 flexible PCG", "resident_setup_s": t_res,
                 "iters_rhs_median": statistics.median([r.iters for r in res if r.kind == "rhs"] or [0]),
-                "gpu_launches": launches, "stats": dict(srv.stats),
+                "gpu_launches": launches, "stats": stats,
                 "config": "512 requests (seed 4), Poisson arrivals 200 req/s, 70% rhs on 4 resident operators "
                           "(48^3, 96^3, 128^3, 160^3 diffusion, sigma 1, seeds 40-43), 30% new operators "
                           "(m log-uniform [32, 160]); rtol 1e-8"})
