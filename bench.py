@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-latency leg")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision leg (FP32 hierarchy and V-cycle, FP64 flexible PCG) of an FP64 run")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-capacity", type=int, default=4)
     ap.add_argument("--no-kernel-events", action="store_true",
@@ -432,6 +434,10 @@ def run_gpu(args, rank, world, dist):
                       f"{ELASTICITY64_FP64_ITERS} iterations x {p.b.shape[1]} columns ({ts_o:.1f} s)")
         cpu = {"value": tp_o + ts_o, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample, "iters": it_o}
 
+    mixed = None
+    if prec == "fp64" and not batch and not args.no_mixed:
+        mixed = run_mixed(args, p, A_dev, b_dev, stream, dev, barrier)
+
     serving = None
     if world == 1 and not args.no_serve:
         serving = run_serving(args)
@@ -462,9 +468,58 @@ def run_gpu(args, rank, world, dist):
         "profile_pass": {"note": "one extra step with events around every launch (not timed)",
                          "kernels_ms": kernels, "by_level_ms": by_level},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-        "serving": serving,
+        "mixed_precision": mixed, "serving": serving,
     }
     print(json.dumps(out), flush=True)
+
+
+def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier):
+    """The same workload with the hierarchy stored and the V-cycle run in FP32 under the FP64
+    flexible PCG (the mixed-precision form): set-up + solve per step timed with CUDA events,
+    its V-cycle bandwidth from one profiled step, and the error against x*."""
+    import numpy as np
+    import torch
+
+    from paper_2102_07417_gb300 import amg
+
+    params = amg.default_params(precision=amg.PREC_FP32, **getattr(p, "params", {}))
+    x_dev = torch.zeros_like(b_dev)
+    rec = {}
+
+    def step():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        h = amg.Hierarchy(A_dev, params, stream=stream)
+        e[1].record(stream)
+        x_dev.zero_()
+        _, it, st, _ = h.solve(b_dev, x_dev, rtol=args.rtol, maxit=1000)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        rec.update(iters=it, status=st, info=h.info())
+        h.close()
+        return e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+
+    for _ in range(max(1, min(args.warmup, 3))):
+        step()
+    amg.profile(True)
+    step()
+    amg.profile(False)
+    prof = amg.profile_read()
+    vb = sum(prof[k]["bytes"] for k in VCYCLE)
+    vt = sum(prof[k]["ms"] for k in VCYCLE)
+    peak, _ = peaks()
+    barrier()
+    times = [step() for _ in range(max(1, min(args.steps, 5)))]
+    tp = statistics.median(t[0] for t in times)
+    ts = statistics.median(t[1] for t in times)
+    x_err = None
+    if p.xstar is not None:
+        x_err = float(np.linalg.norm(x_dev.cpu().numpy() - p.xstar) / np.linalg.norm(p.xstar))
+    return {"precision": "fp32 hierarchy + V-cycle, fp64 flexible PCG", "t_setup_ms": tp, "t_solve_ms": ts,
+            "t_total_ms": tp + ts, "iters": rec["iters"], "status": rec["status"], "x_rel_err": x_err,
+            "steps": len(times),
+            "vcycle_hbm": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s", "peak": peak,
+                           "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None}}
 
 
 def run_serving(args):

@@ -699,11 +699,23 @@ void launch_rows(RowMap map, int n, const int *rp, const int *ci, const Op &op, 
   AMG_CHECK_LAUNCH();
 }
 
-// Runs `op` over the rows of M: the SELL kernel when M has a SELL copy (the
-// op's value pointer must then point into it), else the CSR row kernel.
+// Matrices with at least kSellMinRows rows get a SELL copy (thread per row
+// needs enough rows to fill the GPU; smaller ones use the CSR vector form).
+// The single-vector kernels use it from kSellSolveRows rows up: between the
+// two, rows are few enough (and on coarse levels long enough) that the CSR
+// vector form with a few lanes per row keeps more loads in flight than a lane
+// per row (measured on the 128^3 Poisson hierarchy: level 2, 137K rows of 46
+// entries, smoothing 62 us in CSR against 79 us in SELL).  The batched kernels
+// use the SELL copy whenever it exists.
+constexpr int kSellMinRows = 1 << 15;
+constexpr int kSellSolveRows = 1 << 18;
+inline bool on_sell(const DCsr &M) { return M.use_sell && M.n >= kSellSolveRows; }
+
+// Runs `op` over the rows of M: the SELL kernel when on_sell(M) (the op's
+// value pointer must then point into the SELL copy), else the CSR row kernel.
 template <class Op>
 void launch_mat(const DCsr &M, const RowMap &map, const Op &op, cudaStream_t s) {
-  if (M.use_sell) {
+  if (on_sell(M)) {
     const int grid = std::max(1, std::min(ceil_div(M.sell.nslices, TPB / 32), MAX_GRID));
     k_sell<Op><<<grid, TPB, 0, s>>>(M.n, M.sell.nslices, M.sell.off, M.sell.col, M.sell.perm, op);
     AMG_CHECK_LAUNCH();
@@ -726,18 +738,21 @@ RowMap choose_map(int64_t nnz, int n, bool fp64) {
     m.tr = true;
     return m;
   }
+  // lanes per row: at most the mean row length; from 2^15 rows up at most a
+  // quarter of it (two or more entries per lane: the measured optimum there,
+  // e.g. 4 lanes for 46 entries, 1 lane for P's ~2)
   int cap = 1;
-  while (cap < 32 && cap < avg) cap <<= 1;
+  if (n >= kSellMinRows) {
+    while (cap < 32 && 4 * cap <= avg) cap <<= 1;
+  } else {
+    while (cap < 32 && cap < avg) cap <<= 1;
+  }
   int g = 1;
   while (g < cap && (int64_t)n * g < (1 << 19)) g <<= 1;
   m.g = g;
   m.tr = false;
   return m;
 }
-
-// Matrices with at least this many rows get a SELL copy (thread per row
-// needs enough rows to fill the GPU; smaller ones use the CSR vector form).
-constexpr int kSellMinRows = 1 << 15;
 
 // Builds M's SELL copy with the requested value types.  Rows are permuted
 // (length-sorted within windows) only when that cuts the padding of the
@@ -786,18 +801,18 @@ inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 template <typename T>
 const T *avals(const DCsr &M);
 template <>
-const double *avals<double>(const DCsr &M) { return M.use_sell ? M.sell.v : M.v; }
+const double *avals<double>(const DCsr &M) { return on_sell(M) ? M.sell.v : M.v; }
 template <>
-const float *avals<float>(const DCsr &M) { return M.use_sell ? M.sell.v32 : M.v32; }
+const float *avals<float>(const DCsr &M) { return on_sell(M) ? M.sell.v32 : M.v32; }
 
 template <typename TP>
 const TP *pvals(const DCsr &M);
 template <>
-const double *pvals<double>(const DCsr &M) { return M.use_sell ? M.sell.v : M.v; }
+const double *pvals<double>(const DCsr &M) { return on_sell(M) ? M.sell.v : M.v; }
 template <>
-const float *pvals<float>(const DCsr &M) { return M.use_sell ? M.sell.v32 : M.v32; }
+const float *pvals<float>(const DCsr &M) { return on_sell(M) ? M.sell.v32 : M.v32; }
 template <>
-const __nv_bfloat16 *pvals<__nv_bfloat16>(const DCsr &M) { return M.use_sell ? M.sell.v16 : M.v16; }
+const __nv_bfloat16 *pvals<__nv_bfloat16>(const DCsr &M) { return on_sell(M) ? M.sell.v16 : M.v16; }
 
 template <typename T>
 const T *wdv(const Level &l);
@@ -1202,7 +1217,7 @@ void vcycle_apply(amg_hierarchy *h, const double *y, double *z) {
 void spmv_level(amg_hierarchy *h, int level, const double *x, double *y) {
   const DCsr &A = h->lev[level].A;
   ProfScope ps(h->mem.stream, AMG_K_SOLVE_OTHER, 12.0 * A.nnz + 4.0 * (A.n + 1) + 16.0 * A.n);
-  if (A.use_sell && A.sell.v) {
+  if (on_sell(A) && A.sell.v) {
     OpSpmv op{A.sell.v, x, y};
     launch_mat(A, A.map64, op, h->mem.stream);
   } else {
