@@ -201,6 +201,10 @@ struct amg_hierarchy {
   cudaGraphExec_t iter_exec = nullptr;
   const void *iter_x = nullptr, *iter_hist = nullptr;
   long long iter_launches = 0;
+  // dense operator of the V-cycle from level dense_level down (solve.cu), n x n
+  // FP64 row-major with n = lev[dense_level].A.n; dense_level = -1: none
+  int dense_level = -1;
+  double *dense_op = nullptr;
   size_t bytes = 0;
 };
 

