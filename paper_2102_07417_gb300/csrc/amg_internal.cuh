@@ -247,6 +247,10 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
 
 // device-wide exclusive scan of n int32 counts into out[0..n] (out[n] = total); returns total
 int64_t scan_counts(Mem &mem, const int *in, int *out, int n);
+// the same scan without the read-back: *total_dev (device) receives the total
+void scan_counts_async(Mem &mem, const int *in, int *out, int n, long long *total_dev);
+// fails (AMG_ERR_UNSUPPORTED) on totals that do not fit int32 offsets
+void check_scan_total(long long total);
 
 inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
 

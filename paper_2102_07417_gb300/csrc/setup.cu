@@ -407,6 +407,16 @@ __global__ void k_dof_strength(int n, int bs, const int *__restrict__ rp, const 
 }
 
 // ------------------------------------------------------ interpolation --
+// -1 if v < 0, +1 if v > 0, 0 for +-0 and NaN (what the FP64 comparisons
+// v < 0.0 and v > 0.0 decide), from the bit pattern: the interpolation
+// kernels are bound by the FP64 pipe, which FP64 comparisons also occupy.
+__device__ __forceinline__ int sign_class(double v) {
+  const long long bits = __double_as_longlong(v);
+  const unsigned long long mag = (unsigned long long)bits & 0x7fffffffffffffffULL;
+  if (mag == 0ULL || mag > 0x7ff0000000000000ULL) return 0;
+  return bits < 0 ? -1 : 1;
+}
+
 __global__ void k_interp_count(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                const uint8_t *__restrict__ S, const int8_t *__restrict__ cf,
                                int *__restrict__ cnt) {
@@ -454,12 +464,18 @@ __global__ void k_interp_fill(int n, int bs, const int *__restrict__ rp, const i
       aii = v;
       continue;
     }
-    if (v < 0.0) sn_neg = __dadd_rn(sn_neg, v);
-    if (v > 0.0) sn_pos = __dadd_rn(sn_pos, v);
-    if (S[p] && cf[j]) {
-      ++np;
-      if (v < 0.0) sp_neg = __dadd_rn(sp_neg, v);
-      if (v > 0.0) sp_pos = __dadd_rn(sp_pos, v);
+    const int sg = sign_class(v);
+    const bool strong_c = S[p] && cf[j];
+    np += strong_c;
+    if (sg) {  // one add into the sum of v's sign (the same additions, in the same order)
+      const double sn = __dadd_rn(sg < 0 ? sn_neg : sn_pos, v);
+      if (sg < 0) sn_neg = sn;
+      else sn_pos = sn;
+      if (strong_c) {
+        const double sp = __dadd_rn(sg < 0 ? sp_neg : sp_pos, v);
+        if (sg < 0) sp_neg = sp;
+        else sp_pos = sp;
+      }
     }
   }
   if (np == 0) return;
@@ -470,9 +486,8 @@ __global__ void k_interp_fill(int n, int bs, const int *__restrict__ rp, const i
     const int j = ci[p];
     if (j == i || !S[p] || !cf[j]) continue;
     const double v = a[p];
-    double w = 0.0;
-    if (v < 0.0) w = __ddiv_rn(-__dmul_rn(alpha, v), at);
-    if (v > 0.0) w = __ddiv_rn(-__dmul_rn(beta, v), at);
+    const int sg = sign_class(v);
+    const double w = sg ? __ddiv_rn(-__dmul_rn(sg < 0 ? alpha : beta, v), at) : 0.0;
     pci[pos] = cidx[j];
     pv[pos] = w;
     ++pos;
@@ -648,12 +663,17 @@ __global__ void __launch_bounds__(256) k_interp_fill_w(int n, int bs, const int 
           aii = v;
           continue;
         }
-        if (v < 0.0) sn_neg = __dadd_rn(sn_neg, v);
-        if (v > 0.0) sn_pos = __dadd_rn(sn_pos, v);
-        if (k & 2) {
-          ++np;
-          if (v < 0.0) sp_neg = __dadd_rn(sp_neg, v);
-          if (v > 0.0) sp_pos = __dadd_rn(sp_pos, v);
+        const int sg = sign_class(v);
+        np += (k & 2) ? 1 : 0;
+        if (sg) {
+          const double sn = __dadd_rn(sg < 0 ? sn_neg : sn_pos, v);
+          if (sg < 0) sn_neg = sn;
+          else sn_pos = sn;
+          if (k & 2) {
+            const double sp = __dadd_rn(sg < 0 ? sp_neg : sp_pos, v);
+            if (sg < 0) sp_neg = sp;
+            else sp_pos = sp;
+          }
         }
       }
     }
@@ -681,9 +701,8 @@ __global__ void __launch_bounds__(256) k_interp_fill_w(int n, int bs, const int 
     const unsigned bal = __ballot_sync(0xffffffffu, sel);
     if (sel) {
       const double v = a[p];
-      double wv = 0.0;
-      if (v < 0.0) wv = __ddiv_rn(-__dmul_rn(alpha, v), at);
-      if (v > 0.0) wv = __ddiv_rn(-__dmul_rn(beta, v), at);
+      const int sg = sign_class(v);
+      const double wv = sg ? __ddiv_rn(-__dmul_rn(sg < 0 ? alpha : beta, v), at) : 0.0;
       const int q = pos + __popc(bal & ((1u << lane) - 1u));
       pci[q] = cidx[j];
       pv[q] = wv;
@@ -814,7 +833,10 @@ void transpose(Mem &m, const DCsr &P, int ncols, DCsr &R) {
   R.ncols = P.n;
   R.nnz = P.nnz;
   R.rp = m.get_n<int>((size_t)ncols + 1);
-  scan_counts(m, cnt.p, R.rp, ncols);
+  {
+    Buf<long long> tot(m, 1);  // R.nnz = P.nnz is known: no read-back
+    scan_counts_async(m, cnt.p, R.rp, ncols, tot.p);
+  }
   R.ci = m.get_n<int>(std::max<int64_t>(R.nnz, 1));
   R.v = m.get_n<double>(std::max<int64_t>(R.nnz, 1));
   Buf<int> fill(m, (size_t)ncols + 1);
@@ -843,34 +865,45 @@ void free_csr(Mem &m, DCsr &c) {
 
 }  // namespace
 
-// Exclusive scan of n counts into out[0..n] (out[n] = total); returns the
-// total, read back after the scan has been written (one synchronisation).
-// Totals of 2^31 - 1 or more fail (the offsets are int32); out is then
-// incomplete and must not be used.
-int64_t scan_counts(Mem &m, const int *in, int *out, int n) {
+// Exclusive scan of n counts into out[0..n] (out[n] = total), enqueued on the
+// stream without waiting; *total_dev receives the total.
+void scan_counts_async(Mem &m, const int *in, int *out, int n, long long *total_dev) {
   cudaStream_t s = m.stream;
   const int nb = std::max(1, ceil_div(n, SCAN_TILE));
-  Buf<long long> bsum(m, (size_t)nb + 1);
-  {
-    ProfScope ps(s, AMG_K_SETUP_OTHER, 8.0 * n + 8.0 * nb);
-    if (n <= 16 * SCAN_TILE) {
-      k_scan_single<<<1, SCAN_T, 0, s>>>(in, n, out, bsum.p + nb);
-      AMG_CHECK_LAUNCH();
-    } else {
-      k_scan_reduce<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p);
-      AMG_CHECK_LAUNCH();
-      k_scan_blocks<<<1, SCAN_T, 0, s>>>(bsum.p, nb);
-      AMG_CHECK_LAUNCH();
-      k_scan_apply<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p, out);
-      AMG_CHECK_LAUNCH();
-      k_set_last<<<1, 1, 0, s>>>(out, n, bsum.p + nb);
-      AMG_CHECK_LAUNCH();
-    }
+  ProfScope ps(s, AMG_K_SETUP_OTHER, 8.0 * n + 8.0 * nb);
+  if (n <= 16 * SCAN_TILE) {
+    k_scan_single<<<1, SCAN_T, 0, s>>>(in, n, out, total_dev);
+    AMG_CHECK_LAUNCH();
+  } else {
+    Buf<long long> bsum(m, (size_t)nb + 1);  // released in stream order
+    k_scan_reduce<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p);
+    AMG_CHECK_LAUNCH();
+    k_scan_blocks<<<1, SCAN_T, 0, s>>>(bsum.p, nb);
+    AMG_CHECK_LAUNCH();
+    k_scan_apply<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p, out);
+    AMG_CHECK_LAUNCH();
+    k_set_last<<<1, 1, 0, s>>>(out, n, bsum.p + nb);
+    AMG_CHECK_LAUNCH();
+    AMG_CUDA(cudaMemcpyAsync(total_dev, bsum.p + nb, sizeof(long long), cudaMemcpyDeviceToDevice, s));
   }
-  long long total = 0;
-  AMG_CUDA(cudaMemcpyAsync(&total, bsum.p + nb, sizeof(total), cudaMemcpyDeviceToHost, s));
-  AMG_CUDA(cudaStreamSynchronize(s));
+}
+
+// Totals of 2^31 - 1 or more fail (the offsets are int32).
+void check_scan_total(long long total) {
   if (total >= (1LL << 31) - 1) fail(AMG_ERR_UNSUPPORTED, "more than 2^31-1 nonzeros in one matrix");
+}
+
+// Exclusive scan of n counts into out[0..n] (out[n] = total); returns the
+// total, read back after the scan has been written (one synchronisation).
+// Totals of 2^31 - 1 or more fail; out is then incomplete and must not be used.
+int64_t scan_counts(Mem &m, const int *in, int *out, int n) {
+  cudaStream_t s = m.stream;
+  Buf<long long> tot(m, 1);
+  scan_counts_async(m, in, out, n, tot.p);
+  long long total = 0;
+  AMG_CUDA(cudaMemcpyAsync(&total, tot.p, sizeof(total), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  check_scan_total(total);
   return total;
 }
 
@@ -886,6 +919,10 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
   Flags fl;
   Buf<int> flags_buf(m, 8);
   fl.d = flags_buf.p;
+  auto sync_flags = [&]() {
+    read_flags(m, fl);
+    if (fl.h[3]) fail(AMG_ERR_UNSUPPORTED, "SpGEMM hash table overflow");
+  };
   AMG_CUDA(cudaMemsetAsync(fl.d, 0, sizeof(int) * 8, s));
 
   // level 0: copy A
@@ -904,7 +941,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     k_validate<<<ceil_div(n0, TPB), TPB, 0, s>>>(n0, nnz0, A0.rp, A0.ci, A0.v, fl.d);
     AMG_CHECK_LAUNCH();
   }
-  read_flags(m, fl);
+  sync_flags();
   if (fl.h[0]) fail(AMG_ERR_INVALID_ARG, "malformed CSR (row pointers, column range or unsorted columns)");
   if (fl.h[1]) fail(AMG_ERR_NOT_SPD, "a diagonal entry is missing or not positive");
 
@@ -947,7 +984,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
           k_block_check<<<gnn, TPB, 0, s>>>(nn, bs, A.rp, A.ci, fl.d);
           AMG_CHECK_LAUNCH();
         }
-        read_flags(m, fl);
+        sync_flags();
         if (fl.h[5]) {
           if (k == 0) fail(AMG_ERR_INVALID_ARG, "block_size > 1 needs every coupled node pair stored as a full block");
           fail(AMG_ERR_SETUP, "a coarse operator lost its block structure");
@@ -1007,7 +1044,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
             AMG_CHECK_LAUNCH();
           }
         }
-        read_flags(m, fl);
+        sync_flags();
         if (fl.h[2]) fail(AMG_ERR_INVALID_ARG, "matrix pattern is not structurally symmetric");
         if (fl.h[7] == 0) break;
       }
@@ -1039,7 +1076,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
         k_cholesky<<<1, 256, 0, s>>>(n, h->L, fl.d);
         AMG_CHECK_LAUNCH();
       }
-      read_flags(m, fl);
+      sync_flags();
       if (fl.h[4]) fail(AMG_ERR_NOT_SPD, "dense Cholesky of the last level met a non-positive pivot");
       h->Linv = m.get_n<double>((size_t)n * n);
       {
@@ -1084,8 +1121,8 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     spgemm(m, fl.d, A, P, nc, AP);
     spgemm(m, fl.d, L.R, AP, nc, h->lev[k + 1].A);
     free_csr(m, AP);
-    read_flags(m, fl);
-    if (fl.h[3]) fail(AMG_ERR_UNSUPPORTED, "SpGEMM hash table overflow");
+    // the SpGEMM's overflow flag is read with the next level's first flag
+    // read (every level reads its flags at least once), not with a sync here
     ++k;
   }
 }

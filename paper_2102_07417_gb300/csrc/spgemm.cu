@@ -222,9 +222,15 @@ __device__ __forceinline__ int x_source(const XChunk &c, int u) {
 
 // ------------------------------------------------------ merge tier ----
 // A thread per row for short X rows (<= MERGE_L entries, ub <= 64): a k-way
-// merge of the row's Y rows, which are sorted.  Each step takes the smallest
-// head column c and adds the products of the heads at c in ascending p, so
-// every sum is in the canonical order and the output comes out sorted.
+// merge of the row's Y rows, which are sorted.  Each iteration takes ONE
+// product: the head with the smallest column, ties to the lowest t (= lowest
+// p), so the products of one output column arrive in ascending p and are
+// added left to right from 0 -- the canonical order -- and the output comes
+// out sorted.  One product per iteration keeps every FP64 instruction useful:
+// the kernel is bound by the FP64 pipe, and the earlier form (all heads at
+// the current column per iteration, unrolled) issued a predicated multiply and
+// add for each of the MERGE_L heads at every output column (81% of the FP64
+// pipe busy for ~2 products per output on the 128^3 Poisson A P).
 __global__ void __launch_bounds__(TPB) k_spgemm_merge(const int *__restrict__ rows, int nrows,
                                                       const int *__restrict__ xrp, const int *__restrict__ xci,
                                                       const double *__restrict__ xv, const int *__restrict__ yrp,
@@ -250,22 +256,48 @@ __global__ void __launch_bounds__(TPB) k_spgemm_merge(const int *__restrict__ ro
       }
     }
     const int base = off[i];
-    int count = 0;
+    int count = 0, ccol = -1;
+    double acc = 0.0;
     for (;;) {
-      int c = hc[0];
+      // smallest head column; the strict < keeps the lowest t among equals
+      int bc = hc[0], bt = 0;
 #pragma unroll
-      for (int t = 1; t < MERGE_L; ++t) c = min(c, hc[t]);
-      if (c == INT_MAX) break;
-      double acc = 0.0;
-#pragma unroll
-      for (int t = 0; t < MERGE_L; ++t) {
-        if (hc[t] == c) {
-          acc = __dadd_rn(acc, __dmul_rn(xa[t], yv[hp[t]]));
-          ++hp[t];
-          hc[t] = hp[t] < he[t] ? yci[hp[t]] : INT_MAX;
+      for (int t = 1; t < MERGE_L; ++t)
+        if (hc[t] < bc) {
+          bc = hc[t];
+          bt = t;
         }
+      if (bc == INT_MAX) break;
+      int q = 0, e = 0;
+      double x = 0.0;
+#pragma unroll
+      for (int t = 0; t < MERGE_L; ++t)
+        if (t == bt) {
+          q = hp[t];
+          e = he[t];
+          x = xa[t];
+        }
+      const double prod = __dmul_rn(x, yv[q]);
+      const int cn = q + 1 < e ? yci[q + 1] : INT_MAX;
+#pragma unroll
+      for (int t = 0; t < MERGE_L; ++t)
+        if (t == bt) {
+          hp[t] = q + 1;
+          hc[t] = cn;
+        }
+      if (bc != ccol) {
+        if (ccol >= 0) {
+          tci[base + count] = ccol;
+          tcv[base + count] = acc;
+          ++count;
+        }
+        ccol = bc;
+        acc = 0.0;
       }
-      tci[base + count] = c;
+      acc = __dadd_rn(acc, prod);
+    }
+    if (ccol >= 0) {
+      tci[base + count] = ccol;
       tcv[base + count] = acc;
       ++count;
     }
@@ -572,10 +604,15 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
     k_tier_scatter<<<ntiles, TPB, 0, s>>>(rows, tier.p, tile_off.p, lists.p);
     AMG_CHECK_LAUNCH();
   }
-  const int64_t total_ub = scan_counts(m, ub.p, off.p, rows);  // syncs the stream
+  // the scan's total and the tier counts come back in one synchronisation
+  Buf<long long> ub_tot(m, 1);
+  scan_counts_async(m, ub.p, off.p, rows, ub_tot.p);
   int hm[NTIER + 1];
+  long long total_ub = 0;
   AMG_CUDA(cudaMemcpyAsync(hm, meta.p, sizeof(hm), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaMemcpyAsync(&total_ub, ub_tot.p, sizeof(total_ub), cudaMemcpyDeviceToHost, s));
   AMG_CUDA(cudaStreamSynchronize(s));
+  check_scan_total(total_ub);
   if (hm[NTIER] > (1 << 22)) {
     set_error("SpGEMM row product bound above 2^22 entries");
     throw Status{AMG_ERR_UNSUPPORTED};
