@@ -240,6 +240,14 @@ __global__ void k_pmis_init(int n, const int *__restrict__ rp, const int *__rest
   st[i] = cnt == 0 ? ST_F : ST_U;
 }
 
+// A measure's bit pattern as a signed integer.  Measures are finite and
+// non-negative (|S_i^T| + u with u in [0, 1)), and for non-negative doubles the
+// bit patterns order exactly as the values do, so the comparisons below take
+// the same decisions as FP64 comparisons, on the integer pipe.
+__device__ __forceinline__ long long lam_key(const double *__restrict__ lam, int i) {
+  return __double_as_longlong(lam[i]);
+}
+
 // Selection step of a round: an undecided point beating every undecided
 // strong neighbour (either direction) becomes a new C point.
 __global__ void k_pmis_select(int n, const int *__restrict__ rp, const int *__restrict__ ci,
@@ -253,13 +261,13 @@ __global__ void k_pmis_select(int n, const int *__restrict__ rp, const int *__re
     st_new[i] = s;
     return;
   }
-  const double li = lam[i];
+  const long long li = lam_key(lam, i);
   bool is_max = true;
   for (int p = rp[i]; p < rp[i + 1] && is_max; ++p) {
     if (!(S[p] | ST[p])) continue;
     const int j = ci[p];
     if (st_old[j] != ST_U) continue;
-    const double lj = lam[j];
+    const long long lj = lam_key(lam, j);
     if (lj > li || (lj == li && j > i)) is_max = false;
   }
   st_new[i] = is_max ? ST_NEWC : ST_U;
@@ -564,13 +572,13 @@ __global__ void k_pmis_select_w(int n, const int *__restrict__ rp, const int *__
     if (lane == 0) st_new[i] = s0;
     return;
   }
-  const double li = lam[i];
+  const long long li = lam_key(lam, i);
   bool beaten = false;
   for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
     if (!(S[p] | ST[p])) continue;
     const int j = ci[p];
     if (st_old[j] != ST_U) continue;
-    const double lj = lam[j];
+    const long long lj = lam_key(lam, j);
     if (lj > li || (lj == li && j > i)) beaten = true;
   }
   beaten = __any_sync(0xffffffffu, beaten);

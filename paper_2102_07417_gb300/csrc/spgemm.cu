@@ -539,15 +539,18 @@ __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ ro
   }
 }
 
-// Copies each row's count entries from its scratch slot to the final CSR.
+// Copies each row's count entries from its scratch slot to the final CSR:
+// G lanes per row (G = 8 when rows are short, so that most lanes of a warp
+// copy something; a warp per row otherwise).
+template <int G>
 __global__ void __launch_bounds__(TPB) k_compact(int m, const int *__restrict__ off, const int *__restrict__ tci,
                                                  const double *__restrict__ tcv, const int *__restrict__ crp,
                                                  int *__restrict__ cci, double *__restrict__ cv) {
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  for (int i = gw; i < m; i += nw) {
+  const int sub = threadIdx.x & (G - 1);
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) / G, ng = (gridDim.x * blockDim.x) / G;
+  for (int i = g; i < m; i += ng) {
     const int src = off[i], dst = crp[i], len = crp[i + 1] - dst;
-    for (int e = lane; e < len; e += 32) {
+    for (int e = sub; e < len; e += G) {
       cci[dst + e] = tci[src + e];
       cv[dst + e] = tcv[src + e];
     }
@@ -673,8 +676,12 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
   C.v = m.get_n<double>(std::max<int64_t>(C.nnz, 1));
   {
     ProfScope ps(s, AMG_K_SPGEMM, 24.0 * C.nnz + 8.0 * rows);
-    k_compact<<<std::max(1, std::min(ceil_div(rows, WARPS), kNumSMs * 32)), TPB, 0, s>>>(rows, off.p, tci.p, tcv.p,
-                                                                                         C.rp, C.ci, C.v);
+    if (C.nnz <= 12LL * rows)
+      k_compact<8><<<std::max(1, std::min(ceil_div(rows, TPB / 8), kNumSMs * 32)), TPB, 0, s>>>(
+          rows, off.p, tci.p, tcv.p, C.rp, C.ci, C.v);
+    else
+      k_compact<32><<<std::max(1, std::min(ceil_div(rows, WARPS), kNumSMs * 32)), TPB, 0, s>>>(
+          rows, off.p, tci.p, tcv.p, C.rp, C.ci, C.v);
     AMG_CHECK_LAUNCH();
   }
 }
