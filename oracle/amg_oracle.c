@@ -335,7 +335,8 @@ int or_pmis(int n, const int *rp, const int *ci, const unsigned char *S, uint64_
 /* N_i the off-diagonal neighbours (sums in ascending column order):      */
 /*   alpha = sum_{N_i} a^- / sum_{P_i} a^-,  beta = sum_{N_i} a^+ / sum_{P_i} a^+ */
 /*   at = a_ii + sum_{N_i} a^+  if P_i has no positive entry, else a_ii    */
-/*   w_ij = -(alpha * a_ij) / at  (a_ij < 0),  -(beta * a_ij) / at  (a_ij > 0) */
+/*   w_ij = a_ij * (-(alpha / at))  (a_ij < 0),  a_ij * (-(beta / at))  (a_ij > 0) */
+/* (the weight -alpha a_ij / at with the row factor alpha / at formed once) */
 /* Empty P_i gives an empty row.  Capacity `cap` bounds nnz(P).           */
 /* ------------------------------------------------------------------ */
 /* Systems (block size bs > 1, unknowns numbered node-major): unknown-wise  */
@@ -397,13 +398,14 @@ static int direct_interp(int n, const int *rp, const int *ci, const double *a, c
       double alpha = (sp_neg != 0.0) ? sn_neg / sp_neg : 0.0;
       double beta = (sp_pos != 0.0) ? sn_pos / sp_pos : 0.0;
       double at = (sp_pos != 0.0) ? aii : aii + sn_pos;
+      double f_neg = -(alpha / at), f_pos = -(beta / at);
       if (pos + np > cap) return OR_ERR_MEM;
       for (int p = rp[i]; p < rp[i + 1]; ++p) {
         int j = ci[p];
         if (j == i || !S[p] || !cf[j]) continue;
         double v = a[p], w = 0.0;
-        if (v < 0.0) w = -(alpha * v) / at;
-        if (v > 0.0) w = -(beta * v) / at;
+        if (v < 0.0) w = v * f_neg;
+        if (v > 0.0) w = v * f_pos;
         Pci[pos] = cidx[j];
         Pv[pos] = w;
         ++pos;

@@ -108,6 +108,39 @@ __global__ void k_scan_apply(const int *__restrict__ in, int n, const long long 
 
 __global__ void k_set_last(int *out, int n, const long long *total) { out[n] = static_cast<int>(*total); }
 
+// Second pass of the two-kernel scan (at most kScan2Blocks tiles): each block
+// first sums the totals of the tiles before it (so no pass over the block
+// totals is needed), then scans its own tile; the last block writes out[n]
+// and *total.
+constexpr int kScan2Blocks = 4096;
+__global__ void k_scan_apply2(const int *__restrict__ in, int n, const long long *__restrict__ bsum,
+                              int *__restrict__ out, long long *__restrict__ total) {
+  long long pre = 0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += SCAN_T) pre += bsum[b];
+  long long boff;
+  block_excl_scan(pre, &boff);
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  long long v[SCAN_ITEMS], s = 0;
+#pragma unroll
+  for (int t = 0; t < SCAN_ITEMS; ++t) {
+    int64_t i = base + t;
+    v[t] = i < n ? in[i] : 0;
+    s += v[t];
+  }
+  long long tot;
+  long long ex = block_excl_scan(s, &tot) + boff;
+#pragma unroll
+  for (int t = 0; t < SCAN_ITEMS; ++t) {
+    int64_t i = base + t;
+    if (i < n) out[i] = static_cast<int>(ex);
+    ex += v[t];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    out[n] = static_cast<int>(boff + tot);
+    *total = boff + tot;
+  }
+}
+
 // Whole exclusive scan in one block (small n): tiles in order with a carry;
 // out[n] and *total receive the sum.
 __global__ void k_scan_single(const int *__restrict__ in, int n, int *__restrict__ out, long long *total) {
@@ -445,7 +478,9 @@ __global__ void k_interp_count(int n, const int *__restrict__ rp, const int *__r
 // Direct interpolation with every sum over the row in ascending column order:
 //   alpha = sum_{N_i} a^- / sum_{P_i} a^-,  beta = sum_{N_i} a^+ / sum_{P_i} a^+,
 //   at = a_ii + sum_{N_i} a^+ when P_i holds no positive entry, else a_ii,
-//   w_ij = -(alpha a_ij) / at for a_ij < 0, -(beta a_ij) / at for a_ij > 0.
+//   w_ij = a_ij (-(alpha / at)) for a_ij < 0, a_ij (-(beta / at)) for a_ij > 0
+// (the row factors formed once: two FP64 divisions per row, not one per
+// weight -- the kernel is bound by the FP64 pipe).
 // Systems (bs > 1, node-major unknowns): unknown-wise, row i sees only the
 // columns of its own component (j % bs == i % bs).
 __global__ void k_interp_fill(int n, int bs, const int *__restrict__ rp, const int *__restrict__ ci,
@@ -490,12 +525,15 @@ __global__ void k_interp_fill(int n, int bs, const int *__restrict__ rp, const i
   const double alpha = sp_neg != 0.0 ? __ddiv_rn(sn_neg, sp_neg) : 0.0;
   const double beta = sp_pos != 0.0 ? __ddiv_rn(sn_pos, sp_pos) : 0.0;
   const double at = sp_pos != 0.0 ? aii : __dadd_rn(aii, sn_pos);
+  // a factor is used only by entries of its sign in P_i, which exist iff its sum is nonzero
+  const double f_neg = sp_neg != 0.0 ? -__ddiv_rn(alpha, at) : 0.0;
+  const double f_pos = sp_pos != 0.0 ? -__ddiv_rn(beta, at) : 0.0;
   for (int p = b; p < e; ++p) {
     const int j = ci[p];
     if (j == i || !S[p] || !cf[j]) continue;
     const double v = a[p];
     const int sg = sign_class(v);
-    const double w = sg ? __ddiv_rn(-__dmul_rn(sg < 0 ? alpha : beta, v), at) : 0.0;
+    const double w = sg ? __dmul_rn(v, sg < 0 ? f_neg : f_pos) : 0.0;
     pci[pos] = cidx[j];
     pv[pos] = w;
     ++pos;
@@ -689,15 +727,17 @@ __global__ void __launch_bounds__(256) k_interp_fill_w(int n, int bs, const int 
   }
   np = __shfl_sync(0xffffffffu, np, 0);
   if (np == 0) return;
-  double alpha = 0.0, beta = 0.0, at = 0.0;
+  double f_neg = 0.0, f_pos = 0.0;
   if (lane == 0) {
-    alpha = sp_neg != 0.0 ? __ddiv_rn(sn_neg, sp_neg) : 0.0;
-    beta = sp_pos != 0.0 ? __ddiv_rn(sn_pos, sp_pos) : 0.0;
-    at = sp_pos != 0.0 ? aii : __dadd_rn(aii, sn_pos);
+    const double alpha = sp_neg != 0.0 ? __ddiv_rn(sn_neg, sp_neg) : 0.0;
+    const double beta = sp_pos != 0.0 ? __ddiv_rn(sn_pos, sp_pos) : 0.0;
+    const double at = sp_pos != 0.0 ? aii : __dadd_rn(aii, sn_pos);
+    // a factor is used only by entries of its sign in P_i, which exist iff its sum is nonzero
+    f_neg = sp_neg != 0.0 ? -__ddiv_rn(alpha, at) : 0.0;
+    f_pos = sp_pos != 0.0 ? -__ddiv_rn(beta, at) : 0.0;
   }
-  alpha = __shfl_sync(0xffffffffu, alpha, 0);
-  beta = __shfl_sync(0xffffffffu, beta, 0);
-  at = __shfl_sync(0xffffffffu, at, 0);
+  f_neg = __shfl_sync(0xffffffffu, f_neg, 0);
+  f_pos = __shfl_sync(0xffffffffu, f_pos, 0);
   for (int c0 = b; c0 < e; c0 += 32) {
     const int p = c0 + lane;
     bool sel = false;
@@ -710,7 +750,7 @@ __global__ void __launch_bounds__(256) k_interp_fill_w(int n, int bs, const int 
     if (sel) {
       const double v = a[p];
       const int sg = sign_class(v);
-      const double wv = sg ? __ddiv_rn(-__dmul_rn(sg < 0 ? alpha : beta, v), at) : 0.0;
+      const double wv = sg ? __dmul_rn(v, sg < 0 ? f_neg : f_pos) : 0.0;
       const int q = pos + __popc(bal & ((1u << lane) - 1u));
       pci[q] = cidx[j];
       pv[q] = wv;
@@ -879,8 +919,14 @@ void scan_counts_async(Mem &m, const int *in, int *out, int n, long long *total_
   cudaStream_t s = m.stream;
   const int nb = std::max(1, ceil_div(n, SCAN_TILE));
   ProfScope ps(s, AMG_K_SETUP_OTHER, 8.0 * n + 8.0 * nb);
-  if (n <= 16 * SCAN_TILE) {
+  if (n <= SCAN_TILE) {
     k_scan_single<<<1, SCAN_T, 0, s>>>(in, n, out, total_dev);
+    AMG_CHECK_LAUNCH();
+  } else if (nb <= kScan2Blocks) {
+    Buf<long long> bsum(m, (size_t)nb);  // released in stream order
+    k_scan_reduce<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p);
+    AMG_CHECK_LAUNCH();
+    k_scan_apply2<<<nb, SCAN_T, 0, s>>>(in, n, bsum.p, out, total_dev);
     AMG_CHECK_LAUNCH();
   } else {
     Buf<long long> bsum(m, (size_t)nb + 1);  // released in stream order

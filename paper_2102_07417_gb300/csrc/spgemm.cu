@@ -80,31 +80,51 @@ __device__ __forceinline__ int next_pow2(int v) {
 }
 
 // ------------------------------------------------------------- binning ----
-// ub and tier per row; per-tile tier counts; largest ub of the global tier.
-__global__ void __launch_bounds__(TPB) k_bin_rows(int m, const int *__restrict__ xrp, const int *__restrict__ xci,
-                                                  const int *__restrict__ yrp, int *__restrict__ ub_out,
+// ub_i = sum over the entries p of X row i of nnz(Y_{k_p}), G lanes per row
+// (G = 1 for short X rows, up to 32 for long ones: the coarse levels' rows are
+// long and few, and a thread walking a whole row left most SMs idle).
+template <int G>
+__global__ void __launch_bounds__(TPB) k_row_ub(int m, const int *__restrict__ xrp, const int *__restrict__ xci,
+                                                const int *__restrict__ yrp, int *__restrict__ ub_out, int *flags) {
+  constexpr int RPW = 32 / G;  // rows per warp step
+  const int lane = threadIdx.x & 31, sub = lane & (G - 1), grp = lane / G;
+  const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5, nw = (gridDim.x * TPB) >> 5;
+  for (int base = gw * RPW; base < m; base += nw * RPW) {  // the whole warp iterates together
+    const int i = base + grp;
+    int64_t ub = 0;
+    if (i < m)
+      for (int p = xrp[i] + sub; p < xrp[i + 1]; p += G) {
+        const int k = xci[p];
+        ub += yrp[k + 1] - yrp[k];
+      }
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) ub += __shfl_xor_sync(FULL, ub, o);
+    if (i < m && sub == 0) {
+      if (ub > (1 << 30)) {
+        flags[3] = 1;
+        ub = 1 << 30;
+      }
+      ub_out[i] = (int)ub;
+    }
+  }
+}
+
+// Tier of each row (from its ub and X row length); per-tile tier counts;
+// largest ub of the global tier.
+__global__ void __launch_bounds__(TPB) k_bin_rows(int m, const int *__restrict__ xrp, const int *__restrict__ ub_in,
                                                   int8_t *__restrict__ tier, int *__restrict__ tile_cnt,
-                                                  int *__restrict__ max_ub, int *flags) {
+                                                  int *__restrict__ max_ub) {
   __shared__ int cnt[NTIER];
   if (threadIdx.x < NTIER) cnt[threadIdx.x] = 0;
   __syncthreads();
   for (int t = threadIdx.x; t < TILE; t += TPB) {
     const int i = blockIdx.x * TILE + t;
     if (i >= m) break;
-    int64_t ub = 0;
-    for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
-      const int k = xci[p];
-      ub += yrp[k + 1] - yrp[k];
-    }
-    if (ub > (1 << 30)) {
-      flags[3] = 1;
-      ub = 1 << 30;
-    }
+    const int ub = ub_in[i];
     const int c = tier_of(ub, xrp[i + 1] - xrp[i]);
-    ub_out[i] = (int)ub;
     tier[i] = (int8_t)c;
     atomicAdd(&cnt[c], 1);
-    if (c == T_GLOBAL) atomicMax(max_ub, (int)ub);
+    if (c == T_GLOBAL) atomicMax(max_ub, ub);
   }
   __syncthreads();
   if (threadIdx.x < NTIER) tile_cnt[blockIdx.x * NTIER + threadIdx.x] = cnt[threadIdx.x];
@@ -600,7 +620,14 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
   const double xy_bytes = 4.0 * (rows + 1) + 12.0 * X.nnz + 4.0 * (Y.n + 1) + 12.0 * Y.nnz;
   {
     ProfScope ps(s, AMG_K_SPGEMM, 4.0 * (rows + 1) + 4.0 * X.nnz + 4.0 * (Y.n + 1) + 9.0 * rows);
-    k_bin_rows<<<ntiles, TPB, 0, s>>>(rows, X.rp, X.ci, Y.rp, ub.p, tier.p, tile_cnt.p, meta.p + NTIER, flags);
+    const double xavg = rows ? (double)X.nnz / rows : 0.0;
+    const int G = xavg <= 8.0 ? 1 : xavg <= 24.0 ? 8 : 32;
+    const int grid = std::max(1, std::min(ceil_div((int64_t)rows * G, TPB), kNumSMs * 32));
+    if (G == 1) k_row_ub<1><<<grid, TPB, 0, s>>>(rows, X.rp, X.ci, Y.rp, ub.p, flags);
+    else if (G == 8) k_row_ub<8><<<grid, TPB, 0, s>>>(rows, X.rp, X.ci, Y.rp, ub.p, flags);
+    else k_row_ub<32><<<grid, TPB, 0, s>>>(rows, X.rp, X.ci, Y.rp, ub.p, flags);
+    AMG_CHECK_LAUNCH();
+    k_bin_rows<<<ntiles, TPB, 0, s>>>(rows, X.rp, ub.p, tier.p, tile_cnt.p, meta.p + NTIER);
     AMG_CHECK_LAUNCH();
     k_tier_offsets<<<1, TPB, 0, s>>>(ntiles, tile_cnt.p, tile_off.p, meta.p);
     AMG_CHECK_LAUNCH();
