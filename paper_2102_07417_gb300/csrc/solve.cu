@@ -852,8 +852,12 @@ RowMap choose_map(int64_t nnz, int n, bool fp64) {
   } else {
     while (cap < 32 && cap < avg) cap <<= 1;
   }
+  // lanes to put to work: 2^19 from 2^15 rows up, 2^17 below (the 128^3
+  // hierarchy's level 3, 24K rows of 60 entries, smoothed in 27 us (FP64) with
+  // 8 lanes per row against 43 us with 32; level 4, 3.6K rows, keeps 32)
+  const int64_t lanes = n >= kSellMinRows ? (1 << 19) : (1 << 17);
   int g = 1;
-  while (g < cap && (int64_t)n * g < (1 << 19)) g <<= 1;
+  while (g < cap && (int64_t)n * g < lanes) g <<= 1;
   m.g = g;
   m.tr = false;
   return m;
