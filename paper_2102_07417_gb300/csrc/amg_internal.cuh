@@ -164,6 +164,20 @@ struct Profile {
 };
 extern Profile g_prof;
 
+// True when launches of kernel class `kind` would record events: graphs are
+// captured only when none of their kernels would (events inside a captured
+// graph would not time its replays).
+inline bool prof_records(int kind) {
+  return g_prof.on && (g_prof.only_kind < 0 || g_prof.only_kind == kind);
+}
+// Whether any solve-phase kernel class (AMG_K_SPMV_DOT .. AMG_K_SOLVE_OTHER)
+// would record events.
+inline bool prof_records_solve() {
+  for (int k = AMG_K_SPMV_DOT; k <= AMG_K_SOLVE_OTHER; ++k)
+    if (prof_records(k)) return true;
+  return false;
+}
+
 // Brackets one kernel launch with two events when profiling is on.
 struct ProfScope {
   size_t slot = (size_t)-1;

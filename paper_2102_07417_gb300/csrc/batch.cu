@@ -1421,7 +1421,7 @@ struct SlotsImpl : SlotsBase {
     }
   }
   void run_step() {
-    if (g_prof.on || mem.stream == nullptr) {  // the legacy default stream cannot be captured
+    if (prof_records_solve() || mem.stream == nullptr) {  // the legacy default stream cannot be captured
       issue_step();
       return;
     }
