@@ -1009,7 +1009,13 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     // the warp-per-row kernels (the interpolation's serial FP64 sums only on
     // the smallest levels, where FP64 issue slots are not the limit).
     const bool wide = (double)A.nnz >= 12.0 * n && n < (1 << 18);
-    const bool wide_interp = wide && n < (1 << 15);
+    // The interpolation's FP64 sums are serial per row, and FP64 instructions
+    // issue per warp: a thread per row keeps them lane-dense (the 128^3
+    // level 3, 24K rows of 60 entries: 113 us against 201 us warp per row,
+    // where one lane in 32 issues them); below 8192 rows there are too few rows
+    // for that and the warp per row wins (levels 4-6: 40, 22, 14 us against
+    // 110, 96, 49 us).
+    const bool wide_interp = wide && n < 8192;
     const int gw = ceil_div((int64_t)n * 32, TPB);
     Buf<uint8_t> S, ST;
     Buf<int> cidx;

@@ -673,29 +673,19 @@ __global__ void k_copy(int n, const T *__restrict__ a, T *__restrict__ b) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = a[i];
 }
 
-// wd = omega / a_ii: 8 lanes per row look for the diagonal entry (coalesced
-// reads of the row; a row without one keeps a_ii = 1, as the set-up rejects
-// such matrices before this point).
-__global__ void __launch_bounds__(TPB) k_make_wd(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                                 const double *__restrict__ a, double omega, double *__restrict__ wd,
-                                                 float *__restrict__ wd32) {
-  constexpr int G = 8;
-  const int lane = threadIdx.x & 31, sub = lane & (G - 1), grp = lane / G;
-  const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5, nw = (gridDim.x * TPB) >> 5;
-  for (int base = gw * (32 / G); base < n; base += nw * (32 / G)) {  // whole warps iterate together
-    const int i = base + grp;
-    int pd = -1;
-    if (i < n)
-      for (int p = rp[i] + sub; p < rp[i + 1]; p += G)
-        if (ci[p] == i) pd = p;
-#pragma unroll
-    for (int o = G / 2; o >= 1; o >>= 1) pd = max(pd, __shfl_xor_sync(FULL, pd, o));
-    if (i < n && sub == 0) {
-      const double d = pd >= 0 ? a[pd] : 1.0;
-      const double w = omega / d;
-      wd[i] = w;
-      if (wd32) wd32[i] = static_cast<float>(w);
-    }
+// wd = omega / a_ii, a thread per row.  (Eight lanes per row with the
+// division in one of them was 6.5x slower on the 128^3 level 0: FP64
+// instructions issue per warp, so FP64 work must keep its lanes dense.)
+__global__ void k_make_wd(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                          const double *__restrict__ a, double omega, double *__restrict__ wd,
+                          float *__restrict__ wd32) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double d = 1.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] == i) d = a[p];
+    const double w = omega / d;
+    wd[i] = w;
+    if (wd32) wd32[i] = static_cast<float>(w);
   }
 }
 
@@ -1339,7 +1329,7 @@ void prepare_solve(amg_hierarchy *h) {
     if (!fp64) L.wd32 = m.get_n<float>(n);
     {
       ProfScope ps(s, AMG_K_SETUP_OTHER, 4.0 * (n + 1) + 12.0 * L.A.nnz + 12.0 * n);
-      k_make_wd<<<grid_for((int64_t)n * 8), TPB, 0, s>>>(n, L.A.rp, L.A.ci, L.A.v, h->prm.omega, L.wd, L.wd32);
+      k_make_wd<<<grid_for(n), TPB, 0, s>>>(n, L.A.rp, L.A.ci, L.A.v, h->prm.omega, L.wd, L.wd32);
       AMG_CHECK_LAUNCH();
     }
     if (!fp64) {  // CSR FP32 copies (the CSR kernels of small levels and the export keep them)
