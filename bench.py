@@ -372,7 +372,14 @@ def run_gpu(args, rank, world, dist):
             "launches_timed": d["launches"], "avg_launch_us": d["ms"] * 1e3 / max(d["launches"], 1),
             "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
             "traffic": traffic_for(args.workload, dom, dom_lv, batch)}
-    if batch and dom == "spmv_dot" and d["ms"] > 0:
+    double_float = batch and prec != "fp64" and p.b.shape[1] in (8, 16) and dom == "spmv_dot" and d["ms"] > 0
+    if double_float:
+        # FP32 modes compute q = A p of 8- or 16-column batches in double-float (FP32 pairs, on the FP32
+        # pipe), so the FP64 rate is not its ceiling: the HBM roofline above stands, with the product
+        # rate alongside
+        roof["arith"] = "double-float (FP32 pairs) on the FP32 pipe"
+        roof["tflops_fp64_equivalent"] = 2.0 * p.A.nnz * p.b.shape[1] * d["launches"] / (d["ms"] * 1e-3) / 1e12
+    elif batch and dom == "spmv_dot" and d["ms"] > 0:
         # k columns share each matrix entry: the FP64 SpMM is bound by FP64 arithmetic, not HBM
         # (2 nnz k flops per launch; peak: GB300's nominal FP64 rate, 152 SMs x ~2 DFMA/clk x 2.07 GHz)
         flops = 2.0 * p.A.nnz * p.b.shape[1] * d["launches"]

@@ -1014,7 +1014,8 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     // level 3, 24K rows of 60 entries: 113 us against 201 us warp per row,
     // where one lane in 32 issues them); below 8192 rows there are too few rows
     // for that and the warp per row wins (levels 4-6: 40, 22, 14 us against
-    // 110, 96, 49 us).
+    // 110, 96, 49 us).  The strength kernel (FP64 comparisons) follows the same
+    // split; the integer-only kernels (PMIS, interpolation counts) keep `wide`.
     const bool wide_interp = wide && n < 8192;
     const int gw = ceil_div((int64_t)n * 32, TPB);
     Buf<uint8_t> S, ST;
@@ -1033,7 +1034,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       Buf<uint8_t> SN;
       if (bs == 1) {
         ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n + 1) + 13.0 * A.nnz);
-        if (wide) k_strength_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
+        if (wide_interp) k_strength_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
         else k_strength<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
         AMG_CHECK_LAUNCH();
       } else {
