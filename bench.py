@@ -444,6 +444,7 @@ def run_gpu(args, rank, world, dist):
     mixed = None
     if prec == "fp64" and not batch and not args.no_mixed:
         mixed = run_mixed(args, p, A_dev, b_dev, stream, dev, barrier)
+        mixed["bf16_pr_ablation"] = run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, amg.PREC_FP32_BF16PR)
 
     serving = None
     if world == 1 and not args.no_serve:
@@ -480,16 +481,19 @@ def run_gpu(args, rank, world, dist):
     print(json.dumps(out), flush=True)
 
 
-def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier):
+def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, prec_id=None):
     """The same workload with the hierarchy stored and the V-cycle run in FP32 under the FP64
-    flexible PCG (the mixed-precision form): set-up + solve per step timed with CUDA events,
-    its V-cycle bandwidth from one profiled step, and the error against x*."""
+    flexible PCG (the mixed-precision form; with prec_id = PREC_FP32_BF16PR, P and R stored in
+    BF16): set-up + solve per step timed with CUDA events, its V-cycle bandwidth from one
+    profiled step, and the error against x*."""
     import numpy as np
     import torch
 
     from paper_2102_07417_gb300 import amg
 
-    params = amg.default_params(precision=amg.PREC_FP32, **getattr(p, "params", {}))
+    if prec_id is None:
+        prec_id = amg.PREC_FP32
+    params = amg.default_params(precision=prec_id, **getattr(p, "params", {}))
     x_dev = torch.zeros_like(b_dev)
     rec = {}
 
@@ -522,7 +526,9 @@ def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier):
     x_err = None
     if p.xstar is not None:
         x_err = float(np.linalg.norm(x_dev.cpu().numpy() - p.xstar) / np.linalg.norm(p.xstar))
-    return {"precision": "fp32 hierarchy + V-cycle, fp64 flexible PCG", "t_setup_ms": tp, "t_solve_ms": ts,
+    name = ("fp32 hierarchy + V-cycle, fp64 flexible PCG" if prec_id == amg.PREC_FP32 else
+            "fp32 hierarchy + V-cycle with P and R in bf16, fp64 flexible PCG")
+    return {"precision": name, "t_setup_ms": tp, "t_solve_ms": ts,
             "t_total_ms": tp + ts, "iters": rec["iters"], "status": rec["status"], "x_rel_err": x_err,
             "steps": len(times),
             "vcycle_hbm": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s", "peak": peak,

@@ -70,7 +70,8 @@ typedef struct {
 } amg_allocator;
 
 /* Square sparse matrix in CSR (Sec. 3.2 CSRMAT).  rowptr[n+1] starting at
- * 0; colidx[nnz] strictly ascending within each row and in [0, n); val[nnz].
+ * 0; colidx[nnz] strictly ascending within each row and in [0, n); val[nnz],
+ * every value finite (a NaN or an infinity gives AMG_ERR_INVALID_ARG).
  * The pattern must be structurally symmetric and every row must hold a
  * positive diagonal entry.  on_device = 1: the three arrays are device
  * pointers; 0: host pointers. */

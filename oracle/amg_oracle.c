@@ -107,6 +107,7 @@ int or_check_csr(int n, const int *rp, const int *ci, const double *a) {
     for (int p = rp[i]; p < rp[i + 1]; ++p) {
       if (ci[p] < 0 || ci[p] >= n) return OR_ERR_ARG;
       if (p > rp[i] && ci[p] <= ci[p - 1]) return OR_ERR_ARG;
+      if (!isfinite(a[p])) return OR_ERR_ARG; /* values must be finite */
       if (ci[p] == i) {
         has_diag = 1;
         if (!(a[p] > 0.0)) return OR_ERR_NOT_SPD;

@@ -190,6 +190,10 @@ __global__ void k_validate(int n, int64_t nnz, const int *__restrict__ rp, const
       flags[0] = 1;
       return;
     }
+    if (((unsigned long long)__double_as_longlong(a[p]) & 0x7ff0000000000000ULL) == 0x7ff0000000000000ULL) {
+      flags[0] = 1;  // NaN or infinity
+      return;
+    }
     if (j == i) {
       diag = true;
       if (!(a[p] > 0.0)) flags[1] = 1;
@@ -200,25 +204,38 @@ __global__ void k_validate(int n, int64_t nnz, const int *__restrict__ rp, const
 
 // ----------------------------------------------------------- strength --
 // S[p] = 1 iff ci[p] != i, m_i = max_{k != i} (-a_ik) > 0 and -a[p] >= theta * m_i.
+// Strength of connection, S[p] = 1 iff j = ci[p] != i and -a_ij >= thr_i =
+// theta m_i, m_i = max_{k != i} -a_ik, only when m_i > 0.  The decisions are
+// taken on bit patterns with integer instructions (FP64 comparisons kept
+// GB300's FP64 pipe busy; FP64 instructions issue at a small fraction of the
+// integer rate), exactly equivalent for finite values (the set-up rejects
+// others):
+//   m_i > 0 iff some off-diagonal a_ik is negative (nonzero), and then m_i is
+//   the largest magnitude among them -- the largest magnitude bit pattern, as
+//   non-negative doubles order as their patterns;
+//   thr_i = fl(theta m_i) is formed in FP64 as before; for thr_i > 0,
+//   -a_ij >= thr_i iff a_ij is negative and |a_ij|'s pattern >= thr_i's; for
+//   thr_i = +0 (an underflow), iff a_ij <= 0.
+constexpr unsigned long long kMagMask = 0x7fffffffffffffffULL;
+
+__device__ __forceinline__ bool strong_entry(long long bits, unsigned long long tbits) {
+  if (tbits == 0ULL) return bits < 0 || bits == 0;  // a_ij <= 0
+  return bits < 0 && ((unsigned long long)bits & kMagMask) >= tbits;
+}
+
 __global__ void k_strength(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                            const double *__restrict__ a, double theta, uint8_t *__restrict__ S) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int b = rp[i], e = rp[i + 1];
-  double m = 0.0;
-  bool have = false;
+  unsigned long long mk = 0ULL;  // largest |a_ik| over negative off-diagonals (0: none)
   for (int p = b; p < e; ++p) {
-    if (ci[p] == i) continue;
-    const double t = -a[p];
-    if (!have || t > m) m = t;
-    have = true;
+    const long long bits = __double_as_longlong(a[p]);
+    if (bits < 0 && ci[p] != i) mk = max(mk, (unsigned long long)bits & kMagMask);
   }
-  const double thr = __dmul_rn(theta, m);
-  for (int p = b; p < e; ++p) {
-    uint8_t s = 0;
-    if (have && m > 0.0 && ci[p] != i && -a[p] >= thr) s = 1;
-    S[p] = s;
-  }
+  const unsigned long long tbits = (unsigned long long)__double_as_longlong(__dmul_rn(theta, __longlong_as_double((long long)mk)));
+  for (int p = b; p < e; ++p)
+    S[p] = (mk != 0ULL && ci[p] != i && strong_entry(__double_as_longlong(a[p]), tbits)) ? 1 : 0;
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014) evaluated at counter c: the c-th output
@@ -555,23 +572,16 @@ __global__ void k_strength_w(int n, const int *__restrict__ rp, const int *__res
                              const double *__restrict__ a, double theta, uint8_t *__restrict__ S) {
   WARP_ROW_BEGIN
   const int b = rp[i], e = rp[i + 1];
-  double m = 0.0;
-  bool have = false;
+  unsigned long long mk = 0ULL;  // as in k_strength
   for (int p = b + lane; p < e; p += 32) {
-    if (ci[p] == i) continue;
-    const double t = -a[p];
-    if (!have || t > m) m = t;
-    have = true;
+    const long long bits = __double_as_longlong(a[p]);
+    if (bits < 0 && ci[p] != i) mk = max(mk, (unsigned long long)bits & kMagMask);
   }
 #pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const double om = __shfl_xor_sync(0xffffffffu, m, o);
-    const bool oh = __shfl_xor_sync(0xffffffffu, (int)have, o) != 0;
-    if (oh && (!have || om > m)) m = om;
-    have = have || oh;
-  }
-  const double thr = __dmul_rn(theta, m);
-  for (int p = b + lane; p < e; p += 32) S[p] = (have && m > 0.0 && ci[p] != i && -a[p] >= thr) ? 1 : 0;
+  for (int o = 16; o; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+  const unsigned long long tbits = (unsigned long long)__double_as_longlong(__dmul_rn(theta, __longlong_as_double((long long)mk)));
+  for (int p = b + lane; p < e; p += 32)
+    S[p] = (mk != 0ULL && ci[p] != i && strong_entry(__double_as_longlong(a[p]), tbits)) ? 1 : 0;
 }
 
 __global__ void k_pmis_init_w(int n, const int *__restrict__ rp, const int *__restrict__ ci,
@@ -996,7 +1006,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     AMG_CHECK_LAUNCH();
   }
   sync_flags();
-  if (fl.h[0]) fail(AMG_ERR_INVALID_ARG, "malformed CSR (row pointers, column range or unsorted columns)");
+  if (fl.h[0]) fail(AMG_ERR_INVALID_ARG, "malformed CSR (row pointers, column range, unsorted columns or a non-finite value)");
   if (fl.h[1]) fail(AMG_ERR_NOT_SPD, "a diagonal entry is missing or not positive");
 
   int k = 0;
@@ -1014,8 +1024,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     // level 3, 24K rows of 60 entries: 113 us against 201 us warp per row,
     // where one lane in 32 issues them); below 8192 rows there are too few rows
     // for that and the warp per row wins (levels 4-6: 40, 22, 14 us against
-    // 110, 96, 49 us).  The strength kernel (FP64 comparisons) follows the same
-    // split; the integer-only kernels (PMIS, interpolation counts) keep `wide`.
+    // 110, 96, 49 us).  The other set-up kernels (integer work) keep `wide`.
     const bool wide_interp = wide && n < 8192;
     const int gw = ceil_div((int64_t)n * 32, TPB);
     Buf<uint8_t> S, ST;
@@ -1034,7 +1043,9 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       Buf<uint8_t> SN;
       if (bs == 1) {
         ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n + 1) + 13.0 * A.nnz);
-        if (wide_interp) k_strength_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
+        // integer work only: the warp per row reads long rows coalesced at any size
+        // (128^3 level 2: 44 us warp per row; level 1, thread per row: 148 us)
+        if ((double)A.nnz >= 12.0 * n) k_strength_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
         else k_strength<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
         AMG_CHECK_LAUNCH();
       } else {

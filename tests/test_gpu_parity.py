@@ -328,6 +328,8 @@ def test_isolated_points_and_empty_interpolation_rows():
     ("col_range", amg.AMG_ERR_INVALID_ARG),
     ("nonsym_pattern", amg.AMG_ERR_INVALID_ARG),
     ("indefinite", amg.AMG_ERR_NOT_SPD),
+    ("nan_value", amg.AMG_ERR_INVALID_ARG),
+    ("inf_value", amg.AMG_ERR_INVALID_ARG),
 ])
 def test_setup_rejects_bad_input(mutate, code):
     A = pr.poisson2d(10)
@@ -346,6 +348,10 @@ def test_setup_rejects_bad_input(mutate, code):
     elif mutate == "indefinite":
         B = pr.dense_to_csr(np.array([[1.0, 2.0], [2.0, 1.0]]))
         rp, ci, v = B.rowptr, B.col, B.val
+    elif mutate == "nan_value":
+        v[3] = np.nan
+    elif mutate == "inf_value":
+        v[3] = -np.inf
     bad = pr.CSR(len(rp) - 1, rp, ci, v)
     with pytest.raises(amg.AmgError) as e:
         amg.Hierarchy(bad, max_levels=1 if mutate == "indefinite" else 25)

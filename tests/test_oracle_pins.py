@@ -472,6 +472,10 @@ def test_check_csr_rejects_malformed():
     assert O.check_csr(bad) == O.ERR_ARG
     neg = pr.CSR(A.n, A.rowptr.copy(), A.col.copy(), -A.val)
     assert O.check_csr(neg) == O.ERR_NOT_SPD
+    for bad_value in (np.nan, np.inf, -np.inf):  # values must be finite
+        v = A.val.copy()
+        v[2] = bad_value
+        assert O.check_csr(pr.CSR(A.n, A.rowptr.copy(), A.col.copy(), v)) == O.ERR_ARG
 
 
 # ------------------------------------------------------------ set-up ----
