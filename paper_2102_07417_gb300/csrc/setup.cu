@@ -584,6 +584,28 @@ __global__ void k_strength_w(int n, const int *__restrict__ rp, const int *__res
     S[p] = (mk != 0ULL && ci[p] != i && strong_entry(__double_as_longlong(a[p]), tbits)) ? 1 : 0;
 }
 
+// The same with G lanes per row (rows of moderate length).
+template <int G>
+__global__ void __launch_bounds__(256) k_strength_g(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                    const double *__restrict__ a, double theta,
+                                                    uint8_t *__restrict__ S) {
+  const int lane = threadIdx.x & 31, sub = lane & (G - 1);
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G);  // rows in whole G-lane groups
+  const bool live = i < n;
+  const int b = live ? rp[i] : 0, e = live ? rp[i + 1] : 0;
+  unsigned long long mk = 0ULL;
+  for (int p = b + sub; p < e; p += G) {
+    const long long bits = __double_as_longlong(a[p]);
+    if (bits < 0 && ci[p] != i) mk = max(mk, (unsigned long long)bits & kMagMask);
+  }
+#pragma unroll
+  for (int o = G / 2; o >= 1; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+  if (!live) return;
+  const unsigned long long tbits = (unsigned long long)__double_as_longlong(__dmul_rn(theta, __longlong_as_double((long long)mk)));
+  for (int p = b + sub; p < e; p += G)
+    S[p] = (mk != 0ULL && ci[p] != i && strong_entry(__double_as_longlong(a[p]), tbits)) ? 1 : 0;
+}
+
 __global__ void k_pmis_init_w(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                               const uint8_t *__restrict__ S, uint8_t *__restrict__ ST, double *__restrict__ lam,
                               int8_t *__restrict__ st, uint64_t seed, int level, int *flags) {
@@ -1043,9 +1065,14 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       Buf<uint8_t> SN;
       if (bs == 1) {
         ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n + 1) + 13.0 * A.nnz);
-        // integer work only: the warp per row reads long rows coalesced at any size
-        // (128^3 level 2: 44 us warp per row; level 1, thread per row: 148 us)
-        if ((double)A.nnz >= 12.0 * n) k_strength_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
+        // integer work only: rows of 12 to 32 entries with 8 lanes per row, longer
+        // ones with a warp (128^3 level 1, 18 entries: 148 us with a thread per row,
+        // 144 us with a warp; level 2, 46 entries: 44 us with a warp)
+        const double avg = n ? (double)A.nnz / n : 0.0;
+        if (avg >= 12.0 && avg <= 32.0)
+          k_strength_g<8><<<ceil_div((int64_t)n * 8, TPB), TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
+        else if (avg > 32.0)
+          k_strength_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
         else k_strength<<<g, TPB, 0, s>>>(n, A.rp, A.ci, A.v, prm.theta, S.p);
         AMG_CHECK_LAUNCH();
       } else {
