@@ -851,13 +851,17 @@ __global__ void k_transpose_scatter(int n, const int *__restrict__ rp, const int
 
 // Rows of (src_ci, src_v) sorted by column into (dst_ci, dst_v); a warp per
 // row, rank of each entry = number of smaller keys in its row (keys distinct).
+// Sorts each row of the scattered transpose by column: an entry's position is
+// its rank among the row's (distinct) columns.  G lanes per row (8 for short
+// rows, so that a warp holds several rows; 32 for long ones).
+template <int G>
 __global__ void k_sort_rows(int m, const int *__restrict__ rp, const int *__restrict__ src_ci,
                             const double *__restrict__ src_v, int *__restrict__ dst_ci, double *__restrict__ dst_v) {
-  const int lane = threadIdx.x & 31;
-  const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int sub = threadIdx.x & (G - 1);
+  const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G);
   if (row >= m) return;
   const int b = rp[row], e = rp[row + 1];
-  for (int p = b + lane; p < e; p += 32) {
+  for (int p = b + sub; p < e; p += G) {
     const int key = src_ci[p];
     int rank = 0;
     for (int q = b; q < e; ++q) rank += src_ci[q] < key;
@@ -970,7 +974,10 @@ void transpose(Mem &m, const DCsr &P, int ncols, DCsr &R) {
   }
   {
     ProfScope ps(s, AMG_K_TRANSPOSE, 4.0 * (ncols + 1) + 24.0 * P.nnz);
-    k_sort_rows<<<ceil_div((int64_t)ncols * 32, TPB), TPB, 0, s>>>(ncols, R.rp, tci.p, tv.p, R.ci, R.v);
+    if (P.nnz <= 12LL * ncols)
+      k_sort_rows<8><<<ceil_div((int64_t)ncols * 8, TPB), TPB, 0, s>>>(ncols, R.rp, tci.p, tv.p, R.ci, R.v);
+    else
+      k_sort_rows<32><<<ceil_div((int64_t)ncols * 32, TPB), TPB, 0, s>>>(ncols, R.rp, tci.p, tv.p, R.ci, R.v);
     AMG_CHECK_LAUNCH();
   }
 }
