@@ -257,17 +257,26 @@ double or_pmis_random(uint64_t seed, int level, int i) {
 /*     an undecided i becomes C if it beats every undecided j in           */
 /*     S_i u S_i^T (beats: larger lambda, ties broken by larger index);    */
 /*     then every undecided i with S_i meeting the new C points becomes F. */
+/* or_pmis_rounds takes the measures as input and stops after max_rounds  */
+/* rounds (max_rounds < 0: until no point is undecided); state[i] = 1 C,  */
+/* 0 F, -1 still undecided; *rounds_out (may be NULL) = rounds run.       */
+/* or_pmis draws the measures from the counter-based stream and writes    */
 /* cf[i] = 1 for C, 0 for F.                                              */
 /* ------------------------------------------------------------------ */
 enum { ST_U = 0, ST_C = 1, ST_F = 2, ST_NEWC = 3 };
 
-int or_pmis(int n, const int *rp, const int *ci, const unsigned char *S, uint64_t seed, int level,
-            signed char *cf) {
+/* the state a competitor j had at the start of the round: undecided */
+static int competes(const unsigned char *st, int j) { return st[j] == ST_U || st[j] == ST_NEWC; }
+
+/* i beats j: larger measure, equal measures broken by the larger index */
+static int beats(const double *lam, int i, int j) { return lam[i] > lam[j] || (lam[i] == lam[j] && i > j); }
+
+int or_pmis_rounds(int n, const int *rp, const int *ci, const unsigned char *S, const double *lam, int max_rounds,
+                   signed char *state, int *rounds_out) {
   int *tcnt = (int *)calloc((size_t)n + 1, sizeof(int));
-  double *lam = (double *)malloc((size_t)n * sizeof(double));
-  unsigned char *st = (unsigned char *)malloc((size_t)n);
-  if (!tcnt || !lam || !st) {
-    free(tcnt); free(lam); free(st);
+  unsigned char *st = (unsigned char *)malloc((size_t)n + 1);
+  if (!tcnt || !st) {
+    free(tcnt); free(st);
     return OR_ERR_MEM;
   }
   /* S^T as CSR: for each strong entry (j -> c) of row j, row c of S^T gets j */
@@ -277,9 +286,9 @@ int or_pmis(int n, const int *rp, const int *ci, const unsigned char *S, uint64_
   for (int i = 0; i < n; ++i) tcnt[i + 1] += tcnt[i];
   int ntr = tcnt[n];
   int *tcol = (int *)malloc(((size_t)ntr + 1) * sizeof(int));
-  int *fill = (int *)malloc((size_t)n * sizeof(int));
+  int *fill = (int *)malloc(((size_t)n + 1) * sizeof(int));
   if (!tcol || !fill) {
-    free(tcnt); free(lam); free(st); free(tcol); free(fill);
+    free(tcnt); free(st); free(tcol); free(fill);
     return OR_ERR_MEM;
   }
   for (int i = 0; i < n; ++i) fill[i] = tcnt[i];
@@ -287,32 +296,24 @@ int or_pmis(int n, const int *rp, const int *ci, const unsigned char *S, uint64_
     for (int p = rp[j]; p < rp[j + 1]; ++p)
       if (S[p]) tcol[fill[ci[p]]++] = j;
 
-  for (int i = 0; i < n; ++i) {
-    int deg = tcnt[i + 1] - tcnt[i];
-    lam[i] = (double)deg + or_pmis_random(seed, level, i);
-    st[i] = (deg == 0) ? ST_F : ST_U;
-  }
-  for (;;) {
+  for (int i = 0; i < n; ++i) st[i] = (lam[i] < 1.0) ? ST_F : ST_U;
+  int rounds = 0;
+  while (max_rounds < 0 || rounds < max_rounds) {
     int undecided = 0;
     for (int i = 0; i < n; ++i) undecided += (st[i] == ST_U);
     if (!undecided) break;
+    ++rounds;
     /* selection: local maxima of lambda among undecided strong neighbours */
     for (int i = 0; i < n; ++i) {
       if (st[i] != ST_U) continue;
       int is_max = 1;
-      for (int p = rp[i]; p < rp[i + 1] && is_max; ++p) {
-        int j = ci[p];
-        if (!S[p] || !(st[j] == ST_U || st[j] == ST_NEWC)) continue;
-        if (lam[j] > lam[i] || (lam[j] == lam[i] && j > i)) is_max = 0;
-      }
-      for (int q = tcnt[i]; q < tcnt[i + 1] && is_max; ++q) {
-        int j = tcol[q];
-        if (!(st[j] == ST_U || st[j] == ST_NEWC)) continue;
-        if (lam[j] > lam[i] || (lam[j] == lam[i] && j > i)) is_max = 0;
-      }
+      for (int p = rp[i]; p < rp[i + 1] && is_max; ++p) /* j in S_i */
+        if (S[p] && competes(st, ci[p]) && !beats(lam, i, ci[p])) is_max = 0;
+      for (int q = tcnt[i]; q < tcnt[i + 1] && is_max; ++q) /* j in S_i^T */
+        if (competes(st, tcol[q]) && !beats(lam, i, tcol[q])) is_max = 0;
       if (is_max) st[i] = ST_NEWC;
     }
-    /* undecided points that depend strongly on a new C point become F */
+    /* undecided points that depend strongly on a new C point (S_i meets it) become F */
     for (int i = 0; i < n; ++i) {
       if (st[i] != ST_U) continue;
       for (int p = rp[i]; p < rp[i + 1]; ++p)
@@ -324,9 +325,27 @@ int or_pmis(int n, const int *rp, const int *ci, const unsigned char *S, uint64_
     for (int i = 0; i < n; ++i)
       if (st[i] == ST_NEWC) st[i] = ST_C;
   }
-  for (int i = 0; i < n; ++i) cf[i] = (st[i] == ST_C) ? 1 : 0;
-  free(tcnt); free(lam); free(st); free(tcol); free(fill);
+  for (int i = 0; i < n; ++i) state[i] = (st[i] == ST_C) ? 1 : (st[i] == ST_F) ? 0 : -1;
+  if (rounds_out) *rounds_out = rounds;
+  free(tcnt); free(st); free(tcol); free(fill);
   return OR_OK;
+}
+
+int or_pmis(int n, const int *rp, const int *ci, const unsigned char *S, uint64_t seed, int level,
+            signed char *cf) {
+  int *deg = (int *)calloc((size_t)n + 1, sizeof(int));
+  double *lam = (double *)malloc(((size_t)n + 1) * sizeof(double));
+  if (!deg || !lam) {
+    free(deg); free(lam);
+    return OR_ERR_MEM;
+  }
+  for (int j = 0; j < n; ++j) /* |S_i^T|: the points that i strongly influences */
+    for (int p = rp[j]; p < rp[j + 1]; ++p)
+      if (S[p]) deg[ci[p]]++;
+  for (int i = 0; i < n; ++i) lam[i] = (double)deg[i] + or_pmis_random(seed, level, i);
+  int st = or_pmis_rounds(n, rp, ci, S, lam, -1, cf, NULL);
+  free(deg); free(lam);
+  return st;
 }
 
 /* ------------------------------------------------------------------ */
@@ -336,8 +355,8 @@ int or_pmis(int n, const int *rp, const int *ci, const unsigned char *S, uint64_
 /* N_i the off-diagonal neighbours (sums in ascending column order):      */
 /*   alpha = sum_{N_i} a^- / sum_{P_i} a^-,  beta = sum_{N_i} a^+ / sum_{P_i} a^+ */
 /*   at = a_ii + sum_{N_i} a^+  if P_i has no positive entry, else a_ii    */
-/*   w_ij = a_ij * (-(alpha / at))  (a_ij < 0),  a_ij * (-(beta / at))  (a_ij > 0) */
-/* (the weight -alpha a_ij / at with the row factor alpha / at formed once) */
+/*   w_ij = -(alpha a_ij) / at  (a_ij < 0),  -(beta a_ij) / at  (a_ij > 0)  */
+/* (the product rounded, negated, then divided: one division per weight)  */
 /* Empty P_i gives an empty row.  Capacity `cap` bounds nnz(P).           */
 /* ------------------------------------------------------------------ */
 /* Systems (block size bs > 1, unknowns numbered node-major): unknown-wise  */
@@ -399,14 +418,13 @@ static int direct_interp(int n, const int *rp, const int *ci, const double *a, c
       double alpha = (sp_neg != 0.0) ? sn_neg / sp_neg : 0.0;
       double beta = (sp_pos != 0.0) ? sn_pos / sp_pos : 0.0;
       double at = (sp_pos != 0.0) ? aii : aii + sn_pos;
-      double f_neg = -(alpha / at), f_pos = -(beta / at);
       if (pos + np > cap) return OR_ERR_MEM;
       for (int p = rp[i]; p < rp[i + 1]; ++p) {
         int j = ci[p];
         if (j == i || !S[p] || !cf[j]) continue;
         double v = a[p], w = 0.0;
-        if (v < 0.0) w = v * f_neg;
-        if (v > 0.0) w = v * f_pos;
+        if (v < 0.0) w = -(alpha * v) / at;
+        if (v > 0.0) w = -(beta * v) / at;
         Pci[pos] = cidx[j];
         Pv[pos] = w;
         ++pos;

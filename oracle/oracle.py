@@ -41,7 +41,13 @@ _i8p = np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
+        _lib = configure(C.CDLL(build()))
+    return _lib
+
+
+def configure(L):
+    """Declares the argument types of every oracle entry point on a loaded library."""
+    if True:
         L.or_check_csr.argtypes = [C.c_int, _i32p, _i32p, _f64p]
         L.or_strength.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_double, _u8p]
         L.or_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
@@ -49,6 +55,7 @@ def lib():
         L.or_pmis_random.argtypes = [C.c_uint64, C.c_int, C.c_int]
         L.or_pmis_random.restype = C.c_double
         L.or_pmis.argtypes = [C.c_int, _i32p, _i32p, _u8p, C.c_uint64, C.c_int, _i8p]
+        L.or_pmis_rounds.argtypes = [C.c_int, _i32p, _i32p, _u8p, _f64p, C.c_int, _i8p, C.POINTER(C.c_int)]
         L.or_direct_interp.argtypes = [C.c_int, _i32p, _i32p, _f64p, _u8p, _i8p, _i32p, C.POINTER(C.c_int),
                                        _i32p, _i32p, _f64p, C.c_longlong]
         L.or_direct_interp_bs.argtypes = [C.c_int, _i32p, _i32p, _f64p, _u8p, _i8p, C.c_int, _i32p,
@@ -78,8 +85,7 @@ def lib():
         L.or_vcycle.argtypes = [C.c_void_p, _f64p, _f64p]
         L.or_pcg.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int, C.c_int, C.c_int,
                              C.POINTER(C.c_int), _f64p, C.c_void_p]
-        _lib = L
-    return _lib
+    return L
 
 
 def _i32(a):
@@ -114,6 +120,21 @@ def pmis(A, S: np.ndarray, seed: int, level: int = 0) -> np.ndarray:
     if st:
         raise RuntimeError(f"or_pmis failed: {st}")
     return cf
+
+
+def pmis_rounds(A, S: np.ndarray, lam, max_rounds: int = -1, L=None):
+    """PMIS with given measures: (state after max_rounds rounds, rounds run).
+
+    state[i] = 1 C, 0 F, -1 still undecided; max_rounds < 0 runs to the end.
+    L: a loaded oracle library (default: this one)."""
+    L = L or lib()
+    st = np.zeros(A.n, dtype=np.int8)
+    r = C.c_int(0)
+    ret = L.or_pmis_rounds(A.n, _i32(A.rowptr), _i32(A.col), np.ascontiguousarray(S, np.uint8), _f64(lam),
+                           max_rounds, st, C.byref(r))
+    if ret:
+        raise RuntimeError(f"or_pmis_rounds failed: {ret}")
+    return st, r.value
 
 
 def block_strength(A, bs: int, theta: float):

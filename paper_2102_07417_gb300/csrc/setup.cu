@@ -495,9 +495,8 @@ __global__ void k_interp_count(int n, const int *__restrict__ rp, const int *__r
 // Direct interpolation with every sum over the row in ascending column order:
 //   alpha = sum_{N_i} a^- / sum_{P_i} a^-,  beta = sum_{N_i} a^+ / sum_{P_i} a^+,
 //   at = a_ii + sum_{N_i} a^+ when P_i holds no positive entry, else a_ii,
-//   w_ij = a_ij (-(alpha / at)) for a_ij < 0, a_ij (-(beta / at)) for a_ij > 0
-// (the row factors formed once: two FP64 divisions per row, not one per
-// weight -- the kernel is bound by the FP64 pipe).
+//   w_ij = -(alpha a_ij) / at for a_ij < 0, -(beta a_ij) / at for a_ij > 0
+// (the product rounded, negated, then divided, as the formula reads).
 // Systems (bs > 1, node-major unknowns): unknown-wise, row i sees only the
 // columns of its own component (j % bs == i % bs).
 __global__ void k_interp_fill(int n, int bs, const int *__restrict__ rp, const int *__restrict__ ci,
@@ -542,15 +541,12 @@ __global__ void k_interp_fill(int n, int bs, const int *__restrict__ rp, const i
   const double alpha = sp_neg != 0.0 ? __ddiv_rn(sn_neg, sp_neg) : 0.0;
   const double beta = sp_pos != 0.0 ? __ddiv_rn(sn_pos, sp_pos) : 0.0;
   const double at = sp_pos != 0.0 ? aii : __dadd_rn(aii, sn_pos);
-  // a factor is used only by entries of its sign in P_i, which exist iff its sum is nonzero
-  const double f_neg = sp_neg != 0.0 ? -__ddiv_rn(alpha, at) : 0.0;
-  const double f_pos = sp_pos != 0.0 ? -__ddiv_rn(beta, at) : 0.0;
   for (int p = b; p < e; ++p) {
     const int j = ci[p];
     if (j == i || !S[p] || !cf[j]) continue;
     const double v = a[p];
     const int sg = sign_class(v);
-    const double w = sg ? __dmul_rn(v, sg < 0 ? f_neg : f_pos) : 0.0;
+    const double w = sg ? __ddiv_rn(-__dmul_rn(sg < 0 ? alpha : beta, v), at) : 0.0;
     pci[pos] = cidx[j];
     pv[pos] = w;
     ++pos;
@@ -799,17 +795,15 @@ __global__ void __launch_bounds__(256) k_interp_fill_w(int n, int bs, const int 
   }
   np = __shfl_sync(0xffffffffu, np, 0);
   if (np == 0) return;
-  double f_neg = 0.0, f_pos = 0.0;
+  double alpha = 0.0, beta = 0.0, at = 0.0;
   if (lane == 0) {
-    const double alpha = sp_neg != 0.0 ? __ddiv_rn(sn_neg, sp_neg) : 0.0;
-    const double beta = sp_pos != 0.0 ? __ddiv_rn(sn_pos, sp_pos) : 0.0;
-    const double at = sp_pos != 0.0 ? aii : __dadd_rn(aii, sn_pos);
-    // a factor is used only by entries of its sign in P_i, which exist iff its sum is nonzero
-    f_neg = sp_neg != 0.0 ? -__ddiv_rn(alpha, at) : 0.0;
-    f_pos = sp_pos != 0.0 ? -__ddiv_rn(beta, at) : 0.0;
+    alpha = sp_neg != 0.0 ? __ddiv_rn(sn_neg, sp_neg) : 0.0;
+    beta = sp_pos != 0.0 ? __ddiv_rn(sn_pos, sp_pos) : 0.0;
+    at = sp_pos != 0.0 ? aii : __dadd_rn(aii, sn_pos);
   }
-  f_neg = __shfl_sync(0xffffffffu, f_neg, 0);
-  f_pos = __shfl_sync(0xffffffffu, f_pos, 0);
+  alpha = __shfl_sync(0xffffffffu, alpha, 0);
+  beta = __shfl_sync(0xffffffffu, beta, 0);
+  at = __shfl_sync(0xffffffffu, at, 0);
   for (int c0 = b; c0 < e; c0 += 32) {
     const int p = c0 + lane;
     bool sel = false;
@@ -822,7 +816,7 @@ __global__ void __launch_bounds__(256) k_interp_fill_w(int n, int bs, const int 
     if (sel) {
       const double v = a[p];
       const int sg = sign_class(v);
-      const double wv = sg ? __dmul_rn(v, sg < 0 ? f_neg : f_pos) : 0.0;
+      const double wv = sg ? __ddiv_rn(-__dmul_rn(sg < 0 ? alpha : beta, v), at) : 0.0;
       const int q = pos + __popc(bal & ((1u << lane) - 1u));
       pci[q] = cidx[j];
       pv[q] = wv;

@@ -120,8 +120,13 @@ def check_pmis_invariants(A, S, cf):
     Si, STi = _strong_sets(A, S)
     for i in range(A.n):
         if cf[i]:
-            # (i) no two C points are strongly connected either way
-            assert not any(cf[j] for j in Si[i] | STi[i])
+            # (i) no two C points are strongly connected both ways, and on a
+            # symmetric strength graph not at all.  (With an asymmetric graph a
+            # C point may depend on a later C point that it beat earlier: the
+            # F step only reaches points that depend on a new C point.)
+            assert not any(cf[j] for j in Si[i] & STi[i])
+            if all(Si[j] == STi[j] for j in range(A.n)):
+                assert not any(cf[j] for j in Si[i] | STi[i])
         else:
             # (ii) an F point influenced nobody or depends on a C point
             assert len(STi[i]) == 0 or any(cf[j] for j in Si[i])
