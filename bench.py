@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the served-latency leg")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision leg (FP32 hierarchy and V-cycle, FP64 flexible PCG) of an FP64 run")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the 256^3 heterogeneous-diffusion leg (GPU FP32 V-cycle run and its oracle baseline)")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-capacity", type=int, default=4)
     ap.add_argument("--no-kernel-events", action="store_true",
@@ -196,6 +198,25 @@ def gpu_uuid(dev: int):
         return None
 
 
+def workload_config(p, desc, prec, rtol, world):
+    """The `config` object of the JSON line (the same for both arms)."""
+    kw = getattr(p, "params", {})
+    bs = kw.get("block_size", 1)
+    omega = kw.get("omega", 2.0 / 3.0)
+    batch = p.b.ndim == 2
+    return {"workload": desc, "n": p.A.n, "nnz": p.A.nnz, "precision": prec, "rtol": rtol, "theta": 0.25,
+            "coarsening": "PMIS (seed 0)" + (" on 3x3 nodal blocks" if bs > 1 else ""),
+            "interpolation": "direct" + (" (unknown-wise)" if bs > 1 else ""),
+            "smoother": f"Jacobi omega={omega:.4g}, V(1,1)", "max_coarse": 64,
+            "rhs": p.b.shape[1] if batch else 1,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": f"inputs larger than L2 (A is {(12 * p.A.nnz + 4 * p.A.n) / 1e6:.0f} MB of FP64 CSR)"}
+
+
+def default_precision(p, requested=None):
+    return requested or getattr(p, "precision", None) or ("fp64" if p.A.n <= 4_200_000 else "fp32")
+
+
 # ------------------------------------------------------------------ oracle arm --
 def oracle_solve(p, rtol):
     from oracle import oracle as O
@@ -255,7 +276,8 @@ def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": desc, "n": p.A.n, "nnz": p.A.nnz, "rtol": args.rtol, "precision": "fp64"},
+           "config": workload_config(p, desc, default_precision(p, args.precision), args.rtol, world),
+           "oracle_precision": "fp64 (the oracle computes every step in FP64)",
            "iters": it, "status": st,
            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -274,7 +296,7 @@ def run_gpu(args, rank, world, dist):
     dev = torch.device("cuda", local)
     amg.load()
     p, desc = make_problem(args.workload)
-    prec = args.precision or getattr(p, "precision", None) or ("fp64" if p.A.n <= 4_200_000 else "fp32")
+    prec = default_precision(p, args.precision)
     prec_id = {"fp64": amg.PREC_FP64, "fp32": amg.PREC_FP32, "bf16pr": amg.PREC_FP32_BF16PR}[prec]
     params = amg.default_params(precision=prec_id, **getattr(p, "params", {}))
     batch = p.b.ndim == 2
@@ -372,6 +394,9 @@ def run_gpu(args, rank, world, dist):
             "launches_timed": d["launches"], "avg_launch_us": d["ms"] * 1e3 / max(d["launches"], 1),
             "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
             "traffic": traffic_for(args.workload, dom, dom_lv, batch)}
+    if roof["traffic"] and roof["bytes_per_launch"]:
+        # DRAM bytes moved per launch (ncu) over the algorithmic bytes: above 1 is re-read / scratch traffic
+        roof["traffic_over_algorithmic"] = roof["traffic"] / roof["bytes_per_launch"]
     double_float = batch and prec != "fp64" and p.b.shape[1] in (8, 16) and dom == "spmv_dot" and d["ms"] > 0
     if double_float:
         # FP32 modes compute q = A p of 8- or 16-column batches in double-float (FP32 pairs, on the FP32
@@ -450,6 +475,12 @@ def run_gpu(args, rank, world, dist):
     if world == 1 and not args.no_serve:
         serving = run_serving(args)
 
+    config3 = None
+    if world == 1 and not args.no_config3 and args.workload != "diffusion3d_256":
+        del A_dev, b_dev, x_dev
+        torch.cuda.empty_cache()
+        config3 = run_config3(args, stream, dev, rank == 0 and not args.no_cpu_baseline)
+
     if rank != 0:
         return
     info = rec["info"]
@@ -457,14 +488,7 @@ def run_gpu(args, rank, world, dist):
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
-        "config": {"workload": desc, "n": p.A.n, "nnz": p.A.nnz, "precision": prec, "rtol": args.rtol,
-                   "theta": 0.25,
-                   "coarsening": "PMIS (seed 0)" + (" on 3x3 nodal blocks" if params.block_size > 1 else ""),
-                   "interpolation": "direct" + (" (unknown-wise)" if params.block_size > 1 else ""),
-                   "smoother": f"Jacobi omega={params.omega:.4g}, V(1,1)", "max_coarse": 64,
-                   "rhs": p.b.shape[1] if batch else 1,
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": f"inputs larger than L2 (A is {(12 * p.A.nnz + 4 * p.A.n) / 1e6:.0f} MB of FP64 CSR)"},
+        "config": workload_config(p, desc, prec, args.rtol, world),
         "t_setup_ms": 1e3 * statistics.median(tps), "t_solve_ms": 1e3 * statistics.median(tss),
         "host_ms_median": {k_: statistics.median(v_[-args.steps:]) for k_, v_ in host.items()},
         "iters": rec["iters"], "status": rec["status"], "nlevels": info["nlevels"], "cgd": info["cgd"],
@@ -476,7 +500,7 @@ def run_gpu(args, rank, world, dist):
         "profile_pass": {"note": "one extra step with events around every launch (not timed)",
                          "kernels_ms": kernels, "by_level_ms": by_level},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-        "mixed_precision": mixed, "serving": serving,
+        "mixed_precision": mixed, "serving": serving, "config3": config3,
     }
     print(json.dumps(out), flush=True)
 
@@ -533,6 +557,85 @@ def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, prec_id=None):
             "steps": len(times),
             "vcycle_hbm": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s", "peak": peak,
                            "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None}}
+
+
+def run_config3(args, stream, dev, with_oracle):
+    """The largest configuration: 3-D heterogeneous diffusion on 256^3 (sigma 2, seed 2), hierarchy
+    stored and V-cycle run in FP32 under the FP64 flexible PCG, rtol 1e-8.  Set-up and solve timed
+    with CUDA events (median of a few steps after warm-up), the V-cycle's HBM roofline from one
+    profiled step, and, with `with_oracle`, one FP64 oracle set-up + solve of the same system on one
+    host core with the distance between the two solutions."""
+    import numpy as np
+    import torch
+
+    from paper_2102_07417_gb300 import amg
+    from paper_2102_07417_gb300.problems import CSR
+
+    t0 = time.perf_counter()
+    p, desc = make_problem("diffusion3d_256")
+    t_gen = time.perf_counter() - t0
+    A_dev = CSR(p.A.n, torch.as_tensor(p.A.rowptr, device=dev), torch.as_tensor(p.A.col, device=dev),
+                torch.as_tensor(p.A.val, device=dev))
+    b_dev = torch.as_tensor(p.b, device=dev)
+    x_dev = torch.zeros_like(b_dev)
+    params = amg.default_params(precision=amg.PREC_FP32)
+    rec = {}
+
+    def step():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        h = amg.Hierarchy(A_dev, params, stream=stream)
+        e[1].record(stream)
+        x_dev.zero_()
+        _, it, st, _ = h.solve(b_dev, x_dev, rtol=args.rtol, maxit=1000)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        rec.update(iters=it, status=st, info=h.info())
+        h.close()
+        return e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+
+    step()
+    step()
+    amg.profile(True)
+    step()
+    amg.profile(False)
+    prof = amg.profile_read()
+    vb = sum(prof[k]["bytes"] for k in VCYCLE)
+    vt = sum(prof[k]["ms"] for k in VCYCLE)
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                   "gbs": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None}
+               for k, v in prof.items() if v["launches"]}
+    peak, peak_src = peaks()
+    clk = Clocks(gpu_uuid(dev.index or 0), not args.no_clocks)
+    times = [step() for _ in range(3)]
+    clocks = clk.stop()
+    tp = statistics.median(t[0] for t in times)
+    ts = statistics.median(t[1] for t in times)
+    x_gpu = x_dev.cpu().numpy()
+    out = {"workload": desc, "n": p.A.n, "nnz": p.A.nnz, "precision": "fp32 hierarchy + V-cycle, fp64 flexible PCG",
+           "rtol": args.rtol, "t_setup_ms": tp, "t_solve_ms": ts, "t_total_ms": tp + ts, "iters": rec["iters"],
+           "status": rec["status"], "nlevels": rec["info"]["nlevels"], "cop": rec["info"]["cop"],
+           "steps": len(times), "host_generation_s": t_gen, "clocks": clocks,
+           "vcycle_hbm": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s", "peak": peak,
+                          "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None,
+                          "peak_source": f"{peak_src} hbm_gbs"},
+           "profile_pass_kernels_ms": kernels}
+    if with_oracle:
+        from oracle import oracle as O
+
+        t0 = time.perf_counter()
+        ho = O.Hierarchy(p.A, seed=0)
+        t1 = time.perf_counter()
+        st_o, xo, it_o, _, _ = ho.pcg(p.b, rtol=args.rtol, maxit=1000)
+        t2 = time.perf_counter()
+        out["cpu_baseline"] = {"value": t2 - t0, "unit": "s", "cores": 1, "kind": "oracle",
+                               "sample": f"one full FP64 oracle set-up ({t1 - t0:.1f} s) + PCG solve "
+                                         f"({t2 - t1:.1f} s, {it_o} it) of this workload",
+                               "iters": it_o, "status": st_o}
+        out["x_rel_diff_vs_oracle"] = float(np.linalg.norm(x_gpu - xo) / np.linalg.norm(xo))
+        out["true_rel_residual_gpu"] = float(np.linalg.norm(p.b - p.A.matvec(x_gpu)) / np.linalg.norm(p.b))
+        del ho
+    return out
 
 
 def run_serving(args):

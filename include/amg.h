@@ -223,6 +223,8 @@ int amg_spmv(amg_hierarchy *h, int32_t level, const double *x, double *y, void *
  * rows each); larger n returns AMG_ERR_UNSUPPORTED before any GPU work.
  * The first call on each device looks up the scratch array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The address is kept per device and context: after a cudaDeviceReset the
+ * next call on that device looks it up again (again outside any capture).
  * Every call on a device shares the scratch array and it keeps the previous
  * call's contents; the ticket is cleared at the start of each call, but calls
  * that overlap on the GPU (e.g. on two streams at once) race on it and give

@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -34,6 +35,20 @@ struct Status {
       throw ::amg::Status{AMG_ERR_CUDA};                                                     \
     }                                                                                        \
   } while (0)
+
+// Raises `fn`'s dynamic shared-memory limit to `bytes` on the current device,
+// once per device (bit d of `done` records device d).  Setting the attribute
+// is idempotent, so two host threads racing on a device's first call both
+// set it harmlessly; devices beyond 63 set it on every call.
+template <typename F>
+void ensure_smem_attr(F *fn, int bytes, std::atomic<unsigned long long> &done) {
+  int dev = 0;
+  AMG_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+  AMG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.fetch_or(bit, std::memory_order_acq_rel);
+}
 
 extern std::atomic<long long> g_launches;
 #define AMG_CHECK_LAUNCH()                                    \
@@ -219,6 +234,12 @@ struct amg_hierarchy {
   // FP64 row-major with n = lev[dense_level].A.n; dense_level = -1: none
   int dense_level = -1;
   double *dense_op = nullptr;
+  // double-float (FP32 pair) copy of level 0's sliced-ELLPACK values, built on
+  // first use by a batched FP32-mode solve or slots object; df_mu serialises
+  // its construction across host threads, df_ev marks its completion on the
+  // hierarchy's stream (other streams wait on it before reading the copy)
+  std::mutex df_mu;
+  cudaEvent_t df_ev = nullptr;
   size_t bytes = 0;
 };
 

@@ -1088,12 +1088,22 @@ bool use_df(amg_hierarchy *h) {
   return std::is_same<T, float>::value && K >= 8 && bsell<K>(A) && A.sell.v != nullptr;
 }
 
+// Built once per hierarchy, under its mutex, on the hierarchy's own stream
+// (where its allocator orders the memory); the caller's stream `s` then waits
+// for the build's event, so every user reads a finished copy.
 void ensure_df(amg_hierarchy *h, cudaStream_t s) {
   DCsr &A = h->lev[0].A;
-  if (A.sell.vdf) return;
-  A.sell.vdf = h->mem.get_n<float2>(std::max<int64_t>(A.sell.nent, 1));
-  k_split_df<<<grid_for(A.sell.nent), TPB, 0, s>>>(A.sell.nent, A.sell.v, A.sell.vdf);
-  AMG_CHECK_LAUNCH();
+  std::lock_guard<std::mutex> lock(h->df_mu);
+  cudaStream_t hs = h->mem.stream;
+  if (!A.sell.vdf) {
+    if (!h->df_ev) AMG_CUDA(cudaEventCreateWithFlags(&h->df_ev, cudaEventDisableTiming));
+    float2 *vdf = h->mem.get_n<float2>(std::max<int64_t>(A.sell.nent, 1));
+    k_split_df<<<grid_for(A.sell.nent), TPB, 0, hs>>>(A.sell.nent, A.sell.v, vdf);
+    AMG_CHECK_LAUNCH();
+    AMG_CUDA(cudaEventRecord(h->df_ev, hs));
+    A.sell.vdf = vdf;
+  }
+  if (s != hs) AMG_CUDA(cudaStreamWaitEvent(s, h->df_ev, 0));
 }
 
 // q = A p and the alpha bookkeeping: double-float when p2 is set, FP64 otherwise.
@@ -1510,12 +1520,9 @@ int pcg_solve_batch(amg_hierarchy *h, int k, const double *B, double *X, double 
       set_error("last level of %d rows too large for a %d-column batch", nL, k);
       throw Status{AMG_ERR_UNSUPPORTED};
     }
-    static bool attr = false;
-    if (!attr) {
-      AMG_CUDA(cudaFuncSetAttribute(k_bcoarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      AMG_CUDA(cudaFuncSetAttribute(k_bcoarse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
-    }
+    static std::atomic<unsigned long long> attr_d{0}, attr_f{0};
+    ensure_smem_attr(k_bcoarse<double>, 200 * 1024, attr_d);
+    ensure_smem_attr(k_bcoarse<float>, 200 * 1024, attr_f);
   }
   switch (h->prm.precision) {
     case AMG_PREC_FP64: return batch_dispatch<double, double>(h, k, B, X, rtol, maxit, iters, status, hist, hist_cap);
@@ -1533,12 +1540,9 @@ SlotsBase *make_slots(amg_hierarchy *h, int K, double rtol, int maxit, cudaStrea
     set_error("last level of %d rows too large for %d slots", h->nL, K);
     throw Status{AMG_ERR_UNSUPPORTED};
   }
-  static bool attr = false;
-  if (!attr) {
-    AMG_CUDA(cudaFuncSetAttribute(k_bcoarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    AMG_CUDA(cudaFuncSetAttribute(k_bcoarse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr_d{0}, attr_f{0};
+  ensure_smem_attr(k_bcoarse<double>, 200 * 1024, attr_d);
+  ensure_smem_attr(k_bcoarse<float>, 200 * 1024, attr_f);
   switch (h->prm.precision) {
     case AMG_PREC_FP64: return make_slots_t<double, double>(h, K, rtol, maxit, s);
     case AMG_PREC_FP32: return make_slots_t<float, float>(h, K, rtol, maxit, s);

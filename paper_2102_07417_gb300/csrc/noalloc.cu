@@ -82,9 +82,41 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dot_noalloc(int n, const int 
 
 std::mutex g_mu;
 unsigned char *g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context id the address belongs to (0: unknown)
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the first call on each device does it).
+// Id of the calling thread's current CUDA context (0 when none is current or
+// the driver does not report it).  The driver entry points are looked up
+// through the runtime, so the library keeps no link-time dependency on the
+// driver library.
+unsigned long long current_context_id() {
+  typedef int (*get_current_t)(void **);
+  typedef int (*get_id_t)(void *, unsigned long long *);
+  static get_current_t get_current = nullptr;
+  static get_id_t get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr, *g = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<get_current_t>(f);
+      get_id = reinterpret_cast<get_id_t>(g);
+    }
+  });
+  if (!get_current || !get_id) return 0;
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device, looked up on the
+// first call on each device and again whenever the device's context has
+// changed since (a cudaDeviceReset unloads the module, and the address found
+// before it is no longer valid); when the context id cannot be read, it is
+// looked up on every call.
 int scratch_on_current_device(unsigned char **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -97,7 +129,8 @@ int scratch_on_current_device(unsigned char **out) {
     return AMG_ERR_UNSUPPORTED;
   }
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_ptr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void *ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || !ptr) {
@@ -105,6 +138,7 @@ int scratch_on_current_device(unsigned char **out) {
       return AMG_ERR_CUDA;
     }
     g_scratch_ptr[dev] = static_cast<unsigned char *>(ptr);
+    g_scratch_ctx[dev] = current_context_id();  // the lookup made the context current if it was not
   }
   *out = g_scratch_ptr[dev];
   return AMG_OK;

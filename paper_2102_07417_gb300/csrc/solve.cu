@@ -1390,6 +1390,8 @@ void release_solve(amg_hierarchy *h) {
   h->h_done = nullptr;
   for (auto &e : h->iter_ev)
     if (e) cudaEventDestroy(e);
+  if (h->df_ev) cudaEventDestroy(h->df_ev);
+  h->df_ev = nullptr;
 }
 
 int pcg_solve(amg_hierarchy *h, const double *b, double *x, double rtol, int maxit, int *iters, double *hist,
