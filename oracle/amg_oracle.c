@@ -24,8 +24,10 @@
  *   - R = P^T and A_c = P^T A P (Eq. AcDef), computed as R (A P) in a
  *     canonical order (below).
  *   - Algorithm 1 (AMG_SetUp) with a dense Cholesky on the last level.
- *   - Algorithm 2 (AMG_Apply, V-cycle) with a damped Jacobi smoother
- *     S = I - omega D^{-1} A (Eq. smoother, M = D).
+ *   - Algorithm 2 (AMG_Apply, V-cycle) with the smoother
+ *     S = I - omega M^{-1} A (Eq. smoother): damped Jacobi (M = D), or the
+ *     factored sparse approximate inverse M^{-1} = G^T G with G lower
+ *     triangular (Eq. smo), G on the static pattern of lower(A).
  *   - PCG from x0 with the stopping rule ||r_k|| < rtol ||b|| on the
  *     recursively updated residual (Sec. 4); standard or flexible
  *     (Polak-Ribiere) beta.
@@ -71,10 +73,12 @@ typedef struct {
   or_csr R[OR_MAX_LEVELS]; /* R[k] = P[k]^T */
   signed char *cf[OR_MAX_LEVELS];
   unsigned char *S[OR_MAX_LEVELS];
+  or_csr G[OR_MAX_LEVELS];     /* FSAI factor of level k (smoother 1), k < nlevels-1 */
   double *L;                   /* dense Cholesky factor of the last level, row-major */
   int nL;
   double omega;
   int nu1, nu2;
+  int smoother;                /* 0 damped Jacobi, 1 FSAI */
   /* work vectors per level */
   double *wr[OR_MAX_LEVELS], *wy[OR_MAX_LEVELS], *wz[OR_MAX_LEVELS], *ws[OR_MAX_LEVELS];
 } or_hier;
@@ -435,6 +439,164 @@ static int direct_interp(int n, const int *rp, const int *ci, const double *a, c
   return OR_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* Extended+i interpolation (Sec. 2.3, the distance-two formula; De Sterck, */
+/* Falgout, Nolting & Yang).  Reading of the printed formula:              */
+/*   C_i^S, F_i^S: strong C / F neighbours of i; the interpolatory set is   */
+/*   Chat_i = C_i^S u (union over k in F_i^S of C_k^S);                     */
+/*   abar_kl = a_kl when its sign differs from a_kk's (a_kk > 0: a_kl < 0),  */
+/*   else 0;  d_k = sum over l in row k with l in Chat_i u {i} of abar_kl;   */
+/*   at = a_ii + sum over weak n not in Chat_i of a_in                      */
+/*             + sum over k in F_i^S of (a_ik abar_ki) / d_k ;              */
+/*   w_ij = -(a_ij + sum over k in F_i^S of (a_ik abar_kj) / d_k) / at,     */
+/*   j in Chat_i (a_ij = 0 when j is not a neighbour).                      */
+/* Canonical evaluation (the GPU follows it bit for bit): d_k over row k in  */
+/* ascending l; at from a_ii over row i's off-diagonals in ascending order   */
+/* (an F_i^S term (a_ik abar_ki) / d_k or a weak a_in as the entry calls    */
+/* for); each numerator from a_ij, adding the k terms in ascending k; terms  */
+/* with abar_kj = 0 are skipped; a strong F neighbour with d_k = 0 has no    */
+/* interpolatory connection and is lumped into at as a_ik (its weight terms  */
+/* are skipped); w_ij = -(num / at).  An empty Chat_i, or at = 0, gives an   */
+/* empty row.  Scalar problems only (bs = 1).                               */
+/* ------------------------------------------------------------------ */
+static double abar(double akl) { return akl < 0.0 ? akl : 0.0; } /* a_kk > 0 on every level */
+
+static int row_pos(const int *rp, const int *ci, int i, int j) {
+  int lo = rp[i], hi = rp[i + 1] - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) / 2;
+    if (ci[mid] == j) return mid;
+    if (ci[mid] < j) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+static int in_sorted(const int *set, int m, int j) {
+  int lo = 0, hi = m - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) / 2;
+    if (set[mid] == j) return 1;
+    if (set[mid] < j) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return 0;
+}
+
+static int ext_interp(int n, const int *rp, const int *ci, const double *a, const unsigned char *S,
+                      const signed char *cf, int *cidx, int *nc_out, int *Prp, int *Pci, double *Pv, long long cap) {
+  int nc = 0;
+  for (int i = 0; i < n; ++i) cidx[i] = cf[i] ? nc++ : -1;
+  *nc_out = nc;
+  int maxrow = 0;
+  for (int i = 0; i < n; ++i)
+    if (rp[i + 1] - rp[i] > maxrow) maxrow = rp[i + 1] - rp[i];
+  size_t candcap = (size_t)maxrow * (size_t)maxrow + 1;
+  int *cand = (int *)malloc(candcap * sizeof(int));
+  double *d = (double *)malloc(((size_t)maxrow + 1) * sizeof(double));
+  if (!cand || !d) {
+    free(cand); free(d);
+    return OR_ERR_MEM;
+  }
+  long long pos = 0;
+  Prp[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    if (cf[i]) {
+      if (pos + 1 > cap) { free(cand); free(d); return OR_ERR_MEM; }
+      Pci[pos] = cidx[i];
+      Pv[pos] = 1.0;
+      ++pos;
+      Prp[i + 1] = (int)pos;
+      continue;
+    }
+    /* Chat_i: strong C neighbours of i and of its strong F neighbours */
+    int m = 0;
+    double aii = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      int k = ci[p];
+      if (k == i) aii = a[p];
+      if (k == i || !S[p]) continue;
+      if (cf[k]) {
+        cand[m++] = k;
+      } else {
+        for (int q = rp[k]; q < rp[k + 1]; ++q)
+          if (S[q] && ci[q] != k && cf[ci[q]]) cand[m++] = ci[q];
+      }
+    }
+    qsort(cand, (size_t)m, sizeof(int), cmp_int);
+    int u = 0;
+    for (int t = 0; t < m; ++t)
+      if (u == 0 || cand[t] != cand[u - 1]) cand[u++] = cand[t];
+    m = u;
+    if (m == 0) {
+      Prp[i + 1] = (int)pos;
+      continue;
+    }
+    /* d_k for every strong F neighbour k (indexed by its position in row i) */
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      int k = ci[p];
+      d[p - rp[i]] = 0.0;
+      if (k == i || !S[p] || cf[k]) continue;
+      double dk = 0.0;
+      for (int q = rp[k]; q < rp[k + 1]; ++q) {
+        int l = ci[q];
+        double ab = abar(a[q]);
+        if (l == k || ab == 0.0) continue;
+        if (l == i || in_sorted(cand, m, l)) dk += ab;
+      }
+      d[p - rp[i]] = dk;
+    }
+    /* at = a_ii + lumped weak couplings + the F_i^S terms toward i */
+    double at = aii;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      int k = ci[p];
+      if (k == i) continue;
+      if (S[p] && !cf[k]) {
+        double dk = d[p - rp[i]];
+        if (dk != 0.0) {
+          int q = row_pos(rp, ci, k, i);
+          double ab = q >= 0 ? abar(a[q]) : 0.0;
+          if (ab != 0.0) at += (a[p] * ab) / dk;
+        } else {
+          at += a[p];
+        }
+      } else if (!S[p] && !(cf[k] && in_sorted(cand, m, k))) {
+        at += a[p];
+      }
+    }
+    if (at == 0.0) {
+      Prp[i + 1] = (int)pos;
+      continue;
+    }
+    if (pos + m > cap) { free(cand); free(d); return OR_ERR_MEM; }
+    for (int t = 0; t < m; ++t) {
+      int j = cand[t];
+      int qj = row_pos(rp, ci, i, j);
+      double num = qj >= 0 ? a[qj] : 0.0;
+      for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        int k = ci[p];
+        if (k == i || !S[p] || cf[k]) continue;
+        double dk = d[p - rp[i]];
+        if (dk == 0.0) continue;
+        int q = row_pos(rp, ci, k, j);
+        double ab = q >= 0 ? abar(a[q]) : 0.0;
+        if (ab != 0.0) num += (a[p] * ab) / dk;
+      }
+      Pci[pos] = cidx[j];
+      Pv[pos] = -(num / at);
+      ++pos;
+    }
+    Prp[i + 1] = (int)pos;
+  }
+  free(cand); free(d);
+  return OR_OK;
+}
+
+int or_ext_interp(int n, const int *rp, const int *ci, const double *a, const unsigned char *S,
+                  const signed char *cf, int *cidx, int *nc_out, int *Prp, int *Pci, double *Pv, long long cap) {
+  return ext_interp(n, rp, ci, a, S, cf, cidx, nc_out, Prp, Pci, Pv, cap);
+}
+
 /* R = P^T, rows of R listing fine indices in ascending order. */
 static int transpose(const or_csr *P, int ncols, or_csr *R) {
   if (csr_alloc(R, ncols, P->nnz)) return OR_ERR_MEM;
@@ -601,6 +763,94 @@ void or_jacobi_sweep(int n, const int *rp, const int *ci, const double *a, doubl
 }
 
 /* ------------------------------------------------------------------ */
+/* Factored sparse approximate inverse (Eq. smo: M^{-1} = G^T G, G lower  */
+/* triangular).  The paper's aFSAI grows the pattern of G adaptively      */
+/* (cited, not described); the reading taken here is the static FSAI of   */
+/* Kolotilina & Yeremin on the pattern of the lower triangle of A:        */
+/* for row i, P_i = { j <= i : a_ij stored } (ascending, last = i),        */
+/*   solve A[P_i, P_i] gt = e_last (dense Cholesky of the principal        */
+/*   submatrix, which is SPD when A is), then g_i = gt / sqrt(gt_last),   */
+/* so that (G A G^T)_ii = 1.  Grp[n+1], Gci / Gv with room for nnz(A).    */
+/* ------------------------------------------------------------------ */
+static double csr_entry(const int *rp, const int *ci, const double *a, int i, int j) {
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] == j) return a[p];
+  return 0.0;
+}
+
+int or_fsai(int n, const int *rp, const int *ci, const double *a, int *Grp, int *Gci, double *Gv) {
+  int mmax = 0;
+  for (int i = 0; i < n; ++i) {
+    int m = 0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) m += (ci[p] <= i);
+    if (m > mmax) mmax = m;
+  }
+  int *P = (int *)malloc(((size_t)mmax + 1) * sizeof(int));
+  double *M = (double *)malloc(((size_t)mmax * mmax + 1) * sizeof(double));
+  double *e = (double *)malloc(((size_t)mmax + 1) * sizeof(double));
+  double *g = (double *)malloc(((size_t)mmax + 1) * sizeof(double));
+  if (!P || !M || !e || !g) {
+    free(P); free(M); free(e); free(g);
+    return OR_ERR_MEM;
+  }
+  int pos = 0, st = OR_OK;
+  Grp[0] = 0;
+  for (int i = 0; i < n && !st; ++i) {
+    int m = 0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] <= i) P[m++] = ci[p];
+    if (m == 0 || P[m - 1] != i) {
+      st = OR_ERR_ARG; /* no diagonal */
+      break;
+    }
+    for (int r = 0; r < m; ++r)
+      for (int c = 0; c < m; ++c) M[(size_t)r * m + c] = csr_entry(rp, ci, a, P[r], P[c]);
+    if (or_cholesky(m, M)) {
+      st = OR_ERR_NOT_SPD;
+      break;
+    }
+    for (int r = 0; r < m; ++r) e[r] = (r == m - 1) ? 1.0 : 0.0;
+    or_cholesky_solve(m, M, e, g);
+    if (!(g[m - 1] > 0.0)) {
+      st = OR_ERR_NOT_SPD;
+      break;
+    }
+    double scale = sqrt(g[m - 1]);
+    for (int r = 0; r < m; ++r) {
+      Gci[pos] = P[r];
+      Gv[pos] = g[r] / scale;
+      ++pos;
+    }
+    Grp[i + 1] = pos;
+  }
+  free(P); free(M); free(e); free(g);
+  return st;
+}
+
+/* One FSAI smoothing step s <- s + omega G^T G (y - A s)  (Eq. smoother with */
+/* M^{-1} = G^T G).  G^T u is formed by scattering each row of G.            */
+void or_fsai_sweep(int n, const int *rp, const int *ci, const double *a, const int *Grp, const int *Gci,
+                   const double *Gv, double omega, const double *y, double *s) {
+  double *r = (double *)malloc((size_t)n * sizeof(double));
+  double *u = (double *)malloc((size_t)n * sizeof(double));
+  double *w = (double *)calloc((size_t)n, sizeof(double));
+  for (int i = 0; i < n; ++i) {
+    double t = y[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p) t -= a[p] * s[ci[p]];
+    r[i] = t;
+  }
+  for (int i = 0; i < n; ++i) {
+    double t = 0.0;
+    for (int p = Grp[i]; p < Grp[i + 1]; ++p) t += Gv[p] * r[Gci[p]];
+    u[i] = t;
+  }
+  for (int i = 0; i < n; ++i)
+    for (int p = Grp[i]; p < Grp[i + 1]; ++p) w[Gci[p]] += Gv[p] * u[i];
+  for (int i = 0; i < n; ++i) s[i] += omega * w[i];
+  free(r); free(u); free(w);
+}
+
+/* ------------------------------------------------------------------ */
 /* Algorithm 1: AMG set-up.                                               */
 /* Stop on: n_k <= max_coarse, level max_levels-1 reached, or a stalled   */
 /* coarsening (n_{k+1} == 0 or n_{k+1} > 0.9 n_k).  The last level is      */
@@ -608,23 +858,33 @@ void or_jacobi_sweep(int n, const int *rp, const int *ci, const double *a, doubl
 /* ------------------------------------------------------------------ */
 void or_free(or_hier *h);
 
-int or_setup_bs(int n, const int *rp, const int *ci, const double *a, double theta, uint64_t seed,
-                int max_coarse, int max_levels, double omega, int nu1, int nu2, int bs, or_hier **out);
+int or_setup_ex(int n, const int *rp, const int *ci, const double *a, double theta, uint64_t seed,
+                int max_coarse, int max_levels, double omega, int nu1, int nu2, int bs, int smoother, int interp,
+                or_hier **out);
 
 int or_setup(int n, const int *rp, const int *ci, const double *a, double theta, uint64_t seed,
              int max_coarse, int max_levels, double omega, int nu1, int nu2, or_hier **out) {
-  return or_setup_bs(n, rp, ci, a, theta, seed, max_coarse, max_levels, omega, nu1, nu2, 1, out);
+  return or_setup_ex(n, rp, ci, a, theta, seed, max_coarse, max_levels, omega, nu1, nu2, 1, 0, 0, out);
+}
+
+int or_setup_bs(int n, const int *rp, const int *ci, const double *a, double theta, uint64_t seed,
+                int max_coarse, int max_levels, double omega, int nu1, int nu2, int bs, or_hier **out) {
+  return or_setup_ex(n, rp, ci, a, theta, seed, max_coarse, max_levels, omega, nu1, nu2, bs, 0, 0, out);
 }
 
 /* Algorithm 1.  bs = 1: scalar strength and PMIS on the unknowns.  bs > 1  */
 /* (systems, node-major unknowns): nodal block strength, PMIS on the node   */
 /* graph (the measure counter runs over node indices), every unknown of a   */
 /* node takes the node's C/F label, and unknown-wise direct interpolation.  */
-int or_setup_bs(int n, const int *rp, const int *ci, const double *a, double theta, uint64_t seed,
-                int max_coarse, int max_levels, double omega, int nu1, int nu2, int bs, or_hier **out) {
+/* smoother: 0 damped Jacobi, 1 FSAI (G formed on every level but the last). */
+/* interp: 0 direct interpolation, 1 extended+i (bs = 1).                   */
+int or_setup_ex(int n, const int *rp, const int *ci, const double *a, double theta, uint64_t seed,
+                int max_coarse, int max_levels, double omega, int nu1, int nu2, int bs, int smoother, int interp,
+                or_hier **out) {
   *out = NULL;
   if (!(theta > 0.0 && theta <= 1.0) || max_levels < 1 || max_levels > OR_MAX_LEVELS || nu1 < 0 ||
-      nu2 < 0 || max_coarse < 1 || bs < 1 || n % bs)
+      nu2 < 0 || max_coarse < 1 || bs < 1 || n % bs || smoother < 0 || smoother > 1 || interp < 0 ||
+      interp > 1 || (interp == 1 && bs != 1))
     return OR_ERR_ARG;
   int st = or_check_csr(n, rp, ci, a);
   if (st) return st;
@@ -633,6 +893,7 @@ int or_setup_bs(int n, const int *rp, const int *ci, const double *a, double the
   h->omega = omega;
   h->nu1 = nu1;
   h->nu2 = nu2;
+  h->smoother = smoother;
   if (csr_alloc(&h->A[0], n, rp[n])) {
     or_free(h);
     return OR_ERR_MEM;
@@ -679,14 +940,22 @@ int or_setup_bs(int n, const int *rp, const int *ci, const double *a, double the
         last = 1; /* stalled coarsening: this level becomes the last one */
       } else {
         long long cap = (long long)A->nnz + nk;
+        if (interp == 1) { /* |Chat_i| <= sum over the row's strong neighbours of their row lengths */
+          cap = nk;
+          for (int i = 0; i < nk; ++i)
+            for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) cap += A->rp[A->ci[p] + 1] - A->rp[A->ci[p]];
+        }
         or_csr *P = &h->P[k];
-        if (csr_alloc(P, nk, (int)cap)) {
+        if (cap >= 2147483647LL || csr_alloc(P, nk, (int)cap)) {
           or_free(h);
           return OR_ERR_MEM;
         }
         int *cidx = (int *)malloc((size_t)nk * sizeof(int));
         int ncc = 0;
-        st = direct_interp(nk, A->rp, A->ci, A->v, h->S[k], h->cf[k], bs, cidx, &ncc, P->rp, P->ci, P->v, cap);
+        if (interp == 1)
+          st = ext_interp(nk, A->rp, A->ci, A->v, h->S[k], h->cf[k], cidx, &ncc, P->rp, P->ci, P->v, cap);
+        else
+          st = direct_interp(nk, A->rp, A->ci, A->v, h->S[k], h->cf[k], bs, cidx, &ncc, P->rp, P->ci, P->v, cap);
         free(cidx);
         if (st) {
           or_free(h);
@@ -699,6 +968,12 @@ int or_setup_bs(int n, const int *rp, const int *ci, const double *a, double the
         if (!st) st = spgemm(A, P, nc, &AP);
         if (!st) st = spgemm(&h->R[k], &AP, nc, &h->A[k + 1]);
         csr_free(&AP);
+        if (!st && smoother == 1) {
+          or_csr *G = &h->G[k];
+          st = csr_alloc(G, nk, A->nnz);
+          if (!st) st = or_fsai(nk, A->rp, A->ci, A->v, G->rp, G->ci, G->v);
+          if (!st) G->nnz = G->rp[nk];
+        }
         if (st) {
           or_free(h);
           return st;
@@ -738,6 +1013,7 @@ void or_free(or_hier *h) {
     csr_free(&h->A[k]);
     csr_free(&h->P[k]);
     csr_free(&h->R[k]);
+    csr_free(&h->G[k]);
     free(h->cf[k]);
     free(h->S[k]);
     free(h->wr[k]);
@@ -771,6 +1047,15 @@ void or_get_P(const or_hier *h, int k, int *rp, int *ci, double *v) {
   memcpy(v, m->v, (size_t)m->nnz * sizeof(double));
 }
 
+int or_G_nnz(const or_hier *h, int k) { return (k < h->nlevels - 1 && h->smoother == 1) ? h->G[k].nnz : 0; }
+
+void or_get_G(const or_hier *h, int k, int *rp, int *ci, double *v) {
+  const or_csr *m = &h->G[k];
+  memcpy(rp, m->rp, ((size_t)m->n + 1) * sizeof(int));
+  memcpy(ci, m->ci, (size_t)m->nnz * sizeof(int));
+  memcpy(v, m->v, (size_t)m->nnz * sizeof(double));
+}
+
 void or_get_cf(const or_hier *h, int k, signed char *cf) { memcpy(cf, h->cf[k], (size_t)h->A[k].n); }
 
 void or_get_S(const or_hier *h, int k, unsigned char *S) { memcpy(S, h->S[k], (size_t)h->A[k].nnz); }
@@ -788,6 +1073,17 @@ void or_complexities(const or_hier *h, double *cgd, double *cop) {
 /* ------------------------------------------------------------------ */
 /* Algorithm 2: V-cycle z_k = B_k y_k.                                    */
 /* ------------------------------------------------------------------ */
+/* one smoothing step s <- s + omega M^{-1} (y - A s) on level k (Eq. smoother) */
+static void smooth(or_hier *h, int k, const double *y, double *s) {
+  const or_csr *A = &h->A[k];
+  if (h->smoother == 1) {
+    const or_csr *G = &h->G[k];
+    or_fsai_sweep(A->n, A->rp, A->ci, A->v, G->rp, G->ci, G->v, h->omega, y, s);
+  } else {
+    or_jacobi_sweep(A->n, A->rp, A->ci, A->v, h->omega, y, s);
+  }
+}
+
 static void vcycle(or_hier *h, int k, const double *y, double *z) {
   const or_csr *A = &h->A[k];
   int n = A->n;
@@ -798,7 +1094,7 @@ static void vcycle(or_hier *h, int k, const double *y, double *z) {
   double *s = h->ws[k], *r = h->wr[k];
   /* nu1 smoothing steps on A s = y from s = 0 */
   for (int i = 0; i < n; ++i) s[i] = 0.0;
-  for (int it = 0; it < h->nu1; ++it) or_jacobi_sweep(n, A->rp, A->ci, A->v, h->omega, y, s);
+  for (int it = 0; it < h->nu1; ++it) smooth(h, k, y, s);
   /* residual r = y - A s */
   or_spmv(n, A->rp, A->ci, A->v, s, r);
   for (int i = 0; i < n; ++i) r[i] = y[i] - r[i];
@@ -813,7 +1109,7 @@ static void vcycle(or_hier *h, int k, const double *y, double *z) {
   for (int i = 0; i < n; ++i) s[i] += r[i];
   /* nu2 smoothing steps from z = s */
   for (int i = 0; i < n; ++i) z[i] = s[i];
-  for (int it = 0; it < h->nu2; ++it) or_jacobi_sweep(n, A->rp, A->ci, A->v, h->omega, y, z);
+  for (int it = 0; it < h->nu2; ++it) smooth(h, k, y, z);
 }
 
 void or_vcycle(or_hier *h, const double *y, double *z) {

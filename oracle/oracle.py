@@ -58,10 +58,18 @@ def configure(L):
         L.or_pmis_rounds.argtypes = [C.c_int, _i32p, _i32p, _u8p, _f64p, C.c_int, _i8p, C.POINTER(C.c_int)]
         L.or_direct_interp.argtypes = [C.c_int, _i32p, _i32p, _f64p, _u8p, _i8p, _i32p, C.POINTER(C.c_int),
                                        _i32p, _i32p, _f64p, C.c_longlong]
+        L.or_ext_interp.argtypes = [C.c_int, _i32p, _i32p, _f64p, _u8p, _i8p, _i32p, C.POINTER(C.c_int),
+                                    _i32p, _i32p, _f64p, C.c_longlong]
         L.or_direct_interp_bs.argtypes = [C.c_int, _i32p, _i32p, _f64p, _u8p, _i8p, C.c_int, _i32p,
                                           C.POINTER(C.c_int), _i32p, _i32p, _f64p, C.c_longlong]
         L.or_block_strength.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_int, C.c_double, C.POINTER(C.c_int),
                                         _i32p, _i32p, _u8p, _u8p]
+        L.or_setup_ex.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_double, C.c_uint64, C.c_int, C.c_int,
+                                  C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]
+        L.or_fsai.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p]
+        L.or_fsai_sweep.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p, C.c_double, _f64p, _f64p]
+        L.or_G_nnz.argtypes = [C.c_void_p, C.c_int]
+        L.or_get_G.argtypes = [C.c_void_p, C.c_int, _i32p, _i32p, _f64p]
         L.or_setup_bs.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_double, C.c_uint64, C.c_int, C.c_int,
                                   C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]
         L.or_galerkin.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_int, _i32p, _i32p, _f64p,
@@ -168,6 +176,23 @@ def direct_interp(A, S: np.ndarray, cf: np.ndarray, bs: int = 1):
     return rp, ci[:nnz].copy(), v[:nnz].copy(), nc.value
 
 
+def ext_interp(A, S: np.ndarray, cf: np.ndarray):
+    """Extended+i interpolation: (P_rowptr, P_col, P_val, nc)."""
+    lens = np.diff(A.rowptr)
+    cap = A.n + int(lens[A.col].sum())
+    rp = np.zeros(A.n + 1, np.int32)
+    ci = np.zeros(max(cap, 1), np.int32)
+    v = np.zeros(max(cap, 1), np.float64)
+    cidx = np.zeros(A.n, np.int32)
+    nc = C.c_int(0)
+    st = lib().or_ext_interp(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), np.ascontiguousarray(S, np.uint8),
+                             np.ascontiguousarray(cf, np.int8), cidx, C.byref(nc), rp, ci, v, cap)
+    if st:
+        raise RuntimeError(f"or_ext_interp failed: {st}")
+    nnz = int(rp[-1])
+    return rp, ci[:nnz].copy(), v[:nnz].copy(), nc.value
+
+
 def galerkin(A, P_rowptr, P_col, P_val, nc: int):
     """A_c = P^T A P as (rowptr, col, val)."""
     nnz = C.c_int(0)
@@ -183,6 +208,25 @@ def galerkin(A, P_rowptr, P_col, P_val, nc: int):
     for p in (rp, ci, v):
         lib().or_free_array(C.cast(p, C.c_void_p))
     return out
+
+
+def fsai(A):
+    """Static FSAI factor G (lower triangle of A's pattern) as (rowptr, col, val)."""
+    rp = np.zeros(A.n + 1, np.int32)
+    ci = np.zeros(max(A.nnz, 1), np.int32)
+    v = np.zeros(max(A.nnz, 1))
+    st = lib().or_fsai(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), rp, ci, v)
+    if st:
+        raise RuntimeError(f"or_fsai failed: {st}")
+    nnz = int(rp[-1])
+    return rp, ci[:nnz].copy(), v[:nnz].copy()
+
+
+def fsai_sweep(A, G, omega: float, y: np.ndarray, s: np.ndarray) -> np.ndarray:
+    s = _f64(s).copy()
+    lib().or_fsai_sweep(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), _i32(G[0]), _i32(G[1]), _f64(G[2]), omega,
+                        _f64(y), s)
+    return s
 
 
 def cholesky(M: np.ndarray) -> np.ndarray:
@@ -223,12 +267,15 @@ class Level:
 class Hierarchy:
     """Oracle AMG hierarchy (Algorithm 1) with V-cycle and PCG (Algorithm 2, Sec. 4)."""
 
+    SMOOTHERS = {"jacobi": 0, "fsai": 1}
+    INTERPS = {"direct": 0, "ext": 1}
+
     def __init__(self, A, theta=0.25, seed=0, max_coarse=64, max_levels=25, omega=2.0 / 3.0, nu1=1, nu2=1,
-                 block_size=1):
+                 block_size=1, smoother="jacobi", interp="direct"):
         self._keep = (_i32(A.rowptr), _i32(A.col), _f64(A.val))
         h = C.c_void_p()
-        st = lib().or_setup_bs(A.n, *self._keep, theta, seed, max_coarse, max_levels, omega, nu1, nu2, block_size,
-                               C.byref(h))
+        st = lib().or_setup_ex(A.n, *self._keep, theta, seed, max_coarse, max_levels, omega, nu1, nu2, block_size,
+                               self.SMOOTHERS[smoother], self.INTERPS[interp], C.byref(h))
         if st:
             raise RuntimeError(f"or_setup failed: {st}")
         self.h = h
@@ -259,6 +306,14 @@ class Hierarchy:
         rp, ci, v = np.zeros(n + 1, np.int32), np.zeros(max(npn, 1), np.int32), np.zeros(max(npn, 1))
         lib().or_get_P(self.h, k, rp, ci, v)
         return rp, ci[:npn], v[:npn]
+
+    def G(self, k: int):
+        """FSAI factor of level k as (rowptr, col, val) (smoother "fsai", k < nlevels - 1)."""
+        n, _, _ = self.level_sizes(k)
+        ng = lib().or_G_nnz(self.h, k)
+        rp, ci, v = np.zeros(n + 1, np.int32), np.zeros(max(ng, 1), np.int32), np.zeros(max(ng, 1))
+        lib().or_get_G(self.h, k, rp, ci, v)
+        return rp, ci[:ng], v[:ng]
 
     def cf(self, k: int) -> np.ndarray:
         n, _, _ = self.level_sizes(k)
