@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "AMG-PCG time to rtol 1e-8 & V-cycle HBM GB/s vs peak; served p50/p99 latency"
 FALLBACK_HBM_GBS = 6800.0
-VCYCLE = ("smooth_resid", "restrict", "prolong", "smooth_post", "coarse")
+VCYCLE = ("smooth_resid", "restrict", "prolong", "smooth_post", "coarse", "smooth_fsai")
 
 
 def parse():
@@ -470,6 +470,27 @@ def run_gpu(args, rank, world, dist):
     if prec == "fp64" and not batch and not args.no_mixed:
         mixed = run_mixed(args, p, A_dev, b_dev, stream, dev, barrier)
         mixed["bf16_pr_ablation"] = run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, amg.PREC_FP32_BF16PR)
+    fsai = None
+    if not batch and not args.no_mixed:
+        # the paper's default smoother family (Eq. smo), static FSAI on lower(A_k), omega = 1
+        fsai = {"fp64": run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, amg.PREC_FP64,
+                                  name="FSAI smoother (omega 1), fp64 hierarchy + V-cycle + PCG",
+                                  smoother=amg.SMOOTH_FSAI, omega=1.0),
+                "fp32": run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, amg.PREC_FP32,
+                                  name="FSAI smoother (omega 1), fp32 hierarchy + V-cycle, fp64 flexible PCG",
+                                  smoother=amg.SMOOTH_FSAI, omega=1.0)}
+    ext = None
+    if not batch and not args.no_mixed and getattr(p, "params", {}).get("block_size", 1) == 1:
+        # extended+i interpolation (Sec. 2.3), with Jacobi and with FSAI (the paper's standard set-up
+        # pairs its FSAI-type smoother with extended+i)
+        ext = {"jacobi_fp64": run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, amg.PREC_FP64,
+                                        name="extended+i interpolation, Jacobi, fp64", interp=amg.INTERP_EXT),
+               "fsai_fp64": run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, amg.PREC_FP64,
+                                      name="extended+i interpolation, FSAI (omega 1), fp64", interp=amg.INTERP_EXT,
+                                      smoother=amg.SMOOTH_FSAI, omega=1.0),
+               "fsai_fp32": run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, amg.PREC_FP32,
+                                      name="extended+i interpolation, FSAI (omega 1), fp32 V-cycle, fp64 flexible PCG",
+                                      interp=amg.INTERP_EXT, smoother=amg.SMOOTH_FSAI, omega=1.0)}
 
     serving = None
     if world == 1 and not args.no_serve:
@@ -500,16 +521,18 @@ def run_gpu(args, rank, world, dist):
         "profile_pass": {"note": "one extra step with events around every launch (not timed)",
                          "kernels_ms": kernels, "by_level_ms": by_level},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-        "mixed_precision": mixed, "serving": serving, "config3": config3,
+        "mixed_precision": mixed, "fsai_smoother": fsai, "ext_interp": ext, "serving": serving,
+        "config3": config3,
     }
     print(json.dumps(out), flush=True)
 
 
-def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, prec_id=None):
+def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, prec_id=None, name=None, **kw):
     """The same workload with the hierarchy stored and the V-cycle run in FP32 under the FP64
     flexible PCG (the mixed-precision form; with prec_id = PREC_FP32_BF16PR, P and R stored in
-    BF16): set-up + solve per step timed with CUDA events, its V-cycle bandwidth from one
-    profiled step, and the error against x*."""
+    BF16), or another variant of the method given by `kw` (e.g. the FSAI smoother): set-up +
+    solve per step timed with CUDA events, its V-cycle bandwidth from one profiled step, and the
+    error against x*."""
     import numpy as np
     import torch
 
@@ -517,7 +540,7 @@ def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, prec_id=None):
 
     if prec_id is None:
         prec_id = amg.PREC_FP32
-    params = amg.default_params(precision=prec_id, **getattr(p, "params", {}))
+    params = amg.default_params(precision=prec_id, **{**getattr(p, "params", {}), **kw})
     x_dev = torch.zeros_like(b_dev)
     rec = {}
 
@@ -550,13 +573,15 @@ def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, prec_id=None):
     x_err = None
     if p.xstar is not None:
         x_err = float(np.linalg.norm(x_dev.cpu().numpy() - p.xstar) / np.linalg.norm(p.xstar))
-    name = ("fp32 hierarchy + V-cycle, fp64 flexible PCG" if prec_id == amg.PREC_FP32 else
-            "fp32 hierarchy + V-cycle with P and R in bf16, fp64 flexible PCG")
+    if name is None:
+        name = ("fp32 hierarchy + V-cycle, fp64 flexible PCG" if prec_id == amg.PREC_FP32 else
+                "fp32 hierarchy + V-cycle with P and R in bf16, fp64 flexible PCG")
     return {"precision": name, "t_setup_ms": tp, "t_solve_ms": ts,
             "t_total_ms": tp + ts, "iters": rec["iters"], "status": rec["status"], "x_rel_err": x_err,
-            "steps": len(times),
+            "steps": len(times), "cgd": rec["info"]["cgd"], "cop": rec["info"]["cop"],
             "vcycle_hbm": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s", "peak": peak,
-                           "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None}}
+                           "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None},
+            "profiled_kernels_ms": {k: round(v["ms"], 4) for k, v in prof.items() if v["launches"]}}
 
 
 def run_config3(args, stream, dev, with_oracle):

@@ -48,6 +48,15 @@ extern "C" {
 #define AMG_ERR_TIMEOUT (-8)        /* a bounded device-side wait ran out */
 #define AMG_ERR_UNSUPPORTED (-9)    /* size beyond a documented limit */
 
+/* Smoothers of the V-cycle: S = I - omega M^-1 A (Eq. smoother). */
+#define AMG_SMOOTH_JACOBI 0 /* M = D, damped Jacobi */
+#define AMG_SMOOTH_FSAI 1   /* M^-1 = G^T G, G lower triangular (Eq. smo), static pattern lower(A_k) */
+
+/* Interpolation of the set-up (Sec. 2.3). */
+#define AMG_INTERP_DIRECT 0 /* direct (distance-one) interpolation */
+#define AMG_INTERP_EXT 1    /* extended+i (distance two): interpolatory set C_i^S plus the strong C
+                             * neighbours of i's strong F neighbours; scalar problems only */
+
 /* Precision modes of the solve phase (the set-up is always FP64). */
 #define AMG_PREC_FP64 0        /* hierarchy and V-cycle in FP64 */
 #define AMG_PREC_FP32 1        /* hierarchy stored and V-cycle run in FP32, outer PCG FP64, flexible beta */
@@ -102,6 +111,22 @@ typedef struct {
                        * max_{K != I} s_IK; PMIS runs on the node graph; every unknown takes its
                        * node's C/F label; interpolation is unknown-wise (direct interpolation
                        * over the same-component couplings only). */
+  int32_t smoother;   /* AMG_SMOOTH_*; AMG_SMOOTH_JACOBI.  AMG_SMOOTH_FSAI: the factored sparse
+                       * approximate inverse M^-1 = G^T G of Sec. 2.1 with G on the static pattern
+                       * of the lower triangle of each A_k (the paper's aFSAI chooses the pattern
+                       * adaptively); row i of G solves A[P_i, P_i] g = e_i on P_i = {j <= i :
+                       * a_ij stored}, scaled to (G A G^T)_ii = 1.  A smoothing step costs one
+                       * product with A, G and G^T.  omega must keep omega rho(G^T G A) < 2
+                       * (rho ~ 1.37 on 3-D Poisson: omega = 1 is a good choice).  Single
+                       * right-hand-side solves and V-cycles only: amg_pcg_solve_batch and
+                       * amg_slots_create return AMG_ERR_UNSUPPORTED on such a hierarchy. */
+  int32_t interp;     /* AMG_INTERP_*; AMG_INTERP_DIRECT.  AMG_INTERP_EXT: the extended+i weights of
+                       * Sec. 2.3, w_ij = -(a_ij + sum_{k in F_i^S} a_ik abar_kj / d_k) / at_ii with
+                       * d_k = sum of abar_kl over l in Chat_i u {i}, evaluated in a fixed order so the
+                       * hierarchy is reproducible bit for bit; needs block_size = 1
+                       * (AMG_ERR_INVALID_ARG otherwise); a zero modified diagonal at_ii gives
+                       * AMG_ERR_SETUP; a row with more interpolatory candidates than the per-warp
+                       * shared-memory set holds (~6000) gives AMG_ERR_UNSUPPORTED. */
 } amg_params;
 
 /* Fills *p with the defaults above.  Returns AMG_ERR_INVALID_ARG if p is NULL. */
@@ -262,6 +287,14 @@ int amg_hierarchy_info(const amg_hierarchy *h, int32_t *nlevels, int32_t cap, in
 int amg_hierarchy_export(const amg_hierarchy *h, int32_t level, int8_t *cf, int32_t *A_rowptr, int32_t *A_col,
                          double *A_val, int32_t *P_rowptr, int32_t *P_col, double *P_val);
 
+/* FSAI factor of level k (smoother AMG_SMOOTH_FSAI, k < nlevels - 1): *nnz (may be
+ * NULL) receives nnz(G_k); G_rowptr[n_k + 1], G_col[nnz], G_val[nnz] (host, any may be
+ * NULL) receive G_k as CSR (rows ascending, each ending at its diagonal).  *nnz = 0 and
+ * nothing is copied on the last level or with the Jacobi smoother.  Synchronises the
+ * hierarchy's stream. */
+int amg_hierarchy_export_fsai(const amg_hierarchy *h, int32_t level, int64_t *nnz, int32_t *G_rowptr,
+                              int32_t *G_col, double *G_val);
+
 /* Device bytes held by the hierarchy (for admission by free HBM). */
 size_t amg_hierarchy_bytes(const amg_hierarchy *h);
 
@@ -292,7 +325,9 @@ void amg_free(amg_hierarchy *h);
 #define AMG_K_TRANSPOSE 12    /* set-up: R = P^T */
 #define AMG_K_SPGEMM 13       /* set-up: Galerkin SpGEMM (A P, then R (A P)) */
 #define AMG_K_SETUP_OTHER 14  /* set-up: scans, dense factor, casts, diagonal */
-#define AMG_K_COUNT 15
+#define AMG_K_SMOOTH_FSAI 15  /* V-cycle, FSAI smoother: u = G w and s += omega G^T u */
+#define AMG_K_FSAI 16         /* set-up: FSAI factor G and omega G^T */
+#define AMG_K_COUNT 17
 int amg_profile_enable(int32_t on);
 /* Restricts recording to launches of kernel class `kernel` on level `level`
  * (-1: any level); kernel = -1 records every launch again (the default).

@@ -456,8 +456,8 @@ static int direct_interp(int n, const int *rp, const int *ci, const double *a, c
 /* for); each numerator from a_ij, adding the k terms in ascending k; terms  */
 /* with abar_kj = 0 are skipped; a strong F neighbour with d_k = 0 has no    */
 /* interpolatory connection and is lumped into at as a_ik (its weight terms  */
-/* are skipped); w_ij = -(num / at).  An empty Chat_i, or at = 0, gives an   */
-/* empty row.  Scalar problems only (bs = 1).                               */
+/* are skipped); w_ij = -(num / at).  An empty Chat_i gives an empty row;   */
+/* at = 0 fails the set-up (OR_ERR_SETUP).  Scalar problems only (bs = 1).   */
 /* ------------------------------------------------------------------ */
 static double abar(double akl) { return akl < 0.0 ? akl : 0.0; } /* a_kk > 0 on every level */
 
@@ -565,8 +565,8 @@ static int ext_interp(int n, const int *rp, const int *ci, const double *a, cons
       }
     }
     if (at == 0.0) {
-      Prp[i + 1] = (int)pos;
-      continue;
+      free(cand); free(d);
+      return OR_ERR_SETUP;
     }
     if (pos + m > cap) { free(cand); free(d); return OR_ERR_MEM; }
     for (int t = 0; t < m; ++t) {

@@ -27,18 +27,21 @@ AMG_ERR_TIMEOUT = -8
 AMG_ERR_UNSUPPORTED = -9
 
 PREC_FP64, PREC_FP32, PREC_FP32_BF16PR = 0, 1, 2
+SMOOTH_JACOBI, SMOOTH_FSAI = 0, 1
+INTERP_DIRECT, INTERP_EXT = 0, 1
 
 KERNEL_NAMES = ["spmv_dot", "pcg_update", "smooth_resid", "restrict", "prolong", "smooth_post", "coarse",
-                "direction", "solve_other", "strength", "pmis", "interp", "transpose", "spgemm", "setup_other"]
-SOLVE_KERNELS = KERNEL_NAMES[:9]
-SETUP_KERNELS = KERNEL_NAMES[9:]
+                "direction", "solve_other", "strength", "pmis", "interp", "transpose", "spgemm", "setup_other",
+                "smooth_fsai", "fsai"]
+SOLVE_KERNELS = KERNEL_NAMES[:9] + ["smooth_fsai"]
+SETUP_KERNELS = KERNEL_NAMES[9:15] + ["fsai"]
 
 # Names exported by the C ABI (each declared in include/amg.h).
 EXPORTS = ["amg_params_default", "amg_setup", "amg_pcg_solve", "amg_pcg_solve_batch", "amg_vcycle_apply", "amg_spmv", "amg_solve",
            "amg_hierarchy_info", "amg_hierarchy_export", "amg_hierarchy_bytes", "amg_free", "amg_profile_enable",
            "amg_profile_read", "amg_profile_filter", "amg_launch_count", "amg_status_string", "amg_last_error",
            "amg_spmv_dot_noalloc", "amg_slots_create", "amg_slots_admit", "amg_slots_step", "amg_slots_poll",
-           "amg_slots_query", "amg_slots_wait", "amg_slots_retire", "amg_slots_free"]
+           "amg_slots_query", "amg_slots_wait", "amg_slots_retire", "amg_slots_free", "amg_hierarchy_export_fsai"]
 
 
 class AmgError(RuntimeError):
@@ -55,7 +58,7 @@ class Csr(C.Structure):
 class Params(C.Structure):
     _fields_ = [("theta", C.c_double), ("seed", C.c_uint64), ("max_coarse", C.c_int32), ("max_levels", C.c_int32),
                 ("omega", C.c_double), ("nu1", C.c_int32), ("nu2", C.c_int32), ("precision", C.c_int32),
-                ("block_size", C.c_int32)]
+                ("block_size", C.c_int32), ("smoother", C.c_int32), ("interp", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -109,6 +112,7 @@ def load(build_if_missing: bool = True):
                             C.POINTER(Result)]
     L.amg_hierarchy_info.argtypes = [vp, C.POINTER(i32), i32, vp, vp, vp, C.POINTER(dbl), C.POINTER(dbl)]
     L.amg_hierarchy_export.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.amg_hierarchy_export_fsai.argtypes = [vp, i32, C.POINTER(i64), vp, vp, vp]
     L.amg_hierarchy_bytes.argtypes = [vp]
     L.amg_hierarchy_bytes.restype = C.c_size_t
     L.amg_free.argtypes = [vp]
@@ -133,8 +137,12 @@ def check(code: int, where: str):
 
 
 def default_params(**kw) -> Params:
+    """amg_params_default with keyword overrides.  With smoother=SMOOTH_FSAI and no omega given,
+    omega = 1 (omega rho(G^T G A) ~ 1.37 < 2 on 3-D Poisson, the condition after Eq. smoother)."""
     p = Params()
     check(load().amg_params_default(C.byref(p)), "amg_params_default")
+    if kw.get("smoother") == SMOOTH_FSAI and "omega" not in kw:
+        kw["omega"] = 1.0
     for k, v in kw.items():
         if not hasattr(p, k):
             raise TypeError(f"unknown parameter {k}")
@@ -323,6 +331,19 @@ class Hierarchy:
                                           av.ctypes.data, prp.ctypes.data, pci.ctypes.data, pv.ctypes.data),
               "amg_hierarchy_export")
         return {"cf": cf, "A": (arp, aci[:nnz], av[:nnz]), "P": (prp, pci[:nnzp], pv[:nnzp])}
+
+    def export_fsai(self, level: int):
+        """FSAI factor G of a level as (rowptr, col, val), or None (Jacobi smoother, last level)."""
+        L = load()
+        nnz = C.c_int64(0)
+        check(L.amg_hierarchy_export_fsai(self.h, level, C.byref(nnz), None, None, None), "amg_hierarchy_export_fsai")
+        if nnz.value == 0:
+            return None
+        n = self.info()["n"][level]
+        rp, ci, v = np.zeros(n + 1, np.int32), np.zeros(nnz.value, np.int32), np.zeros(nnz.value)
+        check(L.amg_hierarchy_export_fsai(self.h, level, None, rp.ctypes.data, ci.ctypes.data, v.ctypes.data),
+              "amg_hierarchy_export_fsai")
+        return rp, ci, v
 
     def nbytes(self) -> int:
         return int(load().amg_hierarchy_bytes(self.h))

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
-UNITS = {"setup": ["--fmad=false"], "spgemm": ["--fmad=false"], "solve": [], "batch": [], "api": [], "noalloc": []}
+UNITS = {"setup": ["--fmad=false"], "spgemm": ["--fmad=false"], "solve": [], "batch": [], "api": [], "noalloc": [], "fsai": []}
 
 
 def _nvcc() -> str:

@@ -157,6 +157,7 @@ struct PcgScalars {
 
 struct Level {
   DCsr A, P, R;   // P, R empty on the last level
+  DCsr G, GT;     // FSAI smoother: G and omega G^T (empty with the Jacobi smoother and on the last level)
   int8_t *cf = nullptr;    // C/F of this level (export), nullptr on the last level
   double *wd = nullptr;    // omega / a_ii (FP64)
   float *wd32 = nullptr;   // omega / a_ii (FP32)
@@ -277,8 +278,23 @@ int pcg_solve_batch(amg_hierarchy *h, int k, const double *B, double *X, double 
 void spmv_level(amg_hierarchy *h, int level, const double *x, double *y);
 void release_solve(amg_hierarchy *h);
 
-// C = X Y with the canonical summation order (spgemm.cu); flags: device error flags
-void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C);
+// FSAI factor G of level k and omega G^T (fsai.cu)
+void build_fsai(amg_hierarchy *h, int k);
+// R = P^T with rows sorted (setup.cu)
+void csr_transpose(Mem &m, const DCsr &P, int ncols, DCsr &R);
+
+// A product left in slot form: row i at [rp[i], rp[i] + cnt[i]) of its arrays;
+// nnz (device) = sum of the counts, filled in stream order.
+struct SlotRows {
+  Buf<int> cnt;
+  Buf<long long> nnz;
+};
+// C = X Y with the canonical summation order (spgemm.cu); flags: device error
+// flags.  yslot: Y is in slot form (its arrays in Y, its counts here).  cslot:
+// leave C in slot form (C.rp = row offsets, C.nnz = slot capacity) instead of
+// compacting it into CSR.  level: hierarchy level for the profiler.
+void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, const SlotRows *yslot, int ncols, DCsr &C, int level,
+            SlotRows *cslot);
 
 // device-wide exclusive scan of n int32 counts into out[0..n] (out[n] = total); returns total
 int64_t scan_counts(Mem &mem, const int *in, int *out, int n);

@@ -138,6 +138,8 @@ int amg_params_default(amg_params *p) {
   p->nu2 = 1;
   p->precision = AMG_PREC_FP64;
   p->block_size = 1;
+  p->smoother = AMG_SMOOTH_JACOBI;
+  p->interp = AMG_INTERP_DIRECT;
   return AMG_OK;
 }
 
@@ -149,6 +151,9 @@ static int check_params(const amg_params &p) {
   if (p.nu1 < 0 || p.nu1 > 8 || p.nu2 < 0 || p.nu2 > 8) return bad("nu1, nu2 must be in 0..8");
   if (p.precision < AMG_PREC_FP64 || p.precision > AMG_PREC_FP32_BF16PR) return bad("unknown precision mode");
   if (p.block_size < 1 || p.block_size > 8) return bad("block_size must be in 1..8");
+  if (p.smoother != AMG_SMOOTH_JACOBI && p.smoother != AMG_SMOOTH_FSAI) return bad("unknown smoother");
+  if (p.interp != AMG_INTERP_DIRECT && p.interp != AMG_INTERP_EXT) return bad("unknown interpolation");
+  if (p.interp == AMG_INTERP_EXT && p.block_size != 1) return bad("extended+i interpolation needs block_size 1");
   return AMG_OK;
 }
 
@@ -424,6 +429,26 @@ int amg_hierarchy_export(const amg_hierarchy *h, int32_t level, int8_t *cf, int3
     d2h(P_col, L.P.ci, sizeof(int) * (size_t)L.P.nnz);
     d2h(P_val, L.P.v, sizeof(double) * (size_t)L.P.nnz);
   }
+  AMG_CUDA(cudaStreamSynchronize(s));
+  return AMG_OK;
+  AMG_GUARD_END
+}
+
+int amg_hierarchy_export_fsai(const amg_hierarchy *h, int32_t level, int64_t *nnz, int32_t *G_rowptr,
+                              int32_t *G_col, double *G_val) {
+  if (!h) return bad("NULL hierarchy");
+  if (level < 0 || level >= h->nlevels) return bad("level out of range");
+  AMG_GUARD_BEGIN
+  const amg::DCsr &G = h->lev[level].G;
+  if (nnz) *nnz = G.rp ? G.nnz : 0;
+  if (!G.rp) return AMG_OK;
+  cudaStream_t s = h->mem.stream;
+  auto d2h = [&](void *dst, const void *src, size_t bytes) {
+    if (dst && src && bytes) AMG_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+  };
+  d2h(G_rowptr, G.rp, sizeof(int) * ((size_t)G.n + 1));
+  d2h(G_col, G.ci, sizeof(int) * (size_t)G.nnz);
+  d2h(G_val, G.v, sizeof(double) * (size_t)G.nnz);
   AMG_CUDA(cudaStreamSynchronize(s));
   return AMG_OK;
   AMG_GUARD_END

@@ -1514,6 +1514,10 @@ SlotsBase *make_slots_t(amg_hierarchy *h, int K, double rtol, int maxit, cudaStr
 
 int pcg_solve_batch(amg_hierarchy *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
                     int *status, double *hist, int hist_cap) {
+  if (h->prm.smoother != AMG_SMOOTH_JACOBI) {
+    set_error("multi-RHS solves support the Jacobi smoother only");
+    throw Status{AMG_ERR_UNSUPPORTED};
+  }
   if (h->nlevels > 0) {
     const int nL = h->nL;
     if ((size_t)2 * sizeof(double) * nL * k > 200 * 1024) {
@@ -1536,6 +1540,10 @@ int pcg_solve_batch(amg_hierarchy *h, int k, const double *B, double *X, double 
 namespace amg {
 
 SlotsBase *make_slots(amg_hierarchy *h, int K, double rtol, int maxit, cudaStream_t s) {
+  if (h->prm.smoother != AMG_SMOOTH_JACOBI) {
+    set_error("continuous batching supports the Jacobi smoother only");
+    throw Status{AMG_ERR_UNSUPPORTED};
+  }
   if ((size_t)2 * sizeof(double) * h->nL * K > 200 * 1024) {
     set_error("last level of %d rows too large for %d slots", h->nL, K);
     throw Status{AMG_ERR_UNSUPPORTED};

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 
@@ -825,6 +826,285 @@ __global__ void __launch_bounds__(256) k_interp_fill_w(int n, int bs, const int 
   }
 }
 
+// -------------------------------------------- extended+i interpolation --
+// Sec. 2.3's distance-two formula, evaluated in the order the oracle fixes:
+//   Chat_i = C_i^S u (union over strong F neighbours k of C_k^S);
+//   d_k = sum over row k (ascending l) of a_kl < 0 with l in Chat_i u {i};
+//   at  = a_ii + over row i's off-diagonals in ascending order either
+//         (a_ik a_ki) / d_k (strong F neighbour, a_ki < 0, d_k != 0), a_ik
+//         (strong F neighbour with d_k = 0), or a_in (weak, not in Chat_i);
+//   w_ij = -((a_ij + sum over strong F k ascending of (a_ik a_kj) / d_k) / at)
+//         for j in Chat_i ascending, terms with a_kj >= 0 or d_k = 0 skipped.
+// A warp per row builds Chat_i in a shared-memory hash set (the candidates:
+// strong C neighbours and the strong C neighbours of each strong F
+// neighbour), sorts its keys, then forms d_k (a lane per F neighbour), at
+// (one lane, serial like the oracle) and the weights (a lane per j).
+constexpr int kExtWarps = 4;  // most warps per block of the extended+i kernels
+
+// sc[i] = number of strong C neighbours of row i.
+__global__ void k_strong_c(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                           const uint8_t *__restrict__ S, const int8_t *__restrict__ cf, int *__restrict__ sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) c += (ci[p] != i && S[p] && cf[ci[p]]) ? 1 : 0;
+  sc[i] = c;
+}
+
+// mx[0] = largest candidate bound of a row (its strong C neighbours plus those of
+// its strong F neighbours, repeats counted), mx[1] = longest row.
+__global__ void k_ext_bound(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                            const uint8_t *__restrict__ S, const int8_t *__restrict__ cf,
+                            const int *__restrict__ sc, int *mx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int bnd = 0, len = 0;
+  if (i < n) {
+    len = rp[i + 1] - rp[i];
+    bnd = sc[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int k = ci[p];
+      if (k != i && S[p] && !cf[k]) bnd += sc[k];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    bnd = max(bnd, __shfl_xor_sync(0xffffffffu, bnd, o));
+    len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&mx[0], bnd);
+    atomicMax(&mx[1], len);
+  }
+}
+
+// Inserts key into the warp's open-addressing set (T slots, T a power of two
+// above the row's candidate bound, so a free slot always exists).
+__device__ __forceinline__ void ext_insert(int *table, int T, int key) {
+  unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(T - 1);
+  for (;;) {
+    const int prev = atomicCAS(&table[h], -1, key);
+    if (prev == -1 || prev == key) return;
+    h = (h + 1) & (unsigned)(T - 1);
+  }
+}
+
+// Chat_i of F row i into keys[0..m) ascending; returns m (all lanes).  The
+// strong F neighbours' rows are walked as one flattened sequence (lane u of
+// a 32-product step takes product u of the chunk, found by a shuffle search
+// over the chunk's prefix of row lengths), so the rows are gathered in
+// parallel rather than one after another.
+__device__ int ext_set(int i, int lane, const int *__restrict__ rp, const int *__restrict__ ci,
+                       const uint8_t *__restrict__ S, const int8_t *__restrict__ cf, int *table, int *keys, int T) {
+  for (int t = lane; t < T; t += 32) table[t] = -1;
+  __syncwarp();
+  const int b = rp[i], e = rp[i + 1];
+  for (int c0 = b; c0 < e; c0 += 32) {
+    const int p = c0 + lane;
+    int ks = 0, len = 0;
+    if (p < e) {
+      const int k = ci[p];
+      if (k != i && S[p]) {
+        if (cf[k]) {
+          ext_insert(table, T, k);
+        } else {
+          ks = rp[k];
+          len = rp[k + 1] - ks;
+        }
+      }
+    }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int excl = incl - len;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int u0 = 0; u0 < total; u0 += 32) {
+      const int u = u0 + lane;
+      int lo = 0;  // the last lane whose exclusive prefix is <= u
+#pragma unroll
+      for (int step = 16; step; step >>= 1) {
+        const int ex = __shfl_sync(0xffffffffu, excl, lo + step);
+        if (ex <= u) lo += step;
+      }
+      const int sks = __shfl_sync(0xffffffffu, ks, lo), sex = __shfl_sync(0xffffffffu, excl, lo);
+      const int sk = __shfl_sync(0xffffffffu, p < e ? ci[min(p, e - 1)] : 0, lo);
+      if (u < total) {
+        const int q = sks + u - sex;
+        const int l = ci[q];
+        if (S[q] && l != sk && cf[l]) ext_insert(table, T, l);
+      }
+    }
+  }
+  __syncwarp();
+  int m = 0;
+  for (int t0 = 0; t0 < T; t0 += 32) {
+    const int key = table[t0 + lane];
+    const unsigned bal = __ballot_sync(0xffffffffu, key >= 0);
+    if (key >= 0) keys[m + __popc(bal & ((1u << lane) - 1u))] = key;
+    m += __popc(bal);
+  }
+  int np2 = 1;
+  while (np2 < m) np2 <<= 1;
+  for (int t = m + lane; t < np2; t += 32) keys[t] = INT_MAX;
+  __syncwarp();
+  for (int kk = 2; kk <= np2; kk <<= 1)
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      for (int t = lane; t < np2; t += 32) {
+        const int u = t ^ jj;
+        if (u > t) {
+          const int x = keys[t], y = keys[u];
+          if ((x > y) == ((t & kk) == 0)) {
+            keys[t] = y;
+            keys[u] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  return m;
+}
+
+__device__ __forceinline__ int key_pos(const int *keys, int m, int key) {
+  int lo = 0, hi = m - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int c = keys[mid];
+    if (c == key) return mid;
+    if (c < key) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+// Shared memory per warp of k_ext_interp: table[T], keys[T] (ints), num[T],
+// dv[maxrow], aki[maxrow] (doubles), code[maxrow] (ints).
+__host__ __device__ inline size_t ext_warp_bytes(int T, int maxrow) {
+  const size_t b = (size_t)2 * T * sizeof(int) + (size_t)T * sizeof(double) + (size_t)2 * maxrow * sizeof(double) +
+                   (size_t)maxrow * sizeof(int);
+  return (b + 15) & ~(size_t)15;  // keeps the next warp's doubles aligned
+}
+
+// FILL = false: cnt[i] = |Chat_i| (1 for C rows).  FILL = true: row i of P:
+//   per entry p of row i (lanes in parallel): code 1 for a strong F neighbour k
+//   with its d_k (the lane walks row k in ascending order) and a_ki; code 2 for
+//   a weak coupling outside Chat_i; then one lane forms at serially in the
+//   row's order; the numerators start at a_ij (0 off the row) and take the k
+//   terms one strong F neighbour at a time in ascending k (lanes over row k:
+//   each column appears once per row, so every numerator still adds its terms
+//   in ascending k); w_ij = -(num / at).
+// flags[0]: at = 0 met.
+template <bool FILL>
+__global__ void __launch_bounds__(kExtWarps * 32) k_ext_interp(int n, const int *__restrict__ rp,
+                                                               const int *__restrict__ ci, const double *__restrict__ a,
+                                                               const uint8_t *__restrict__ S,
+                                                               const int8_t *__restrict__ cf,
+                                                               const int *__restrict__ cidx, int T, int maxrow,
+                                                               int *__restrict__ cnt, const int *__restrict__ prp,
+                                                               int *__restrict__ pci, double *__restrict__ pv,
+                                                               int *flags) {
+  extern __shared__ __align__(16) unsigned char ext_smem[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned char *base = ext_smem + ext_warp_bytes(T, maxrow) * w;
+  double *num = reinterpret_cast<double *>(base);
+  double *dv = num + T;
+  double *aki = dv + maxrow;
+  int *table = reinterpret_cast<int *>(aki + maxrow);
+  int *keys = table + T;
+  int *code = keys + T;
+  const int wpb = blockDim.x >> 5;
+  const int nw = gridDim.x * wpb;
+  for (int i = blockIdx.x * wpb + w; i < n; i += nw) {
+    if (cf[i]) {
+      if (lane == 0) {
+        if (FILL) {
+          pci[prp[i]] = cidx[i];
+          pv[prp[i]] = 1.0;
+        } else {
+          cnt[i] = 1;
+        }
+      }
+      continue;
+    }
+    const int m = ext_set(i, lane, rp, ci, S, cf, table, keys, T);
+    if (!FILL) {
+      if (lane == 0) cnt[i] = m;
+      __syncwarp();
+      continue;
+    }
+    if (m == 0) continue;
+    const int b = rp[i], e = rp[i + 1];
+    for (int t = lane; t < m; t += 32) num[t] = 0.0;
+    __syncwarp();
+    for (int p = b + lane; p < e; p += 32) {
+      const int k = ci[p];
+      int c = 0;
+      double dk = 0.0, ak = 0.0;
+      if (k != i) {
+        if (S[p] && !cf[k]) {
+          c = 1;
+          for (int q = rp[k]; q < rp[k + 1]; ++q) {
+            const int l = ci[q];
+            const double v = a[q];
+            if (l == i) ak = v;
+            if (l != k && v < 0.0 && (l == i || key_pos(keys, m, l) >= 0)) dk = __dadd_rn(dk, v);
+          }
+        } else if (!S[p]) {
+          c = (cf[k] && key_pos(keys, m, k) >= 0) ? 0 : 2;
+        }
+        const int t = key_pos(keys, m, k);  // numerators start at a_ij
+        if (t >= 0) num[t] = a[p];
+      }
+      code[p - b] = c;
+      dv[p - b] = dk;
+      aki[p - b] = ak;
+    }
+    __syncwarp();
+    double at = 0.0;
+    if (lane == 0) {
+      const int pd = find_col(ci, b, e, i);
+      at = pd >= 0 ? a[pd] : 0.0;
+      for (int p = b; p < e; ++p) {
+        const int c = code[p - b];
+        if (c == 1) {
+          const double dk = dv[p - b], ak = aki[p - b];
+          if (dk != 0.0) {
+            if (ak < 0.0) at = __dadd_rn(at, __ddiv_rn(__dmul_rn(a[p], ak), dk));
+          } else {
+            at = __dadd_rn(at, a[p]);
+          }
+        } else if (c == 2) {
+          at = __dadd_rn(at, a[p]);
+        }
+      }
+      if (at == 0.0) flags[0] = 1;
+    }
+    at = __shfl_sync(0xffffffffu, at, 0);
+    for (int p = b; p < e; ++p) {  // strong F neighbours in ascending order
+      if (code[p - b] != 1) continue;
+      const double dk = dv[p - b];
+      if (dk == 0.0) continue;
+      const int k = ci[p];
+      const double aik = a[p];
+      for (int q = rp[k] + lane; q < rp[k + 1]; q += 32) {
+        const double v = a[q];
+        if (v < 0.0 && ci[q] != k) {
+          const int t = key_pos(keys, m, ci[q]);
+          if (t >= 0) num[t] = __dadd_rn(num[t], __ddiv_rn(__dmul_rn(aik, v), dk));
+        }
+      }
+      __syncwarp();
+    }
+    const int off = prp[i];
+    for (int t = lane; t < m; t += 32) {
+      pci[off + t] = cidx[keys[t]];
+      pv[off + t] = -__ddiv_rn(num[t], at);
+    }
+    __syncwarp();
+  }
+}
+
 // ---------------------------------------------------------- transpose --
 __global__ void k_col_count(int64_t nnz, const int *__restrict__ ci, int *__restrict__ cnt) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -986,6 +1266,8 @@ void free_csr(Mem &m, DCsr &c) {
 
 }  // namespace
 
+void csr_transpose(Mem &m, const DCsr &P, int ncols, DCsr &R) { transpose(m, P, ncols, R); }
+
 // Exclusive scan of n counts into out[0..n] (out[n] = total), enqueued on the
 // stream without waiting; *total_dev receives the total.
 void scan_counts_async(Mem &m, const int *in, int *out, int n, long long *total_dev) {
@@ -1105,7 +1387,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       Buf<int> nrp, nci;
       Buf<uint8_t> SN;
       if (bs == 1) {
-        ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n + 1) + 13.0 * A.nnz);
+        ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n + 1) + 13.0 * A.nnz, k);
         // integer work only: rows of 12 to 32 entries with 8 lanes per row, longer
         // ones with a warp (128^3 level 1, 18 entries: 148 us with a thread per row,
         // 144 us with a warp; level 2, 46 entries: 44 us with a warp)
@@ -1120,7 +1402,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
         const int nn = n / bs;
         const int gnn = ceil_div(nn, TPB);
         {
-          ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n + 1) + 4.0 * A.nnz);
+          ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n + 1) + 4.0 * A.nnz, k);
           k_block_check<<<gnn, TPB, 0, s>>>(nn, bs, A.rp, A.ci, fl.d);
           AMG_CHECK_LAUNCH();
         }
@@ -1135,7 +1417,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
         SN = Buf<uint8_t>(m, std::max<int64_t>(nne, 1));
         Buf<double> dn(m, nn), sv(m, std::max<int64_t>(nne, 1));
         {
-          ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n + 1) + 12.0 * A.nnz + 8.0 * nn + 13.0 * nne);
+          ProfScope ps(s, AMG_K_STRENGTH, 4.0 * (n + 1) + 12.0 * A.nnz + 8.0 * nn + 13.0 * nne, k);
           k_node_graph<<<ceil_div(nn + 1, TPB), TPB, 0, s>>>(nn, bs, A.rp, A.ci, nrp.p, nci.p);
           AMG_CHECK_LAUNCH();
           k_block_dnorm<<<gnn, TPB, 0, s>>>(nn, bs, A.rp, A.ci, A.v, dn.p);
@@ -1160,7 +1442,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       Buf<double> lam(m, gn);
       Buf<int8_t> st0(m, gn), st1(m, gn);
       {
-        ProfScope ps(s, AMG_K_STRENGTH, rows + 6.0 * nz + 9.0 * gn);
+        ProfScope ps(s, AMG_K_STRENGTH, rows + 6.0 * nz + 9.0 * gn, k);
         if (gwide) k_pmis_init_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
         else if (gavg >= 12.0) k_pmis_init_g<8><<<gg8, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
         else k_pmis_init<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
@@ -1175,13 +1457,13 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
         AMG_CUDA(cudaMemsetAsync(fl.d + 6, 0, 2 * sizeof(int), s));
         for (int sub = 0; sub < 2; ++sub) {
           {
-            ProfScope ps(s, AMG_K_PMIS, rows + 6.0 * nz + 10.0 * gn);
+            ProfScope ps(s, AMG_K_PMIS, rows + 6.0 * nz + 10.0 * gn, k);
             if (gwide) k_pmis_select_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, st1.p);
             else k_pmis_select<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, st1.p);
             AMG_CHECK_LAUNCH();
           }
           {
-            ProfScope ps(s, AMG_K_PMIS, rows + 5.0 * nz + 2.0 * gn);
+            ProfScope ps(s, AMG_K_PMIS, rows + 5.0 * nz + 2.0 * gn, k);
             if (gwide) k_pmis_update_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, st1.p, st0.p, fl.d + 6 + sub);
             else k_pmis_update<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, st1.p, st0.p, fl.d + 6 + sub);
             AMG_CHECK_LAUNCH();
@@ -1194,7 +1476,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       L.cf = m.get_n<int8_t>(n);
       Buf<int> isC(m, n);
       {
-        ProfScope ps(s, AMG_K_PMIS, 6.0 * n);
+        ProfScope ps(s, AMG_K_PMIS, 6.0 * n, k);
         if (bs == 1) k_cf_out<<<g, TPB, 0, s>>>(n, st0.p, L.cf, isC.p);
         else k_cf_expand<<<gg, TPB, 0, s>>>(gn, bs, st0.p, L.cf, isC.p);
         AMG_CHECK_LAUNCH();
@@ -1213,7 +1495,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       h->L = m.get_n<double>((size_t)n * n);
       AMG_CUDA(cudaMemsetAsync(h->L, 0, sizeof(double) * (size_t)n * n, s));
       {
-        ProfScope ps(s, AMG_K_SETUP_OTHER, 4.0 * (n + 1) + 12.0 * A.nnz + 16.0 * (double)n * n);
+        ProfScope ps(s, AMG_K_SETUP_OTHER, 4.0 * (n + 1) + 12.0 * A.nnz + 16.0 * (double)n * n, k);
         k_to_dense<<<ceil_div(n, TPB), TPB, 0, s>>>(n, A.rp, A.ci, A.v, h->L);
         AMG_CHECK_LAUNCH();
         k_cholesky<<<1, 256, 0, s>>>(n, h->L, fl.d);
@@ -1223,7 +1505,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       if (fl.h[4]) fail(AMG_ERR_NOT_SPD, "dense Cholesky of the last level met a non-positive pivot");
       h->Linv = m.get_n<double>((size_t)n * n);
       {
-        ProfScope ps(s, AMG_K_SETUP_OTHER, 16.0 * (double)n * n);
+        ProfScope ps(s, AMG_K_SETUP_OTHER, 16.0 * (double)n * n, k);
         k_tri_inverse<<<ceil_div(n, 64), 64, 0, s>>>(n, h->L, h->Linv);
         AMG_CHECK_LAUNCH();
       }
@@ -1233,10 +1515,58 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     // interpolation
     const int g = ceil_div(n, TPB);
     DCsr &P = L.P;
-    {
+    if (prm.interp == AMG_INTERP_EXT) {
+      Buf<int> mx(m, 2), eflag(m, 1), pcnt(m, n);
+      AMG_CUDA(cudaMemsetAsync(mx.p, 0, 2 * sizeof(int), s));
+      AMG_CUDA(cudaMemsetAsync(eflag.p, 0, sizeof(int), s));
+      {
+        ProfScope ps(s, AMG_K_INTERP, 8.0 * (n + 1) + 10.0 * A.nnz + 2.0 * n, k);
+        k_strong_c<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, L.cf, pcnt.p);
+        AMG_CHECK_LAUNCH();
+        k_ext_bound<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, L.cf, pcnt.p, mx.p);
+        AMG_CHECK_LAUNCH();
+      }
+      int hmx[2];
+      AMG_CUDA(cudaMemcpyAsync(hmx, mx.p, sizeof(hmx), cudaMemcpyDeviceToHost, s));
+      AMG_CUDA(cudaStreamSynchronize(s));
+      int T = 32;
+      while (T <= hmx[0]) T <<= 1;  // a free slot always remains
+      const size_t per = ext_warp_bytes(T, std::max(hmx[1], 1));
+      const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kExtWarps, (size_t)(200 * 1024) / per));
+      const size_t smem = per * wpb;
+      if (smem > 200 * 1024) fail(AMG_ERR_UNSUPPORTED, "extended+i: a row's interpolatory candidates exceed the shared-memory set");
+      static std::atomic<unsigned long long> attr_c{0}, attr_f{0};
+      ensure_smem_attr(k_ext_interp<false>, 200 * 1024, attr_c);
+      ensure_smem_attr(k_ext_interp<true>, 200 * 1024, attr_f);
+      const int grid = std::max(1, std::min(ceil_div(n, wpb), kNumSMs * 16));
+      {
+        ProfScope ps(s, AMG_K_INTERP, 4.0 * (n + 1) + 5.0 * A.nnz + 5.0 * n, k);
+        k_ext_interp<false><<<grid, wpb * 32, smem, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, T,
+                                                                std::max(hmx[1], 1), pcnt.p, nullptr, nullptr,
+                                                                nullptr, eflag.p);
+        AMG_CHECK_LAUNCH();
+      }
+      P.n = n;
+      P.ncols = nc;
+      P.rp = m.get_n<int>((size_t)n + 1);
+      P.nnz = scan_counts(m, pcnt.p, P.rp, n);
+      P.ci = m.get_n<int>(std::max<int64_t>(P.nnz, 1));
+      P.v = m.get_n<double>(std::max<int64_t>(P.nnz, 1));
+      {
+        ProfScope ps(s, AMG_K_INTERP, 8.0 * (n + 1) + 13.0 * A.nnz + 5.0 * n + 12.0 * P.nnz, k);
+        k_ext_interp<true><<<grid, wpb * 32, smem, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, T,
+                                                               std::max(hmx[1], 1), nullptr, P.rp, P.ci, P.v,
+                                                               eflag.p);
+        AMG_CHECK_LAUNCH();
+      }
+      int he = 0;
+      AMG_CUDA(cudaMemcpyAsync(&he, eflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+      AMG_CUDA(cudaStreamSynchronize(s));
+      if (he) fail(AMG_ERR_SETUP, "extended+i: an F row's modified diagonal is zero");
+    } else {
       Buf<int> pcnt(m, n);
       {
-        ProfScope ps(s, AMG_K_INTERP, 4.0 * (n + 1) + 5.0 * A.nnz + 5.0 * n);
+        ProfScope ps(s, AMG_K_INTERP, 4.0 * (n + 1) + 5.0 * A.nnz + 5.0 * n, k);
         if (wide) k_interp_count_w<<<gw, TPB, 0, s>>>(n, A.rp, A.ci, S.p, L.cf, pcnt.p);
         else k_interp_count<<<g, TPB, 0, s>>>(n, A.rp, A.ci, S.p, L.cf, pcnt.p);
         AMG_CHECK_LAUNCH();
@@ -1248,7 +1578,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       P.ci = m.get_n<int>(std::max<int64_t>(P.nnz, 1));
       P.v = m.get_n<double>(std::max<int64_t>(P.nnz, 1));
       {
-        ProfScope ps(s, AMG_K_INTERP, 8.0 * (n + 1) + 13.0 * A.nnz + 5.0 * n + 12.0 * P.nnz);
+        ProfScope ps(s, AMG_K_INTERP, 8.0 * (n + 1) + 13.0 * A.nnz + 5.0 * n + 12.0 * P.nnz, k);
         if (wide_interp)
           k_interp_fill_w<<<gw, TPB, 0, s>>>(n, prm.block_size, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, P.rp, P.ci, P.v);
         else
@@ -1260,9 +1590,12 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     ST.reset();
     cidx.reset();
     transpose(m, P, nc, L.R);
-    DCsr AP;
-    spgemm(m, fl.d, A, P, nc, AP);
-    spgemm(m, fl.d, L.R, AP, nc, h->lev[k + 1].A);
+    DCsr AP;  // A P stays in the product's slot form; R (A P) reads it so
+    {
+      SlotRows ap;
+      spgemm(m, fl.d, A, P, nullptr, nc, AP, k, &ap);
+      spgemm(m, fl.d, L.R, AP, &ap, nc, h->lev[k + 1].A, k, nullptr);
+    }
     free_csr(m, AP);
     // the SpGEMM's overflow flag is read with the next level's first flag
     // read (every level reads its flags at least once), not with a sync here

@@ -10,6 +10,11 @@
 //   t_k = s_k + P_k z_{k+1}           OpProlong  (prolongation + correction)
 //   z_k = t_k + wd_k .* (y_k - A_k t_k)   OpJacobi (level 0: OpPost0, fused with the CG dots)
 // nu1 > 1 or nu2 > 1 adds plain Jacobi sweeps; nu = 0 drops them.
+// With the FSAI smoother (M^-1 = G^T G, Eq. smo) a smoothing step
+// s <- s + omega G^T G (y - A s) is three products: w = y - A s (OpResid),
+// u = G w and s += (omega G^T) u (OpGemv); the pre-smoothing step from zero
+// is u = G y, s = (omega G^T) u, and level 0's last post-smoothing product
+// carries the CG bookkeeping (OpPost0 with the G^T product).
 //
 // FP64 arithmetic on this part runs at ~1.2 TFLOP/s (about 2 DFMA lanes per
 // clock per SM), so FP64 issue slots, not HBM bandwidth, bind the FP64 solve:
@@ -467,6 +472,23 @@ struct OpProlong {
   __device__ void finish(Acc<1> &) const {}
 };
 
+// out = M x (+ base when BASE): the FSAI products u = G w and s = base + omega G^T u
+template <typename TT, bool BASE>
+struct OpGemv {
+  using T = TT;
+  static constexpr int NV = 0;
+  static constexpr bool kMatrix = true, kNeg = false;
+  const T *mv, *x, *base;
+  T *dst;
+  const int *done;
+  __device__ bool skip() const { return *done; }
+  __device__ T mat(int k) const { return ld(mv + k); }
+  __device__ T vec(int c) const { return ld(x + c); }
+  __device__ T init(int) const { return T(0); }
+  __device__ void out(int i, T sum, Acc<1> &) const { dst[i] = BASE ? base[i] + sum : sum; }
+  __device__ void finish(Acc<1> &) const {}
+};
+
 // z = t + wd .* (y - A t)
 template <typename TT>
 struct OpJacobi {
@@ -487,16 +509,19 @@ struct OpJacobi {
 enum Post0Mode { POST_APPLY = 0, POST_FIRST = 1, POST_ITER = 2 };
 
 // Level-0 post-smoothing fused with the CG bookkeeping:
-//   z = t + wd .* (y - A t) (SWEEP) or z = t, written in FP64;
+//   z = t + wd .* (y - A t) (KIND = POST_JACOBI), z = t + (omega G^T) u
+//   (POST_FSAI, a = omega G^T's values, u = G (y - A t)) or z = t
+//   (POST_NONE), written in FP64;
 //   APPLY: nothing else; FIRST: rho = (r, z), p = z;
 //   ITER:  beta = (z, r) / rho (standard) or -alpha (z, q) / rho (flexible:
 //          (z_{k+1}, r_{k+1} - r_k) with r_{k+1} - r_k = -alpha q_k), rho = (r, z).
-template <typename TT, bool SWEEP>
+enum Post0Kind { POST_NONE = 0, POST_JACOBI = 1, POST_FSAI = 2 };
+template <typename TT, int KIND>
 struct OpPost0 {
   using T = TT;
   static constexpr int NV = 2;
-  static constexpr bool kMatrix = SWEEP, kNeg = SWEEP;
-  const T *a, *wd, *y, *t;
+  static constexpr bool kMatrix = KIND != POST_NONE, kNeg = KIND == POST_JACOBI;
+  const T *a, *wd, *y, *t, *u;
   double *z;
   const double *r, *q;
   double *p;
@@ -507,10 +532,10 @@ struct OpPost0 {
   unsigned int *counter;
   __device__ bool skip() const { return *done; }
   __device__ T mat(int k) const { return ld(a + k); }
-  __device__ T vec(int c) const { return ld(t + c); }
+  __device__ T vec(int c) const { return KIND == POST_FSAI ? ld(u + c) : ld(t + c); }
   __device__ T init(int i) const { return y[i]; }
   __device__ void out(int i, T res, Acc<NV> &acc) const {
-    const T zi = SWEEP ? fma(wd[i], res, t[i]) : t[i];
+    const T zi = KIND == POST_JACOBI ? fma(wd[i], res, t[i]) : KIND == POST_FSAI ? t[i] + res : t[i];
     const double zd = static_cast<double>(zi);
     z[i] = zd;
     if (mode != POST_APPLY) {
@@ -743,6 +768,29 @@ __global__ void k_dop_gemm(int m, int k, int ncol, const double *__restrict__ M,
   out[t] = acc;
 }
 
+// out = base + M V: M m x k, V k x ncol, base and out m x ncol (row-major).
+__global__ void k_dop_gemm_add(int m, int k, int ncol, const double *__restrict__ M, const double *__restrict__ V,
+                               const double *__restrict__ base, double *__restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * ncol) return;
+  const int i = (int)(t / ncol), c = (int)(t % ncol);
+  double acc = 0.0;
+  for (int j = 0; j < k; ++j) acc = fma(M[(size_t)i * k + j], V[(size_t)j * ncol + c], acc);
+  out[t] = base[t] + acc;
+}
+
+// out = the CSR matrix (n x n) as a dense row-major array.
+__global__ void k_dop_csr_dense(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                const double *__restrict__ v, double *__restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int i = (int)(t / n), c = (int)(t % n);
+  double x = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] == c) x = v[p];
+  out[t] = x;
+}
+
 // M = Li^T Li for the lower-triangular Li = L^-1 (n x n row-major).
 __global__ void k_dop_coarse(int n, const double *__restrict__ Li, double *__restrict__ M) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -955,6 +1003,41 @@ void jacobi_sweep(amg_hierarchy *h, int k, const T *y, const T *t, T *z, const i
   launch_mat(A, A.map, op, h->mem.stream);
 }
 
+// out = y - A_k s (a residual outside the pre-smoothed one; profiled as `kind`)
+template <typename T>
+void residual(amg_hierarchy *h, int k, const T *y, const T *sv, T *out, const int *done, int kind) {
+  const DCsr &A = h->lev[k].A;
+  const double bt = sizeof(T);
+  ProfScope ps(h->mem.stream, kind, (idx_bytes + bt) * (double)A.nnz + 4.0 * (A.n + 1) + 3.0 * bt * A.n, k);
+  OpResid<T> op{avals<T>(A), sv, y, out, done};
+  launch_mat(A, A.map, op, h->mem.stream);
+}
+
+// FSAI halves of a smoothing step: u = G w, and out = base + (omega G^T) u
+template <typename T>
+void fsai_g(amg_hierarchy *h, int k, const T *w, T *u, const int *done) {
+  const DCsr &G = h->lev[k].G;
+  const double bt = sizeof(T);
+  ProfScope ps(h->mem.stream, AMG_K_SMOOTH_FSAI, (idx_bytes + bt) * (double)G.nnz + 4.0 * (G.n + 1) + 2.0 * bt * G.n, k);
+  OpGemv<T, false> op{avals<T>(G), w, nullptr, u, done};
+  launch_mat(G, G.map, op, h->mem.stream);
+}
+
+template <typename T>
+void fsai_gt(amg_hierarchy *h, int k, const T *u, const T *base, T *out, const int *done) {
+  const DCsr &GT = h->lev[k].GT;
+  const double bt = sizeof(T);
+  ProfScope ps(h->mem.stream, AMG_K_SMOOTH_FSAI,
+               (idx_bytes + bt) * (double)GT.nnz + 4.0 * (GT.n + 1) + (base ? 3.0 : 2.0) * bt * GT.n, k);
+  if (base) {
+    OpGemv<T, true> op{avals<T>(GT), u, base, out, done};
+    launch_mat(GT, GT.map, op, h->mem.stream);
+  } else {
+    OpGemv<T, false> op{avals<T>(GT), u, nullptr, out, done};
+    launch_mat(GT, GT.map, op, h->mem.stream);
+  }
+}
+
 template <typename T>
 void coarse_solve(amg_hierarchy *h, int n, const T *y, T *z, const int *done) {
   cudaStream_t s = h->mem.stream;
@@ -985,10 +1068,23 @@ void cycle_level(amg_hierarchy *h, int k, const CycleCtx &cc) {
     return;
   }
   const amg_params &prm = h->prm;
+  const bool fsai = prm.smoother == AMG_SMOOTH_FSAI;
   T *y = vec<T>(L.y), *sv = vec<T>(L.s), *r = vec<T>(L.r), *w = vec<T>(L.w);
-  for (int it = 1; it < prm.nu1; ++it) {  // extra pre-smoothing sweeps
-    jacobi_sweep<T>(h, k, y, sv, w, cc.done, AMG_K_SOLVE_OTHER);
-    std::swap(sv, w);
+  if (fsai) {
+    if (prm.nu1 > 0) {  // s = omega G^T G y (from s = 0), then further steps in place
+      fsai_g<T>(h, k, y, w, cc.done);
+      fsai_gt<T>(h, k, w, nullptr, sv, cc.done);
+      for (int it = 1; it < prm.nu1; ++it) {
+        residual<T>(h, k, y, sv, r, cc.done, AMG_K_SOLVE_OTHER);
+        fsai_g<T>(h, k, r, w, cc.done);
+        fsai_gt<T>(h, k, w, sv, sv, cc.done);
+      }
+    }  // nu1 = 0: s = 0 was written by the producer of y
+  } else {
+    for (int it = 1; it < prm.nu1; ++it) {  // extra pre-smoothing sweeps
+      jacobi_sweep<T>(h, k, y, sv, w, cc.done, AMG_K_SOLVE_OTHER);
+      std::swap(sv, w);
+    }
   }
   {
     ProfScope ps(s, AMG_K_SMOOTH_RESID, (idx_bytes + bt) * (double)A.nnz + 4.0 * (n + 1) + 3.0 * bt * n, k);
@@ -1003,8 +1099,9 @@ void cycle_level(amg_hierarchy *h, int k, const CycleCtx &cc) {
     const DCsr &R = L.R;
     ProfScope ps(s, AMG_K_RESTRICT, (idx_bytes + bp) * (double)R.nnz + 4.0 * (nc + 1) + bt * n + bt * nc +
                                         (c_last ? 0.0 : 2.0 * bt * nc), k);
-    OpRestrict<T, TP> op{pvals<TP>(R), r, c_last ? nullptr : wdv<T>(C), vec<T>(C.y), vec<T>(C.s),
-                         c_last ? -1 : (prm.nu1 > 0 ? 1 : 0), cc.done};
+    // the coarse level's s: wd .* y (Jacobi), formed by the coarse level itself (FSAI), 0 (nu1 = 0)
+    const int pre = c_last ? -1 : prm.nu1 == 0 ? 0 : fsai ? -1 : 1;
+    OpRestrict<T, TP> op{pvals<TP>(R), r, pre == 1 ? wdv<T>(C) : nullptr, vec<T>(C.y), vec<T>(C.s), pre, cc.done};
     launch_mat(R, R.map, op, s);
   }
   cycle_level<T, TP>(h, k + 1, cc);
@@ -1020,6 +1117,17 @@ void cycle_level(amg_hierarchy *h, int k, const CycleCtx &cc) {
     ProfScope ps(s, AMG_K_SOLVE_OTHER, 2.0 * bt * n, k);
     k_copy<T><<<grid_for(n), TPB, 0, s>>>(n, t, vec<T>(L.z));
     AMG_CHECK_LAUNCH();
+    return;
+  }
+  if (fsai) {  // w = y - A t, u = G w (in s, free after the prolongation), z = t + omega G^T u
+    for (int it = 0; it < prm.nu2; ++it) {
+      const bool lastp = it == prm.nu2 - 1;
+      T *dst = lastp ? vec<T>(L.z) : t;  // in place: out[i] reads only t[i]
+      residual<T>(h, k, y, t, w, cc.done, lastp ? AMG_K_SMOOTH_POST : AMG_K_SOLVE_OTHER);
+      fsai_g<T>(h, k, w, sv, cc.done);
+      fsai_gt<T>(h, k, sv, t, dst, cc.done);
+      t = dst;
+    }
     return;
   }
   for (int it = 0; it < prm.nu2; ++it) {
@@ -1042,6 +1150,7 @@ void vcycle(amg_hierarchy *h, double *z, const CycleCtx &cc) {
   const T *y = vec<T>(L0.y);
   const T *t;
   bool sweep = true;
+  const bool fsai = h->prm.smoother == AMG_SMOOTH_FSAI && h->nlevels > 1;
   if (h->nlevels == 1) {
     coarse_solve<T>(h, n, y, vec<T>(L0.z), cc.done);
     t = vec<T>(L0.z);
@@ -1049,24 +1158,38 @@ void vcycle(amg_hierarchy *h, double *z, const CycleCtx &cc) {
   } else {
     cycle_level<T, TP>(h, 0, cc);
     T *tt = vec<T>(L0.r), *w = vec<T>(L0.w);
-    for (int it = 0; it + 1 < h->prm.nu2; ++it) {  // all but the last post sweep
-      jacobi_sweep<T>(h, 0, y, tt, w, cc.done, AMG_K_SOLVE_OTHER);
-      std::swap(tt, w);
+    if (fsai) {
+      T *u = vec<T>(L0.s);  // free after the prolongation
+      for (int it = 0; it < h->prm.nu2; ++it) {
+        residual<T>(h, 0, y, tt, w, cc.done, it + 1 < h->prm.nu2 ? AMG_K_SOLVE_OTHER : AMG_K_SMOOTH_POST);
+        fsai_g<T>(h, 0, w, u, cc.done);
+        if (it + 1 < h->prm.nu2) fsai_gt<T>(h, 0, u, tt, tt, cc.done);  // all but the last step, in place
+      }
+    } else {
+      for (int it = 0; it + 1 < h->prm.nu2; ++it) {  // all but the last post sweep
+        jacobi_sweep<T>(h, 0, y, tt, w, cc.done, AMG_K_SOLVE_OTHER);
+        std::swap(tt, w);
+      }
     }
     t = tt;
     sweep = h->prm.nu2 > 0;
   }
-  double bytes = 8.0 * n + bt * n;  // z (FP64) write, t read
-  if (sweep) bytes += (idx_bytes + bt) * (double)A.nnz + 4.0 * (n + 1) + 2.0 * bt * n;
+  const DCsr &M = fsai ? L0.GT : A;  // matrix of the last post-smoothing product
+  double bytes = 8.0 * n + bt * n;   // z (FP64) write, t read
+  if (sweep) bytes += (idx_bytes + bt) * (double)M.nnz + 4.0 * (n + 1) + 2.0 * bt * n;
   if (cc.mode != POST_APPLY) bytes += 8.0 * n + (cc.mode == POST_FIRST ? 8.0 * n : (cc.flexible ? 8.0 * n : 0.0));
-  ProfScope ps(s, AMG_K_SMOOTH_POST, bytes, 0);
-  if (sweep) {
-    OpPost0<T, true> op{avals<T>(A), wdv<T>(L0), y, t, z, h->r, h->q, h->p, cc.mode, cc.flexible,
-                        h->sc, cc.done, h->partials, h->counter};
+  ProfScope ps(s, fsai && sweep ? AMG_K_SMOOTH_FSAI : AMG_K_SMOOTH_POST, bytes, 0);
+  if (sweep && fsai) {
+    OpPost0<T, POST_FSAI> op{avals<T>(M), nullptr, y, t, vec<T>(L0.s), z, h->r, h->q, h->p, cc.mode, cc.flexible,
+                             h->sc, cc.done, h->partials, h->counter};
+    launch_mat(M, M.map, op, s);
+  } else if (sweep) {
+    OpPost0<T, POST_JACOBI> op{avals<T>(A), wdv<T>(L0), y, t, nullptr, z, h->r, h->q, h->p, cc.mode, cc.flexible,
+                               h->sc, cc.done, h->partials, h->counter};
     launch_mat(A, A.map, op, s);
   } else {
-    OpPost0<T, false> op{nullptr, wdv<T>(L0), y, t, z, h->r, h->q, h->p, cc.mode, cc.flexible,
-                         h->sc, cc.done, h->partials, h->counter};
+    OpPost0<T, POST_NONE> op{nullptr, wdv<T>(L0), y, t, nullptr, z, h->r, h->q, h->p, cc.mode, cc.flexible,
+                             h->sc, cc.done, h->partials, h->counter};
     launch_rows(RowMap{}, n, A.rp, A.ci, op, s);
   }
 }
@@ -1077,7 +1200,7 @@ void load_y0(amg_hierarchy *h, const double *src) {
   const int n = L0.A.n;
   const bool write_y = !std::is_same<T, double>::value || L0.y != (void *)src;
   k_load_y0<T><<<grid_for(n), TPB, 0, h->mem.stream>>>(n, src, wdv<T>(L0), vec<T>(L0.y), vec<T>(L0.s), write_y,
-                                                        h->prm.nu1 > 0);
+                                                        h->prm.nu1 > 0 && h->prm.smoother == AMG_SMOOTH_JACOBI);
   AMG_CHECK_LAUNCH();
 }
 
@@ -1104,7 +1227,8 @@ int pcg_impl(amg_hierarchy *h, const double *b, double *x, double rtol, int maxi
   T *y0 = vec<T>(L0.y);  // aliases r in FP64 mode
   T *s0 = vec<T>(L0.s);
   const T *wd0 = wdv<T>(L0);
-  const bool pre = h->prm.nu1 > 0;
+  // the pointwise first pre-smoothing step s = wd .* y (Jacobi); FSAI forms s in the cycle
+  const bool pre = h->prm.nu1 > 0 && h->prm.smoother == AMG_SMOOTH_JACOBI;
   const double *a64 = avals<double>(A);
   {
     ProfScope ps(s, AMG_K_SOLVE_OTHER, 12.0 * A.nnz + 4.0 * (n + 1) + 8.0 * 3 * n + (fp64 ? 0 : bt * n) + 2 * bt * n);
@@ -1257,24 +1381,48 @@ void build_dense_tail(amg_hierarchy *h) {
   Buf<double> Mn(m, (size_t)nl * nl);
   k_dop_coarse<<<blocks((int64_t)nl * nl), TPB, 0, s>>>(nl, h->Linv, Mn.p);
   AMG_CHECK_LAUNCH();
+  const bool fsai = prm.smoother == AMG_SMOOTH_FSAI;
   for (int k = Lst - 1; k >= kd; --k) {
     const Level &L = h->lev[k];
     const DCsr &A = L.A, &P = L.P, &R = L.R;
     const int n = A.n, nc = P.ncols;
     const int64_t nn = (int64_t)n * n;
+    // FSAI: the smoothing matrix W = omega G^T G, dense
+    Buf<double> W;
+    if (fsai) {
+      Buf<double> Gd(m, (size_t)nn);
+      k_dop_csr_dense<<<blocks(nn), TPB, 0, s>>>(n, L.G.rp, L.G.ci, L.G.v, Gd.p);
+      AMG_CHECK_LAUNCH();
+      W = Buf<double>(m, (size_t)nn);
+      k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, L.GT.rp, L.GT.ci, L.GT.v, Gd.p, nullptr, nullptr, 0.0, 1.0, W.p);
+      AMG_CHECK_LAUNCH();
+    }
+    // T + W (I - A T): one smoothing sweep applied to the columns of T
+    auto sweep = [&](Buf<double> &T) {
+      Buf<double> T2(m, (size_t)nn);
+      if (fsai) {
+        Buf<double> E(m, (size_t)nn);
+        k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, A.rp, A.ci, A.v, T.p, nullptr, nullptr, 1.0, -1.0, E.p);
+        AMG_CHECK_LAUNCH();
+        k_dop_gemm_add<<<blocks(nn), TPB, 0, s>>>(n, n, n, W.p, E.p, T.p, T2.p);
+        AMG_CHECK_LAUNCH();
+      } else {
+        k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, A.rp, A.ci, A.v, T.p, T.p, L.wd, 1.0, -1.0, T2.p);
+        AMG_CHECK_LAUNCH();
+      }
+      std::swap(T, T2);
+    };
     // X: the pre-smoothing sweeps applied to the identity
-    Buf<double> X, Xt;
+    Buf<double> X;
     if (prm.nu1 > 0) {
       X = Buf<double>(m, (size_t)nn);
-      k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, A.rp, A.ci, A.v, nullptr, nullptr, L.wd, 1.0, -1.0, X.p);
-      AMG_CHECK_LAUNCH();
-      for (int j = 1; j < prm.nu1; ++j) {
-        Xt = Buf<double>(m, (size_t)nn);
-        k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, A.rp, A.ci, A.v, X.p, X.p, L.wd, 1.0, -1.0, Xt.p);
+      if (fsai) {
+        AMG_CUDA(cudaMemcpyAsync(X.p, W.p, sizeof(double) * (size_t)nn, cudaMemcpyDeviceToDevice, s));
+      } else {
+        k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, A.rp, A.ci, A.v, nullptr, nullptr, L.wd, 1.0, -1.0, X.p);
         AMG_CHECK_LAUNCH();
-        std::swap(X, Xt);
-        Xt.reset();
       }
+      for (int j = 1; j < prm.nu1; ++j) sweep(X);
     }
     Buf<double> E(m, (size_t)nn);  // I - A X
     k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, A.rp, A.ci, A.v, X.p, nullptr, nullptr, 1.0, -1.0, E.p);
@@ -1293,12 +1441,7 @@ void build_dense_tail(amg_hierarchy *h) {
     AMG_CHECK_LAUNCH();
     U.reset();
     X.reset();
-    for (int j = 0; j < prm.nu2; ++j) {  // post-smoothing sweeps
-      Buf<double> T2(m, (size_t)nn);
-      k_dop_sparse<<<blocks(nn), TPB, 0, s>>>(n, n, A.rp, A.ci, A.v, T.p, T.p, L.wd, 1.0, -1.0, T2.p);
-      AMG_CHECK_LAUNCH();
-      std::swap(T, T2);
-    }
+    for (int j = 0; j < prm.nu2; ++j) sweep(T);  // post-smoothing sweeps
     Mn = std::move(T);
   }
   h->dense_op = Mn.release();
@@ -1358,6 +1501,20 @@ void prepare_solve(amg_hierarchy *h) {
     if (!last) {
       if (L.P.n >= kSellMinRows) build_sell(m, L.P, fp64, prec == AMG_PREC_FP32, prec == AMG_PREC_FP32_BF16PR);
       if (L.R.n >= kSellMinRows) build_sell(m, L.R, fp64, prec == AMG_PREC_FP32, prec == AMG_PREC_FP32_BF16PR);
+    }
+    if (!last && h->prm.smoother == AMG_SMOOTH_FSAI) {  // G and omega G^T, stored like A
+      build_fsai(h, k);
+      for (DCsr *M : {&L.G, &L.GT}) {
+        M->map = choose_map(M->nnz, M->n, fp64);
+        M->map64 = choose_map(M->nnz, M->n, true);
+        if (!fp64) {
+          M->v32 = m.get_n<float>(std::max<int64_t>(M->nnz, 1));
+          ProfScope ps(s, AMG_K_FSAI, 12.0 * M->nnz, k);
+          k_to_f32<<<grid_for(M->nnz), TPB, 0, s>>>(M->nnz, M->v, M->v32);
+          AMG_CHECK_LAUNCH();
+        }
+        if (n >= kSellMinRows) build_sell(m, *M, fp64, !fp64, false);
+      }
     }
   }
   // CG vectors (FP64) and scalars

@@ -9,10 +9,10 @@
 //
 // One numeric pass.  Each row i gets ub_i = sum_{p in X_i} nnz(Y_{k_p})
 // slots of scratch (an upper bound on its distinct columns); the row's sorted
-// columns and sums are written there with their count, and a compaction copies
-// the rows into the final CSR.  Rows are binned by ub_i into tiers, each a
-// stable (row-ordered) list so that neighbouring warps work on neighbouring
-// rows:
+// columns and sums are written there with their count.  A P stays in that
+// slot form (row i at off[i], cnt[i] entries) and is read so by R (A P); the
+// coarse operator is compacted into CSR.  Rows are binned by ub_i into tiers
+// (lists filled tile by tile, so neighbouring warps work on neighbouring rows):
 //   tier 0    ub <= 32     a warp per row, one candidate product per lane in
 //                          registers; duplicates found with __match_any_sync,
 //                          each group summed by its lowest lane in lane order
@@ -25,6 +25,9 @@
 //   tier 7    larger       a block per row, table in a global scratch slice;
 //   tier 8    X row <= 8 entries and ub <= 64 (taken first): a thread per
 //                          row merging the row's sorted Y rows.
+// (A thread-per-row variant with a private accumulator in shared memory for
+// every short row was bit-exact but twice as slow over a 128^3 set-up: its
+// lanes gather Y entries of 32 different rows at once, uncoalesced.)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -79,13 +82,28 @@ __device__ __forceinline__ int next_pow2(int v) {
   return p;
 }
 
+
+// Rows of the right operand Y: [rp[k], rp[k] + cnt[k]) in slot form (cnt set),
+// else [rp[k], rp[k + 1]).
+struct YRows {
+  const int *rp, *cnt;
+  __device__ __forceinline__ int b(int k) const { return rp[k]; }
+  __device__ __forceinline__ int e(int k) const { return cnt ? rp[k] + cnt[k] : rp[k + 1]; }
+};
+
 // ------------------------------------------------------------- binning ----
 // ub_i = sum over the entries p of X row i of nnz(Y_{k_p}), G lanes per row
 // (G = 1 for short X rows, up to 32 for long ones: the coarse levels' rows are
-// long and few, and a thread walking a whole row left most SMs idle).
+// long and few, and a thread walking a whole row left most SMs idle); the
+// row's tier; per-tier row counts (block-aggregated) and the largest ub of
+// the global tier in tcount[NTIER].
 template <int G>
 __global__ void __launch_bounds__(TPB) k_row_ub(int m, const int *__restrict__ xrp, const int *__restrict__ xci,
-                                                const int *__restrict__ yrp, int *__restrict__ ub_out, int *flags) {
+                                                YRows y, int *__restrict__ ub_out, int8_t *__restrict__ tier,
+                                                int *__restrict__ tcount, int *flags) {
+  __shared__ int cnt[NTIER];
+  if (threadIdx.x < NTIER) cnt[threadIdx.x] = 0;
+  __syncthreads();
   constexpr int RPW = 32 / G;  // rows per warp step
   const int lane = threadIdx.x & 31, sub = lane & (G - 1), grp = lane / G;
   const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5, nw = (gridDim.x * TPB) >> 5;
@@ -95,7 +113,7 @@ __global__ void __launch_bounds__(TPB) k_row_ub(int m, const int *__restrict__ x
     if (i < m)
       for (int p = xrp[i] + sub; p < xrp[i + 1]; p += G) {
         const int k = xci[p];
-        ub += yrp[k + 1] - yrp[k];
+        ub += y.e(k) - y.b(k);
       }
 #pragma unroll
     for (int o = G / 2; o >= 1; o >>= 1) ub += __shfl_xor_sync(FULL, ub, o);
@@ -105,73 +123,37 @@ __global__ void __launch_bounds__(TPB) k_row_ub(int m, const int *__restrict__ x
         ub = 1 << 30;
       }
       ub_out[i] = (int)ub;
+      const int t = tier_of(ub, xrp[i + 1] - xrp[i]);
+      tier[i] = (int8_t)t;
+      atomicAdd(&cnt[t], 1);
+      if (t == T_GLOBAL) atomicMax(&tcount[NTIER], (int)ub);
     }
   }
+  __syncthreads();
+  if (threadIdx.x < NTIER && cnt[threadIdx.x]) atomicAdd(&tcount[threadIdx.x], cnt[threadIdx.x]);
 }
 
-// Tier of each row (from its ub and X row length); per-tile tier counts;
-// largest ub of the global tier.
-__global__ void __launch_bounds__(TPB) k_bin_rows(int m, const int *__restrict__ xrp, const int *__restrict__ ub_in,
-                                                  int8_t *__restrict__ tier, int *__restrict__ tile_cnt,
-                                                  int *__restrict__ max_ub) {
-  __shared__ int cnt[NTIER];
-  if (threadIdx.x < NTIER) cnt[threadIdx.x] = 0;
-  __syncthreads();
-  for (int t = threadIdx.x; t < TILE; t += TPB) {
-    const int i = blockIdx.x * TILE + t;
-    if (i >= m) break;
-    const int ub = ub_in[i];
-    const int c = tier_of(ub, xrp[i + 1] - xrp[i]);
-    tier[i] = (int8_t)c;
-    atomicAdd(&cnt[c], 1);
-    if (c == T_GLOBAL) atomicMax(max_ub, ub);
-  }
-  __syncthreads();
-  if (threadIdx.x < NTIER) tile_cnt[blockIdx.x * NTIER + threadIdx.x] = cnt[threadIdx.x];
-}
-
-// Exclusive offsets of every (tile, tier) pair in the concatenated tier
-// lists (tier-major, tiles in order); totals[t] = rows in tier t.
-__global__ void k_tier_offsets(int ntiles, const int *__restrict__ tile_cnt, int *__restrict__ tile_off,
-                               int *__restrict__ totals) {
-  __shared__ int base;
-  if (threadIdx.x == 0) base = 0;
-  __syncthreads();
-  for (int t = 0; t < NTIER; ++t) {
-    // serial over tiles in chunks: one thread per tile chunk would need a
-    // scan; tile counts are few (n / 1024), a block-wide scan per chunk
-    __shared__ int chunk[TPB];
-    int carry = 0;
-    for (int c0 = 0; c0 < ntiles; c0 += TPB) {
-      const int j = c0 + threadIdx.x;
-      const int v = j < ntiles ? tile_cnt[j * NTIER + t] : 0;
-      chunk[threadIdx.x] = v;
-      __syncthreads();
-      for (int d = 1; d < TPB; d <<= 1) {  // inclusive Hillis-Steele scan
-        const int add = threadIdx.x >= d ? chunk[threadIdx.x - d] : 0;
-        __syncthreads();
-        chunk[threadIdx.x] += add;
-        __syncthreads();
-      }
-      if (j < ntiles) tile_off[j * NTIER + t] = base + carry + chunk[threadIdx.x] - v;
-      carry += chunk[TPB - 1];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      totals[t] = carry;
-      base += carry;
-    }
-    __syncthreads();
-  }
-}
-
-// Writes each row to its tier's list at its stable (row-ordered) position.
+// Appends each row to its tier's list: tiles of TILE consecutive rows reserve a
+// range of each list with one atomic per (tile, tier) and fill it in row order,
+// so neighbouring rows stay together (the order affects speed only: a row's
+// output position comes from its own offset).
 __global__ void __launch_bounds__(TPB) k_tier_scatter(int m, const int8_t *__restrict__ tier,
-                                                      const int *__restrict__ tile_off, int *__restrict__ lists) {
+                                                      const int *__restrict__ start, int *__restrict__ cursor,
+                                                      int *__restrict__ lists) {
   __shared__ int run[NTIER];
   __shared__ int wcnt[NTIER][WARPS];
+  __shared__ int tot[NTIER];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x < NTIER) run[threadIdx.x] = tile_off[blockIdx.x * NTIER + threadIdx.x];
+  if (threadIdx.x < NTIER) tot[threadIdx.x] = 0;
+  __syncthreads();
+  for (int t0 = 0; t0 < TILE; t0 += TPB) {
+    const int i = blockIdx.x * TILE + t0 + threadIdx.x;
+    if (i < m) atomicAdd(&tot[tier[i]], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < NTIER) run[threadIdx.x] = tot[threadIdx.x] ? start[threadIdx.x] +
+                                                                 atomicAdd(&cursor[threadIdx.x], tot[threadIdx.x])
+                                                               : 0;
   __syncthreads();
   for (int t0 = 0; t0 < TILE; t0 += TPB) {
     const int i = blockIdx.x * TILE + t0 + threadIdx.x;
@@ -208,13 +190,13 @@ struct XChunk {
 };
 
 __device__ __forceinline__ XChunk x_chunk(int c0, int xe, const int *__restrict__ xci, const double *__restrict__ xv,
-                                          const int *__restrict__ yrp, int lane, int *total) {
+                                          const YRows &y, int lane, int *total) {
   XChunk c{0, 0, 0, 0.0};
   const int p = c0 + lane;
   if (p < xe) {
     const int k = xci[p];
-    c.ys = yrp[k];
-    c.len = yrp[k + 1] - c.ys;
+    c.ys = y.b(k);
+    c.len = y.e(k) - c.ys;
     c.xv = xv[p];
   }
   int incl = c.len;
@@ -253,7 +235,7 @@ __device__ __forceinline__ int x_source(const XChunk &c, int u) {
 // pipe busy for ~2 products per output on the 128^3 Poisson A P).
 __global__ void __launch_bounds__(TPB) k_spgemm_merge(const int *__restrict__ rows, int nrows,
                                                       const int *__restrict__ xrp, const int *__restrict__ xci,
-                                                      const double *__restrict__ xv, const int *__restrict__ yrp,
+                                                      const double *__restrict__ xv, YRows y,
                                                       const int *__restrict__ yci, const double *__restrict__ yv,
                                                       const int *__restrict__ off, int *__restrict__ tci,
                                                       double *__restrict__ tcv, int *__restrict__ cnt) {
@@ -270,8 +252,8 @@ __global__ void __launch_bounds__(TPB) k_spgemm_merge(const int *__restrict__ ro
       if (t < len) {
         const int k = xci[xb + t];
         xa[t] = xv[xb + t];
-        hp[t] = yrp[k];
-        he[t] = yrp[k + 1];
+        hp[t] = y.b(k);
+        he[t] = y.e(k);
         if (hp[t] < he[t]) hc[t] = yci[hp[t]];
       }
     }
@@ -328,7 +310,7 @@ __global__ void __launch_bounds__(TPB) k_spgemm_merge(const int *__restrict__ ro
 // ---------------------------------------------------------- tier 0 ----
 __global__ void __launch_bounds__(TPB) k_spgemm_reg(const int *__restrict__ rows, int nrows,
                                                     const int *__restrict__ xrp, const int *__restrict__ xci,
-                                                    const double *__restrict__ xv, const int *__restrict__ yrp,
+                                                    const double *__restrict__ xv, YRows y,
                                                     const int *__restrict__ yci, const double *__restrict__ yv,
                                                     const int *__restrict__ off, int *__restrict__ tci,
                                                     double *__restrict__ tcv, int *__restrict__ cnt) {
@@ -342,7 +324,7 @@ __global__ void __launch_bounds__(TPB) k_spgemm_reg(const int *__restrict__ rows
     int o = 0;  // products placed so far (ub <= 32, so product t sits in lane t)
     for (int c0 = xb; c0 < xe; c0 += 32) {
       int total;
-      const XChunk c = x_chunk(c0, xe, xci, xv, yrp, lane, &total);
+      const XChunk c = x_chunk(c0, xe, xci, xv, y, lane, &total);
       const int u = lane - o;
       const int src = x_source(c, u < 0 ? 0 : u);
       const int ys = __shfl_sync(FULL, c.ys, src), ex = __shfl_sync(FULL, c.excl, src);
@@ -393,7 +375,7 @@ __global__ void __launch_bounds__(TPB) k_spgemm_reg(const int *__restrict__ rows
 template <int TAB>
 __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ rows, int nrows,
                                                      const int *__restrict__ xrp, const int *__restrict__ xci,
-                                                     const double *__restrict__ xv, const int *__restrict__ yrp,
+                                                     const double *__restrict__ xv, YRows y,
                                                      const int *__restrict__ yci, const double *__restrict__ yv,
                                                      const int *__restrict__ off, int *__restrict__ tci,
                                                      double *__restrict__ tcv, int *__restrict__ cnt, int *flags) {
@@ -414,7 +396,7 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
     int nprod = 0;
     for (int c0 = xb; c0 < xe; c0 += 32) {
       int total;
-      const XChunk c = x_chunk(c0, xe, xci, xv, yrp, lane, &total);
+      const XChunk c = x_chunk(c0, xe, xci, xv, y, lane, &total);
       for (int u0 = 0; u0 < total; u0 += 32) {
         const int u = u0 + lane;
         const int src = x_source(c, u);
@@ -493,7 +475,7 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
 template <bool GLOBAL>
 __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ rows, int nrows,
                                                       const int *__restrict__ xrp, const int *__restrict__ xci,
-                                                      const double *__restrict__ xv, const int *__restrict__ yrp,
+                                                      const double *__restrict__ xv, YRows y,
                                                       const int *__restrict__ yci, const double *__restrict__ yv,
                                                       const int *__restrict__ off, int *__restrict__ tci,
                                                       double *__restrict__ tcv, int *__restrict__ cnt, int *flags,
@@ -512,7 +494,7 @@ __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ ro
     const int xb = xrp[i], xe = xrp[i + 1];
     for (int p = xb; p < xe; ++p) {
       const int k = xci[p];
-      for (int q = yrp[k] + threadIdx.x; q < yrp[k + 1]; q += blockDim.x) hash_insert(table, cap - 1, yci[q], flags);
+      for (int q = y.b(k) + threadIdx.x; q < y.e(k); q += blockDim.x) hash_insert(table, cap - 1, yci[q], flags);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < cap; t += blockDim.x) {
@@ -543,7 +525,7 @@ __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ ro
     for (int p = xb; p < xe; ++p) {
       const int k = xci[p];
       const double x = xv[p];
-      for (int q = yrp[k] + threadIdx.x; q < yrp[k + 1]; q += blockDim.x) {
+      for (int q = y.b(k) + threadIdx.x; q < y.e(k); q += blockDim.x) {
         const int pos = lower_bound(keys, count, yci[q]);
         acc[pos] = __dadd_rn(acc[pos], __dmul_rn(x, yv[q]));
       }
@@ -577,6 +559,15 @@ __global__ void __launch_bounds__(TPB) k_compact(int m, const int *__restrict__ 
   }
 }
 
+// Sum of the per-row counts (the entries of a product left in slot form).
+__global__ void k_sum_counts(int m, const int *__restrict__ cnt, long long *total) {
+  long long s = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) s += cnt[i];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(reinterpret_cast<unsigned long long *>(total), (unsigned long long)s);
+}
+
 template <int TAB>
 constexpr size_t hash_smem() {
   return (size_t)WARPS * 3 * TAB * sizeof(int);
@@ -584,7 +575,10 @@ constexpr size_t hash_smem() {
 constexpr size_t block_smem = (size_t)(BTAB + BTAB / 2) * sizeof(int);
 
 struct Args {
-  const DCsr *X, *Y;
+  const DCsr *X;
+  YRows y;
+  const int *yci;
+  const double *yv;
   const int *off;
   int *tci;
   double *tcv;
@@ -597,56 +591,56 @@ void launch_hash(int nr, const int *list, const Args &a) {
   static std::atomic<unsigned long long> attr{0};
   ensure_smem_attr(k_spgemm_hash<TAB>, (int)hash_smem<TAB>(), attr);
   const int grid = std::max(1, std::min(ceil_div(nr, WARPS), kNumSMs * 32));
-  k_spgemm_hash<TAB><<<grid, TPB, hash_smem<TAB>(), a.s>>>(list, nr, a.X->rp, a.X->ci, a.X->v, a.Y->rp, a.Y->ci,
-                                                           a.Y->v, a.off, a.tci, a.tcv, a.cnt, a.flags);
+  k_spgemm_hash<TAB><<<grid, TPB, hash_smem<TAB>(), a.s>>>(list, nr, a.X->rp, a.X->ci, a.X->v, a.y, a.yci, a.yv,
+                                                           a.off, a.tci, a.tcv, a.cnt, a.flags);
   AMG_CHECK_LAUNCH();
 }
 
 }  // namespace
 
-void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C) {
+void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, const SlotRows *yslot, int ncols, DCsr &C, int level,
+            SlotRows *cslot) {
   cudaStream_t s = m.stream;
   const int rows = X.n;
   const int ntiles = ceil_div(rows, TILE);
-  Buf<int> ub(m, (size_t)rows + 1), off(m, (size_t)rows + 1), lists(m, (size_t)rows);
-  Buf<int8_t> tier(m, (size_t)rows);
-  Buf<int> tile_cnt(m, (size_t)ntiles * NTIER), tile_off(m, (size_t)ntiles * NTIER);
-  Buf<int> meta(m, NTIER + 1);  // per-tier row counts, max ub of the last tier
-  AMG_CUDA(cudaMemsetAsync(meta.p, 0, sizeof(int) * (NTIER + 1), s));
-  // Algorithmic bytes of C = X Y: X and Y read once, C written once (CSR with
-  // int32 indices and FP64 values).  The row bounds, tier lists, scratch rows
-  // and the compaction's re-read are this implementation's overhead, not part
-  // of the product, so the binning scope carries no bytes, the numeric pass X
-  // and Y, and the compaction C.
-  const double xy_bytes = 4.0 * (rows + 1) + 12.0 * X.nnz + 4.0 * (Y.n + 1) + 12.0 * Y.nnz;
+  const YRows y{Y.rp, yslot ? yslot->cnt.p : nullptr};
+  Buf<int> ub(m, (size_t)rows + 1), off(m, (size_t)rows + 1), lists(m, (size_t)std::max(rows, 1));
+  Buf<int8_t> tier(m, (size_t)std::max(rows, 1));
+  Buf<int> meta(m, 2 * NTIER + 1);  // per-tier row counts, max ub of the global tier, list cursors
+  AMG_CUDA(cudaMemsetAsync(meta.p, 0, sizeof(int) * (2 * NTIER + 1), s));
   {
-    ProfScope ps(s, AMG_K_SPGEMM, 0.0);
+    ProfScope ps(s, AMG_K_SPGEMM, 0.0, level);  // bookkeeping: no algorithmic bytes
     const double xavg = rows ? (double)X.nnz / rows : 0.0;
     const int G = xavg <= 8.0 ? 1 : xavg <= 24.0 ? 8 : 32;
     const int grid = std::max(1, std::min(ceil_div((int64_t)rows * G, TPB), kNumSMs * 32));
-    if (G == 1) k_row_ub<1><<<grid, TPB, 0, s>>>(rows, X.rp, X.ci, Y.rp, ub.p, flags);
-    else if (G == 8) k_row_ub<8><<<grid, TPB, 0, s>>>(rows, X.rp, X.ci, Y.rp, ub.p, flags);
-    else k_row_ub<32><<<grid, TPB, 0, s>>>(rows, X.rp, X.ci, Y.rp, ub.p, flags);
-    AMG_CHECK_LAUNCH();
-    k_bin_rows<<<ntiles, TPB, 0, s>>>(rows, X.rp, ub.p, tier.p, tile_cnt.p, meta.p + NTIER);
-    AMG_CHECK_LAUNCH();
-    k_tier_offsets<<<1, TPB, 0, s>>>(ntiles, tile_cnt.p, tile_off.p, meta.p);
-    AMG_CHECK_LAUNCH();
-    k_tier_scatter<<<ntiles, TPB, 0, s>>>(rows, tier.p, tile_off.p, lists.p);
+    if (G == 1) k_row_ub<1><<<grid, TPB, 0, s>>>(rows, X.rp, X.ci, y, ub.p, tier.p, meta.p, flags);
+    else if (G == 8) k_row_ub<8><<<grid, TPB, 0, s>>>(rows, X.rp, X.ci, y, ub.p, tier.p, meta.p, flags);
+    else k_row_ub<32><<<grid, TPB, 0, s>>>(rows, X.rp, X.ci, y, ub.p, tier.p, meta.p, flags);
     AMG_CHECK_LAUNCH();
   }
-  // the scan's total and the tier counts come back in one synchronisation
+  // the scan's total, the tier counts and Y's entry count come back in one synchronisation
   Buf<long long> ub_tot(m, 1);
   scan_counts_async(m, ub.p, off.p, rows, ub_tot.p);
   int hm[NTIER + 1];
-  long long total_ub = 0;
+  long long total_ub = 0, ynnz = Y.nnz;
   AMG_CUDA(cudaMemcpyAsync(hm, meta.p, sizeof(hm), cudaMemcpyDeviceToHost, s));
   AMG_CUDA(cudaMemcpyAsync(&total_ub, ub_tot.p, sizeof(total_ub), cudaMemcpyDeviceToHost, s));
+  if (yslot) AMG_CUDA(cudaMemcpyAsync(&ynnz, yslot->nnz.p, sizeof(ynnz), cudaMemcpyDeviceToHost, s));
   AMG_CUDA(cudaStreamSynchronize(s));
   check_scan_total(total_ub);
   if (hm[NTIER] > (1 << 22)) {
     set_error("SpGEMM row product bound above 2^22 entries");
     throw Status{AMG_ERR_UNSUPPORTED};
+  }
+  int start[NTIER + 1];
+  start[0] = 0;
+  for (int t = 0; t < NTIER; ++t) start[t + 1] = start[t] + hm[t];
+  Buf<int> startd(m, NTIER);
+  AMG_CUDA(cudaMemcpyAsync(startd.p, start, sizeof(int) * NTIER, cudaMemcpyHostToDevice, s));
+  {
+    ProfScope ps(s, AMG_K_SPGEMM, 0.0, level);
+    k_tier_scatter<<<std::max(1, ntiles), TPB, 0, s>>>(rows, tier.p, startd.p, meta.p + NTIER + 1, lists.p);
+    AMG_CHECK_LAUNCH();
   }
   int gcap = 2;
   while (gcap < 2 * std::max(hm[NTIER], 1)) gcap <<= 1;
@@ -658,22 +652,24 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
   Buf<int> tci(m, (size_t)std::max<int64_t>(total_ub, 1));
   Buf<double> tcv(m, (size_t)std::max<int64_t>(total_ub, 1));
   Buf<int> cnt(m, (size_t)rows + 1);
-  int start[NTIER + 1];
-  start[0] = 0;
-  for (int t = 0; t < NTIER; ++t) start[t + 1] = start[t] + hm[t];
   auto list = [&](int t) { return lists.p + start[t]; };
-  const Args a{&X, &Y, off.p, tci.p, tcv.p, cnt.p, flags, s};
+  const Args a{&X, y, Y.ci, Y.v, off.p, tci.p, tcv.p, cnt.p, flags, s};
+  // Algorithmic bytes (the byte model of A_c = R (A P)): X and Y read once; C
+  // written once -- charged here for a product left in slot form (A P) when it
+  // is read by the next product, and by the compaction for the coarse operator.
+  const double ybytes = 4.0 * (Y.n + 1) + (yslot ? 4.0 * Y.n : 0.0) + 12.0 * (double)ynnz;
+  const double xy_bytes = 4.0 * (rows + 1) + 12.0 * (double)X.nnz + ybytes + (yslot ? ybytes : 0.0);
   {
-    ProfScope ps(s, AMG_K_SPGEMM, xy_bytes);
+    ProfScope ps(s, AMG_K_SPGEMM, xy_bytes, level);
     if (hm[T_THREAD] > 0) {
       const int grid = std::max(1, std::min(ceil_div(hm[T_THREAD], TPB), kNumSMs * 16));
-      k_spgemm_merge<<<grid, TPB, 0, s>>>(list(T_THREAD), hm[T_THREAD], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off.p,
+      k_spgemm_merge<<<grid, TPB, 0, s>>>(list(T_THREAD), hm[T_THREAD], X.rp, X.ci, X.v, y, Y.ci, Y.v, off.p,
                                           tci.p, tcv.p, cnt.p);
       AMG_CHECK_LAUNCH();
     }
     if (hm[0] > 0) {
       const int grid = std::max(1, std::min(ceil_div(hm[0], WARPS), kNumSMs * 32));
-      k_spgemm_reg<<<grid, TPB, 0, s>>>(list(0), hm[0], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off.p, tci.p, tcv.p, cnt.p);
+      k_spgemm_reg<<<grid, TPB, 0, s>>>(list(0), hm[0], X.rp, X.ci, X.v, y, Y.ci, Y.v, off.p, tci.p, tcv.p, cnt.p);
       AMG_CHECK_LAUNCH();
     }
     if (hm[1] > 0) launch_hash<128>(hm[1], list(1), a);
@@ -683,24 +679,38 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
     if (hm[5] > 0) launch_hash<2048>(hm[5], list(5), a);
     if (hm[6] > 0) {
       const int grid = std::max(1, std::min(hm[6], kNumSMs * 4));
-      k_spgemm_block<false><<<grid, TPB, block_smem, s>>>(list(6), hm[6], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off.p,
+      k_spgemm_block<false><<<grid, TPB, block_smem, s>>>(list(6), hm[6], X.rp, X.ci, X.v, y, Y.ci, Y.v, off.p,
                                                           tci.p, tcv.p, cnt.p, flags, nullptr, 0);
       AMG_CHECK_LAUNCH();
     }
     if (hm[T_GLOBAL] > 0) {
-      k_spgemm_block<true><<<gblocks, TPB, 0, s>>>(list(T_GLOBAL), hm[T_GLOBAL], X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off.p, tci.p,
-                                                   tcv.p, cnt.p, flags, gscr.p, gcap);
+      k_spgemm_block<true><<<gblocks, TPB, 0, s>>>(list(T_GLOBAL), hm[T_GLOBAL], X.rp, X.ci, X.v, y, Y.ci, Y.v, off.p,
+                                                   tci.p, tcv.p, cnt.p, flags, gscr.p, gcap);
       AMG_CHECK_LAUNCH();
     }
   }
   C.n = rows;
   C.ncols = ncols;
+  if (cslot) {  // leave C in slot form: row i at off[i], cnt[i] entries
+    C.rp = off.release();
+    C.ci = tci.release();
+    C.v = tcv.release();
+    C.nnz = total_ub;  // capacity of the slots
+    cslot->cnt = std::move(cnt);
+    cslot->nnz = Buf<long long>(m, 1);
+    AMG_CUDA(cudaMemsetAsync(cslot->nnz.p, 0, sizeof(long long), s));
+    ProfScope ps(s, AMG_K_SPGEMM, 0.0, level);
+    k_sum_counts<<<std::max(1, std::min(ceil_div(rows, TPB), kNumSMs * 4)), TPB, 0, s>>>(rows, cslot->cnt.p,
+                                                                                       cslot->nnz.p);
+    AMG_CHECK_LAUNCH();
+    return;
+  }
   C.rp = m.get_n<int>((size_t)rows + 1);
   C.nnz = scan_counts(m, cnt.p, C.rp, rows);
   C.ci = m.get_n<int>(std::max<int64_t>(C.nnz, 1));
   C.v = m.get_n<double>(std::max<int64_t>(C.nnz, 1));
   {
-    ProfScope ps(s, AMG_K_SPGEMM, 4.0 * (rows + 1) + 12.0 * C.nnz);
+    ProfScope ps(s, AMG_K_SPGEMM, 4.0 * (rows + 1) + 12.0 * C.nnz, level);
     if (C.nnz <= 12LL * rows)
       k_compact<8><<<std::max(1, std::min(ceil_div(rows, TPB / 8), kNumSMs * 32)), TPB, 0, s>>>(
           rows, off.p, tci.p, tcv.p, C.rp, C.ci, C.v);

@@ -72,7 +72,8 @@ def test_bad_params_rejected_without_gpu(lib):
     for kw, code in (({"theta": 0.0}, amg.AMG_ERR_INVALID_ARG), ({"max_levels": 0}, amg.AMG_ERR_INVALID_ARG),
                      ({"omega": 2.5}, amg.AMG_ERR_INVALID_ARG), ({"nu1": -1}, amg.AMG_ERR_INVALID_ARG),
                      ({"precision": 7}, amg.AMG_ERR_INVALID_ARG), ({"block_size": 0}, amg.AMG_ERR_INVALID_ARG),
-                     ({"block_size": 9}, amg.AMG_ERR_INVALID_ARG),
+                     ({"block_size": 9}, amg.AMG_ERR_INVALID_ARG), ({"smoother": 5}, amg.AMG_ERR_INVALID_ARG),
+                     ({"interp": 7}, amg.AMG_ERR_INVALID_ARG),
                      ({"block_size": 3}, amg.AMG_ERR_INVALID_ARG)):  # n = 1 is not a multiple of 3
         p = amg.default_params(**kw)
         assert lib.amg_setup(C.byref(csr), C.byref(p), None, None, C.byref(h)) == code

@@ -101,13 +101,21 @@ def test_block_size_needs_full_blocks():
     assert e.value.code == amg.AMG_ERR_INVALID_ARG
 
 
-def test_config4_full_size_properties():
+def test_config4_full_size():
     """64^3 Q1 elasticity (811,200 unknowns, 63.7M nonzeros), 16 right-hand sides in one batched
-    FP32 V-cycle under the FP64 flexible PCG.  The oracle is too slow at this size, so the checks
-    are properties: every column converges; its true residual, from an FP64 product through
-    amg_spmv, is within 10x of rtol; node labels are shared by a node's unknowns; and sampled
-    rows of the level-1 operator equal the brute-force sum over R_I and A P."""
+    FP32 V-cycle under the FP64 flexible PCG.  The hierarchy is checked against the oracle's
+    systems set-up at full size (~8 s on one host core): every level's node labels, P and A_k
+    bit-exact.  The oracle's solve (~3400 iterations per column) is too slow here, so the solve is
+    checked by properties: every column converges; its true residual, from an FP64 product through
+    amg_spmv, is within 10x of rtol; node labels are shared by a node's unknowns; and sampled rows
+    of the level-1 operator equal the brute-force sum over R_I and A P."""
     A, Bm = pr.config4()
+    ho = O.Hierarchy(A, seed=0, block_size=3, omega=OMEGA)
+    h64 = amg.Hierarchy(A, seed=0, block_size=3, omega=OMEGA)
+    assert_same_hierarchy(h64, ho)
+    assert bitwise_equal_hierarchy(h64, ho)
+    h64.close()
+    del ho
     hg = amg.Hierarchy(A, seed=0, block_size=3, omega=OMEGA, precision=amg.PREC_FP32)
     B = dev(Bm)
     X, iters, stats, st, _ = hg.solve_batch(B, rtol=1e-8, maxit=5000)
