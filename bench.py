@@ -343,14 +343,13 @@ def run_gpu(args, rank, world, dist):
     prof_pass = amg.profile_read()
     nlev = rec["info"]["nlevels"]
     per_level = {lv: amg.profile_read(lv) for lv in range(nlev)}
-    cands = [(d["ms"], name, lv) for lv, pl in per_level.items() for name, d in pl.items() if d["launches"]]
-    for name, d in prof_pass.items():  # launches outside any level (set-up kernels)
-        rest_ms = d["ms"] - sum(per_level[lv][name]["ms"] for lv in per_level)
-        if rest_ms > 1e-9:
-            cands.append((rest_ms, name, None))
+    # the dominant kernel: the kernel class with the largest summed time over
+    # all its launches (every level) in one step
+    cands = [(d["ms"], name) for name, d in prof_pass.items() if d["launches"]]
     if not cands:
-        cands = [(0.0, "spmv_dot", 0)]
-    _, dom, dom_lv = max(cands)
+        cands = [(0.0, "spmv_dot")]
+    _, dom = max(cands)
+    dom_lv = None
     by_level = {lv: {k: {"ms": round(v["ms"], 4),
                          "gbs": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None}
                      for k, v in pl.items() if v["launches"]}

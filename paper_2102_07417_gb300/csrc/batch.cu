@@ -130,31 +130,38 @@ struct BAcc {
   double v[NV > 0 ? NV : 1];
 };
 
-// SpMM row kernel: group of K lanes per row, lane j = column j (< k).
+// SpMM row kernel: G x K lanes per row (K * G <= 32).  Lane (g, j) takes
+// column j (< k) and the row's entries g, g + G, g + 2G, ...; the G partial
+// sums of a column are then added with shuffles (a fixed order).  G > 1 keeps
+// more loads in flight on the short, long-row coarse levels, where one lane
+// walking a whole row for its column was bound by the row's load latency.
 // For each (row, j): sum = sum_p mat(p) vec(ci[p], j); op.out(row, j, sum, acc).
-template <int K, class Op>
+template <int K, int G, class Op>
 __global__ void __launch_bounds__(TPB) k_brows(int n, int k, const int *__restrict__ rp, const int *__restrict__ ci,
                                                Op op) {
   using T = typename Op::T;
   constexpr int NA = Op::NV > 0 ? Op::NV : 1;
+  constexpr int LPR = K * G;  // lanes per row
+  constexpr int RPW = 32 / LPR;
   if (op.skip()) return;
-  const int lane = threadIdx.x & 31, j = lane & (K - 1), grp = lane / K;
-  constexpr int RPW = 32 / K;
+  const int lane = threadIdx.x & 31, j = lane & (K - 1), g = (lane / K) & (G - 1), grp = lane / LPR;
   const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5, nw = (gridDim.x * TPB) >> 5;
   BAcc<NA> acc;
 #pragma unroll
   for (int c = 0; c < NA; ++c) acc.v[c] = 0.0;
-  for (int base = gw * RPW; base < n; base += nw * RPW) {
+  for (int base = gw * RPW; base < n; base += nw * RPW) {  // the whole warp iterates together
     const int row = base + grp;
-    if (row < n && j < k) {
-      T sum = T(0);
-      if constexpr (Op::kMatrix) {
+    T sum = T(0);
+    if constexpr (Op::kMatrix) {
+      if (row < n && j < k) {
         const int e = rp[row + 1];
 #pragma unroll 4
-        for (int p = rp[row]; p < e; ++p) sum = fma(op.mat(p), op.vec(ci[p], j), sum);
+        for (int p = rp[row] + g; p < e; p += G) sum = fma(op.mat(p), op.vec(ci[p], j), sum);
       }
-      op.out(row, j, sum, acc);
+#pragma unroll
+      for (int o = K; o < LPR; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     }
+    if (row < n && j < k && g == 0) op.out(row, j, sum, acc);
   }
   op.finish(acc);
 }
@@ -886,11 +893,23 @@ __global__ void k_bcopy(int64_t total, const T *__restrict__ a, T *__restrict__ 
 
 inline int grid_for(int64_t work) { return std::max(1, std::min<int>(ceil_div(work, TPB), MAX_GRID)); }
 
-// Batches of up to 16 columns run on a matrix's sliced-ELLPACK copy when it
-// has one (the op's value pointer must then point into it: bv below).
+// Batches of up to 16 columns run on a matrix's sliced-ELLPACK copy from 2^18
+// rows up (the op's value pointer must then point into it: bv below); smaller
+// matrices use the CSR row kernel with several lanes per row and column.
+constexpr int kBSellRows = 1 << 18;
 template <int K>
 bool bsell(const DCsr &M) {
-  return M.use_sell && K <= 16;
+  return M.use_sell && K <= 16 && M.n >= kBSellRows;
+}
+
+// Entry lanes G per (row, column) of k_brows: about a quarter of the mean row
+// length, at most 32 / K.
+template <int K>
+int brows_g(const DCsr &M) {
+  const double avg = M.n ? (double)M.nnz / M.n : 0.0;
+  int g = 1;
+  while (g * 2 * K <= 32 && 4.0 * g * 2 <= avg) g <<= 1;
+  return g;
 }
 
 template <typename V>
@@ -928,7 +947,18 @@ void launch_b(int n, int k, const DCsr &M, const Op &op, cudaStream_t s) {
       done = true;
     }
   }
-  if (!done) k_brows<K, Op><<<grid_for((int64_t)n * K), TPB, 0, s>>>(n, k, M.rp, M.ci, op);
+  if (!done) {
+    const int g = brows_g<K>(M);
+    const int grid = grid_for((int64_t)n * K * g);
+    switch (g) {
+      case 1: k_brows<K, 1, Op><<<grid, TPB, 0, s>>>(n, k, M.rp, M.ci, op); break;
+      case 2: if constexpr (K * 2 <= 32) k_brows<K, 2, Op><<<grid, TPB, 0, s>>>(n, k, M.rp, M.ci, op); break;
+      case 4: if constexpr (K * 4 <= 32) k_brows<K, 4, Op><<<grid, TPB, 0, s>>>(n, k, M.rp, M.ci, op); break;
+      case 8: if constexpr (K * 8 <= 32) k_brows<K, 8, Op><<<grid, TPB, 0, s>>>(n, k, M.rp, M.ci, op); break;
+      case 16: if constexpr (K * 16 <= 32) k_brows<K, 16, Op><<<grid, TPB, 0, s>>>(n, k, M.rp, M.ci, op); break;
+      default: if constexpr (K * 32 <= 32) k_brows<K, 32, Op><<<grid, TPB, 0, s>>>(n, k, M.rp, M.ci, op); break;
+    }
+  }
   AMG_CHECK_LAUNCH();
 }
 
@@ -1485,6 +1515,7 @@ struct SlotsImpl : SlotsBase {
   void poll(int *state, int *iters) override {
     AMG_CUDA(cudaMemcpyAsync(host, scb.p, sizeof(BScal), cudaMemcpyDeviceToHost, mem.stream));
     AMG_CUDA(cudaStreamSynchronize(mem.stream));
+    prof_collect(mem.stream);  // event-timed launches of the steps (profiling on)
     completed = issued;
     report(host, state, iters);
   }

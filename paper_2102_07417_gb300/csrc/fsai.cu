@@ -28,6 +28,7 @@ namespace amg {
 namespace {
 
 constexpr int TPB = 256;
+constexpr int kThreadRows = 16;  // longest lower row taken by the thread-per-row kernel
 
 // cnt[i] = number of stored entries of row i with column <= i; flags[0] when
 // the last of them is not the diagonal.  *mmax receives the largest count.
@@ -130,7 +131,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 //     trailing lower triangle updated with independent multiply-adds;
 //   solve: L^T g = e_last backwards, one warp sum per component.
 template <bool SMEM>
-__global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+__global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict__ rows, const int *__restrict__ rp,
+                                                   const int *__restrict__ ci,
                                                    const double *__restrict__ a, const int *__restrict__ grp,
                                                    int *__restrict__ gci, double *__restrict__ gv, double *scratch,
                                                    int ld, int nw, int *flags) {
@@ -143,7 +145,8 @@ __global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict_
   double *M = SMEM ? fsai_smem + slice * wb : scratch + slice * w;
   double *g = M + (size_t)ld * ld;
   int *P = reinterpret_cast<int *>(g + ld);
-  for (int i = w; i < n; i += nw) {
+  for (int r0 = w; r0 < n; r0 += nw) {
+    const int i = rows ? rows[r0] : r0;
     const int b = rp[i], o = grp[i], m = grp[i + 1] - o;
     for (int t = lane; t < m; t += 32) P[t] = ci[b + t];
     for (int t = lane; t < m * m; t += 32) M[(size_t)(t / m) * ld + (t % m)] = 0.0;
@@ -194,20 +197,40 @@ __global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict_
     }
     __syncwarp();
     bool ok = true;
-    for (int j = 0; j < m; ++j) {
-      const double d = M[(size_t)j * ld + j];
-      ok = ok && d > 0.0;
-      const double l = sqrt(d > 0.0 ? d : 1.0);
-      __syncwarp();
-      for (int r = j + 1 + lane; r < m; r += 32) M[(size_t)r * ld + j] /= l;
-      if (lane == 0) M[(size_t)j * ld + j] = l;
-      __syncwarp();
-      for (int r = j + 1 + lane; r < m; r += 32) {  // trailing update of row r: columns j+1..r
-        double *Mr = M + (size_t)r * ld;
-        const double lrj = Mr[j];
-        for (int c = j + 1; c <= r; ++c) Mr[c] -= lrj * M[(size_t)c * ld + j];
+    if (SMEM) {  // right-looking: independent updates of the trailing triangle
+      for (int j = 0; j < m; ++j) {
+        const double d = M[(size_t)j * ld + j];
+        ok = ok && d > 0.0;
+        const double l = sqrt(d > 0.0 ? d : 1.0), inv = 1.0 / l;
+        __syncwarp();
+        for (int r = j + 1 + lane; r < m; r += 32) M[(size_t)r * ld + j] *= inv;
+        if (lane == 0) M[(size_t)j * ld + j] = l;
+        __syncwarp();
+        for (int r = j + 1 + lane; r < m; r += 32) {  // trailing update of row r: columns j+1..r
+          double *Mr = M + (size_t)r * ld;
+          const double lrj = Mr[j];
+          for (int c = j + 1; c <= r; ++c) Mr[c] -= lrj * M[(size_t)c * ld + j];
+        }
+        __syncwarp();
       }
-      __syncwarp();
+    } else {  // left-looking: global scratch is read far more than written
+      for (int j = 0; j < m; ++j) {
+        const double *Mj = M + (size_t)j * ld;
+        double d = 0.0;
+        for (int k = lane; k < j; k += 32) d += Mj[k] * Mj[k];
+        d = Mj[j] - warp_sum(d);
+        ok = ok && d > 0.0;
+        const double l = sqrt(d > 0.0 ? d : 1.0), inv = 1.0 / l;
+        for (int r = j + 1 + lane; r < m; r += 32) {
+          double *Mr = M + (size_t)r * ld;
+          double sum = Mr[j];
+          for (int k = 0; k < j; ++k) sum -= Mr[k] * Mj[k];
+          Mr[j] = sum * inv;
+        }
+        __syncwarp();
+        if (lane == 0) M[(size_t)j * ld + j] = l;
+        __syncwarp();
+      }
     }
     if (!ok && lane == 0) flags[1] = 1;
     // L^T g = e_last, backwards: g_k = (e_k - sum_{l > k} L_lk g_l) / L_kk
@@ -224,6 +247,95 @@ __global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict_
     }
     __syncwarp();
   }
+}
+
+// Thread per row for rows of at most ld lower entries: the submatrix in the
+// thread's slice of shared memory, interleaved across the block's threads
+// (element e of thread t at e * NT + t, so a warp's accesses hit distinct
+// banks).  Every FP64 operation of the factor and the solve is then done by
+// all lanes of a warp at once: GB300 issues FP64 per warp at a small fraction
+// of the FP32 rate, so a factor spread over the lanes of one row (the warp
+// kernel) spends most of its FP64 issue slots on idle lanes.  rows (may be
+// null: all rows) lists the rows to take.
+__global__ void k_fsai_thread(int n, const int *__restrict__ rows, int nrows, const int *__restrict__ rp,
+                              const int *__restrict__ ci, const double *__restrict__ a, const int *__restrict__ grp,
+                              int *__restrict__ gci, double *__restrict__ gv, int ld, int *flags) {
+  extern __shared__ __align__(16) double fsai_tsmem[];
+  const int NT = blockDim.x, t = threadIdx.x;
+  double *M = fsai_tsmem;              // M[(r * ld + c) * NT + t]
+  double *g = fsai_tsmem + (size_t)ld * ld * NT;  // g[k * NT + t]
+  for (int r0 = blockIdx.x * NT + t; r0 < nrows; r0 += gridDim.x * NT) {
+    const int i = rows ? rows[r0] : r0;
+    const int b = rp[i], o = grp[i], m = grp[i + 1] - o;
+    const int *P = ci + b;  // the row's lower part, ascending, ending at i
+    for (int r = 0; r < m; ++r) {
+      // row P[r] and P[0..r] are both ascending: one merge walk
+      const int row = P[r];
+      int q = rp[row], c = 0;
+      while (c <= r) {
+        const int col = ci[q];
+        if (col == P[c]) {
+          M[(size_t)(r * ld + c) * NT + t] = a[q];
+          ++c;
+          ++q;
+        } else if (col < P[c]) {
+          ++q;
+        } else {
+          M[(size_t)(r * ld + c) * NT + t] = 0.0;
+          ++c;
+        }
+      }
+    }
+    bool ok = true;
+    for (int j = 0; j < m; ++j) {  // left-looking Cholesky, one multiply by 1/l_jj per entry
+      double d = M[(size_t)(j * ld + j) * NT + t];
+      for (int k = 0; k < j; ++k) {
+        const double v = M[(size_t)(j * ld + k) * NT + t];
+        d -= v * v;
+      }
+      ok = ok && d > 0.0;
+      const double l = sqrt(d > 0.0 ? d : 1.0), inv = 1.0 / l;
+      M[(size_t)(j * ld + j) * NT + t] = l;
+      for (int r = j + 1; r < m; ++r) {
+        double s = M[(size_t)(r * ld + j) * NT + t];
+        for (int k = 0; k < j; ++k) s -= M[(size_t)(r * ld + k) * NT + t] * M[(size_t)(j * ld + k) * NT + t];
+        M[(size_t)(r * ld + j) * NT + t] = s * inv;
+      }
+    }
+    if (!ok) flags[1] = 1;
+    for (int k = m - 1; k >= 0; --k) {  // L^T g = e_last
+      double s = k == m - 1 ? 1.0 : 0.0;
+      for (int l = k + 1; l < m; ++l) s -= M[(size_t)(l * ld + k) * NT + t] * g[(size_t)l * NT + t];
+      g[(size_t)k * NT + t] = s / M[(size_t)(k * ld + k) * NT + t];
+    }
+    for (int r = 0; r < m; ++r) {
+      gci[o + r] = P[r];
+      gv[o + r] = g[(size_t)r * NT + t];
+    }
+  }
+}
+
+// Rows of at most lim lower entries to list s, the others to list l (counts in
+// ns, nl); tiles of the block append with one atomic each.
+__global__ void k_fsai_split(int n, const int *__restrict__ grp, int lim, int *__restrict__ ls, int *ns,
+                             int *__restrict__ ll, int *nl) {
+  __shared__ int cs, cl, bs, bl;
+  if (threadIdx.x == 0) cs = cl = 0;
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = i < n;
+  const bool small = live && grp[i + 1] - grp[i] <= lim;
+  int ps = -1, pl = -1;
+  if (live && small) ps = atomicAdd(&cs, 1);
+  if (live && !small) pl = atomicAdd(&cl, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bs = cs ? atomicAdd(ns, cs) : 0;
+    bl = cl ? atomicAdd(nl, cl) : 0;
+  }
+  __syncthreads();
+  if (ps >= 0) ls[bs + ps] = i;
+  if (pl >= 0) ll[bl + pl] = i;
 }
 
 __global__ void k_scale(int64_t n, double f, double *__restrict__ v) {
@@ -263,26 +375,49 @@ void build_fsai(amg_hierarchy *h, int k) {
   {
     // bytes: A's lower rows gathered (once per use, ~m per row), G written
     ProfScope ps(s, AMG_K_FSAI, 4.0 * (n + 1) + 12.0 * (double)A.nnz + 4.0 * (n + 1) + 12.0 * (double)G.nnz, k);
+    auto launch_thread = [&](const int *rows, int nrows, int ld) {
+      const size_t per = ((size_t)ld * ld + ld) * sizeof(double);  // per thread
+      const int nt = (int)std::max<size_t>(32, std::min<size_t>(256, (200 * 1024 / per) / 32 * 32));
+      static std::atomic<unsigned long long> attr{0};
+      ensure_smem_attr(k_fsai_thread, 200 * 1024, attr);
+      const int blocks = std::max(1, std::min(ceil_div(nrows, nt), kNumSMs * 8));
+      k_fsai_thread<<<blocks, nt, per * nt, s>>>(n, rows, nrows, A.rp, A.ci, A.v, G.rp, G.ci, G.v, ld, meta.p);
+      AMG_CHECK_LAUNCH();
+    };
     if (mmax <= 4) {
       k_fsai_rows<4><<<ceil_div(n, TPB), TPB, 0, s>>>(n, A.rp, A.ci, A.v, G.rp, G.ci, G.v, meta.p);
     } else if (mmax <= 8) {
       k_fsai_rows<8><<<ceil_div(n, TPB), TPB, 0, s>>>(n, A.rp, A.ci, A.v, G.rp, G.ci, G.v, meta.p);
+    } else if (mmax <= kThreadRows) {
+      launch_thread(nullptr, n, mmax);
     } else {
+      // rows of at most kThreadRows lower entries by the thread kernel, the
+      // others by the warp kernel
+      Buf<int> lsmall(m, n), llarge(m, n), nsl(m, 2);
+      AMG_CUDA(cudaMemsetAsync(nsl.p, 0, 2 * sizeof(int), s));
+      k_fsai_split<<<ceil_div(n, TPB), TPB, 0, s>>>(n, G.rp, kThreadRows, lsmall.p, nsl.p, llarge.p, nsl.p + 1);
+      AMG_CHECK_LAUNCH();
+      int hn[2];
+      AMG_CUDA(cudaMemcpyAsync(hn, nsl.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
+      AMG_CUDA(cudaStreamSynchronize(s));
+      if (hn[0] > 0) launch_thread(lsmall.p, hn[0], kThreadRows);
+      const int nbig = hn[1];
       // slice per warp: ld * ld + 2 ld doubles (P_i's ints fit in the last ld)
       const size_t slice = ((size_t)mmax * mmax + 2 * (size_t)mmax) * sizeof(double);
       const int wpb = (int)std::min<size_t>(8, (size_t)(200 * 1024) / slice);
       if (wpb >= 1) {  // shared memory
         static std::atomic<unsigned long long> attr{0};
         ensure_smem_attr(k_fsai_warp<true>, 200 * 1024, attr);
-        const int blocks = std::max(1, std::min(ceil_div(n, wpb), kNumSMs * 32));
-        k_fsai_warp<true><<<blocks, wpb * 32, slice * wpb, s>>>(n, A.rp, A.ci, A.v, G.rp, G.ci, G.v, nullptr, mmax,
-                                                                 blocks * wpb, meta.p);
+        const int blocks = std::max(1, std::min(ceil_div(nbig, wpb), kNumSMs * 32));
+        k_fsai_warp<true><<<blocks, wpb * 32, slice * wpb, s>>>(nbig, llarge.p, A.rp, A.ci, A.v, G.rp, G.ci, G.v,
+                                                                 nullptr, mmax, blocks * wpb, meta.p);
       } else {  // global scratch
         const int64_t cap_warps = std::max<int64_t>(1, ((int64_t)256 << 20) / (int64_t)slice);
-        const int warps = (int)std::min<int64_t>({(int64_t)n, (int64_t)kNumSMs * 16, cap_warps});
+        const int warps = (int)std::min<int64_t>({(int64_t)std::max(nbig, 1), (int64_t)kNumSMs * 16, cap_warps});
         Buf<double> scr(m, slice / sizeof(double) * (size_t)warps);
-        k_fsai_warp<false><<<ceil_div((int64_t)warps * 32, TPB), TPB, 0, s>>>(n, A.rp, A.ci, A.v, G.rp, G.ci, G.v,
-                                                                             scr.p, mmax, warps, meta.p);
+        k_fsai_warp<false><<<ceil_div((int64_t)warps * 32, TPB), TPB, 0, s>>>(nbig, llarge.p, A.rp, A.ci, A.v,
+                                                                             G.rp, G.ci, G.v, scr.p, mmax, warps,
+                                                                             meta.p);
       }
     }
     AMG_CHECK_LAUNCH();

@@ -966,34 +966,58 @@ __device__ int ext_set(int i, int lane, const int *__restrict__ rp, const int *_
   return m;
 }
 
-__device__ __forceinline__ int key_pos(const int *keys, int m, int key) {
-  int lo = 0, hi = m - 1;
-  while (lo <= hi) {
-    const int mid = (lo + hi) >> 1;
-    const int c = keys[mid];
-    if (c == key) return mid;
-    if (c < key) lo = mid + 1;
-    else hi = mid - 1;
+// Rank of key among Chat_i's sorted keys, or -1: one probe sequence in the
+// warp's hash set, whose slots hold, after ext_rank, the key's rank beside it.
+__device__ __forceinline__ int key_pos(const int *table, const int *rank, int T, int key) {
+  unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(T - 1);
+  for (;;) {
+    const int kk = table[h];
+    if (kk == key) return rank[h];
+    if (kk < 0) return -1;
+    h = (h + 1) & (unsigned)(T - 1);
   }
-  return -1;
 }
 
-// Shared memory per warp of k_ext_interp: table[T], keys[T] (ints), num[T],
-// dv[maxrow], aki[maxrow] (doubles), code[maxrow] (ints).
-__host__ __device__ inline size_t ext_warp_bytes(int T, int maxrow) {
-  const size_t b = (size_t)2 * T * sizeof(int) + (size_t)T * sizeof(double) + (size_t)2 * maxrow * sizeof(double) +
-                   (size_t)maxrow * sizeof(int);
+// rank[slot of keys[t]] = t for every key of the set.
+__device__ __forceinline__ void ext_rank(int lane, const int *table, int *rank, int T, const int *keys, int m) {
+  for (int t = lane; t < m; t += 32) {
+    const int key = keys[t];
+    unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(T - 1);
+    while (table[h] != key) h = (h + 1) & (unsigned)(T - 1);
+    rank[h] = t;
+  }
+  __syncwarp();
+}
+
+// Shared memory per warp of k_ext_interp: num[T], dv[maxrow], cv[maxrow],
+// bv[kExtBatch] (doubles), table[T], keys[T], rank[T], code[maxrow],
+// flist[maxrow], bt[kExtBatch], bs[kExtBatch], sstart[kExtSegs + 1],
+// sp[kExtSegs] (ints).
+constexpr int kExtBatch = 512;  // numerator terms per batch of divisions
+constexpr int kExtSegs = 128;   // F-neighbour segments per batch
+__host__ __device__ inline size_t ext_warp_bytes(int T, int maxrow, bool fill = true) {
+  if (!fill) return (size_t)2 * T * sizeof(int);  // the count pass: table[T], keys[T]
+  const size_t b = (size_t)T * sizeof(double) + (size_t)2 * maxrow * sizeof(double) + (size_t)kExtBatch * sizeof(double) +
+                   (size_t)3 * T * sizeof(int) + (size_t)2 * maxrow * sizeof(int) + (size_t)2 * kExtBatch * sizeof(int) +
+                   (size_t)(2 * kExtSegs + 1) * sizeof(int);
   return (b + 15) & ~(size_t)15;  // keeps the next warp's doubles aligned
 }
 
-// FILL = false: cnt[i] = |Chat_i| (1 for C rows).  FILL = true: row i of P:
-//   per entry p of row i (lanes in parallel): code 1 for a strong F neighbour k
-//   with its d_k (the lane walks row k in ascending order) and a_ki; code 2 for
-//   a weak coupling outside Chat_i; then one lane forms at serially in the
-//   row's order; the numerators start at a_ij (0 off the row) and take the k
-//   terms one strong F neighbour at a time in ascending k (lanes over row k:
-//   each column appears once per row, so every numerator still adds its terms
-//   in ascending k); w_ij = -(num / at).
+// FILL = false: cnt[i] = |Chat_i| (1 for C rows).  FILL = true: row i of P.
+// GB300 issues FP64 per warp at a small fraction of the FP32 rate, so every
+// FP64 step keeps its lanes dense:
+//   the strong F neighbours k of row i are listed (ascending); a lane per k
+//   forms d_k walking row k in ascending order;
+//   a lane per entry p of row i forms its term of at -- (a_ik a_ki) / d_k for a
+//   strong F neighbour (a_ki < 0, d_k != 0), a_ik for one with d_k = 0, a_in
+//   for a weak coupling outside Chat_i -- and one lane adds them to a_ii in
+//   the row's order;
+//   the numerators start at a_ij (0 off the row); their terms
+//   (a_ik a_kj) / d_k are gathered for the listed k in ascending order into
+//   batches (qualifying entries of row k: a_kj < 0, j in Chat_i), divided with
+//   all lanes busy, then added k segment by k segment (a column appears once
+//   in a row, so each numerator takes its terms in ascending k);
+//   w_ij = -(num / at).
 // flags[0]: at = 0 met.
 template <bool FILL>
 __global__ void __launch_bounds__(kExtWarps * 32) k_ext_interp(int n, const int *__restrict__ rp,
@@ -1006,13 +1030,21 @@ __global__ void __launch_bounds__(kExtWarps * 32) k_ext_interp(int n, const int 
                                                                int *flags) {
   extern __shared__ __align__(16) unsigned char ext_smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned char *base = ext_smem + ext_warp_bytes(T, maxrow) * w;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned char *base = ext_smem + ext_warp_bytes(T, maxrow, FILL) * w;
   double *num = reinterpret_cast<double *>(base);
   double *dv = num + T;
-  double *aki = dv + maxrow;
-  int *table = reinterpret_cast<int *>(aki + maxrow);
+  double *cv = dv + maxrow;
+  double *bv = cv + maxrow;
+  int *table = FILL ? reinterpret_cast<int *>(bv + kExtBatch) : reinterpret_cast<int *>(base);
   int *keys = table + T;
-  int *code = keys + T;
+  int *rank = keys + T;
+  int *code = rank + T;
+  int *flist = code + maxrow;
+  int *bt = flist + maxrow;
+  int *bs = bt + kExtBatch;
+  int *sstart = bs + kExtBatch;
+  int *sp = sstart + kExtSegs + 1;
   const int wpb = blockDim.x >> 5;
   const int nw = gridDim.x * wpb;
   for (int i = blockIdx.x * wpb + w; i < n; i += nw) {
@@ -1029,73 +1061,126 @@ __global__ void __launch_bounds__(kExtWarps * 32) k_ext_interp(int n, const int 
     }
     const int m = ext_set(i, lane, rp, ci, S, cf, table, keys, T);
     if (!FILL) {
-      if (lane == 0) cnt[i] = m;
+      if (lane == 0) {
+        cnt[i] = m;
+        atomicMax(flags + 1, m);  // the largest |Chat_i|, which sizes the fill pass's set
+      }
       __syncwarp();
       continue;
     }
     if (m == 0) continue;
+    ext_rank(lane, table, rank, T, keys, m);
     const int b = rp[i], e = rp[i + 1];
     for (int t = lane; t < m; t += 32) num[t] = 0.0;
+    // the strong F neighbours in ascending order
+    int nf = 0;
+    for (int c0 = b; c0 < e; c0 += 32) {
+      const int p = c0 + lane;
+      const bool f = p < e && ci[p] != i && S[p] && !cf[ci[p]];
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (f) flist[nf + __popc(bal & lt)] = p;
+      nf += __popc(bal);
+    }
     __syncwarp();
-    for (int p = b + lane; p < e; p += 32) {
+    for (int f = lane; f < nf; f += 32) {  // d_k, a lane per strong F neighbour
+      const int p = flist[f], k = ci[p];
+      double dk = 0.0;
+      for (int q = rp[k]; q < rp[k + 1]; ++q) {
+        const int l = ci[q];
+        const double v = a[q];
+        if (l != k && v < 0.0 && (l == i || key_pos(table, rank, T, l) >= 0)) dk = __dadd_rn(dk, v);
+      }
+      dv[p - b] = dk;
+    }
+    __syncwarp();
+    for (int p = b + lane; p < e; p += 32) {  // each entry's term of at; numerators start at a_ij
       const int k = ci[p];
-      int c = 0;
-      double dk = 0.0, ak = 0.0;
+      int c = 0;  // bit 0: a term of at; bit 1: a strong F neighbour with d_k != 0
+      double term = 0.0;
       if (k != i) {
         if (S[p] && !cf[k]) {
-          c = 1;
-          for (int q = rp[k]; q < rp[k + 1]; ++q) {
-            const int l = ci[q];
-            const double v = a[q];
-            if (l == i) ak = v;
-            if (l != k && v < 0.0 && (l == i || key_pos(keys, m, l) >= 0)) dk = __dadd_rn(dk, v);
+          const double dk = dv[p - b];
+          if (dk != 0.0) {
+            c = 2;
+            const int q = find_col(ci, rp[k], rp[k + 1], i);
+            if (q >= 0 && a[q] < 0.0) {
+              term = __ddiv_rn(__dmul_rn(a[p], a[q]), dk);
+              c |= 1;
+            }
+          } else {
+            term = a[p];
+            c = 1;
           }
-        } else if (!S[p]) {
-          c = (cf[k] && key_pos(keys, m, k) >= 0) ? 0 : 2;
+        } else if (!S[p] && !(cf[k] && key_pos(table, rank, T, k) >= 0)) {
+          term = a[p];
+          c = 1;
         }
-        const int t = key_pos(keys, m, k);  // numerators start at a_ij
+        const int t = key_pos(table, rank, T, k);
         if (t >= 0) num[t] = a[p];
       }
       code[p - b] = c;
-      dv[p - b] = dk;
-      aki[p - b] = ak;
+      cv[p - b] = term;
     }
     __syncwarp();
     double at = 0.0;
     if (lane == 0) {
       const int pd = find_col(ci, b, e, i);
       at = pd >= 0 ? a[pd] : 0.0;
-      for (int p = b; p < e; ++p) {
-        const int c = code[p - b];
-        if (c == 1) {
-          const double dk = dv[p - b], ak = aki[p - b];
-          if (dk != 0.0) {
-            if (ak < 0.0) at = __dadd_rn(at, __ddiv_rn(__dmul_rn(a[p], ak), dk));
-          } else {
-            at = __dadd_rn(at, a[p]);
-          }
-        } else if (c == 2) {
-          at = __dadd_rn(at, a[p]);
-        }
-      }
+      for (int p = b; p < e; ++p)
+        if (code[p - b] & 1) at = __dadd_rn(at, cv[p - b]);
       if (at == 0.0) flags[0] = 1;
     }
     at = __shfl_sync(0xffffffffu, at, 0);
-    for (int p = b; p < e; ++p) {  // strong F neighbours in ascending order
-      if (code[p - b] != 1) continue;
-      const double dk = dv[p - b];
-      if (dk == 0.0) continue;
-      const int k = ci[p];
-      const double aik = a[p];
-      for (int q = rp[k] + lane; q < rp[k + 1]; q += 32) {
-        const double v = a[q];
-        if (v < 0.0 && ci[q] != k) {
-          const int t = key_pos(keys, m, ci[q]);
-          if (t >= 0) num[t] = __dadd_rn(num[t], __ddiv_rn(__dmul_rn(aik, v), dk));
-        }
+    // numerator terms in batches: gather, divide (lanes dense), add in k order
+    int fill = 0, nseg = 0;
+    auto flush = [&]() {
+      if (lane == 0) sstart[nseg] = fill;
+      __syncwarp();
+      for (int x = lane; x < fill; x += 32) {
+        const int pp = sp[bs[x]];
+        bv[x] = __ddiv_rn(__dmul_rn(a[pp], bv[x]), dv[pp - b]);
       }
       __syncwarp();
+      for (int sg = 0; sg < nseg; ++sg) {
+        for (int x = sstart[sg] + lane; x < sstart[sg + 1]; x += 32) num[bt[x]] = __dadd_rn(num[bt[x]], bv[x]);
+        __syncwarp();
+      }
+      fill = 0;
+      nseg = 0;
+    };
+    for (int f = 0; f < nf; ++f) {
+      const int p = flist[f];
+      if (!(code[p - b] & 2)) continue;
+      const int k = ci[p];
+      bool open = false;  // a segment of this k is open in the current batch
+      for (int c0 = rp[k]; c0 < rp[k + 1]; c0 += 32) {
+        if (fill + 32 > kExtBatch || (!open && nseg == kExtSegs)) {
+          flush();
+          open = false;
+        }
+        if (!open) {
+          if (lane == 0) {
+            sstart[nseg] = fill;
+            sp[nseg] = p;
+          }
+          ++nseg;
+          open = true;
+        }
+        const int q = c0 + lane;
+        int t = -1;
+        if (q < rp[k + 1] && a[q] < 0.0 && ci[q] != k) t = key_pos(table, rank, T, ci[q]);
+        const unsigned bal = __ballot_sync(0xffffffffu, t >= 0);
+        if (t >= 0) {
+          const int x = fill + __popc(bal & lt);
+          bt[x] = t;
+          bv[x] = a[q];
+          bs[x] = nseg - 1;
+        }
+        fill += __popc(bal);
+      }
     }
+    if (nseg > 0) flush();
+    __syncwarp();
     const int off = prp[i];
     for (int t = lane; t < m; t += 32) {
       pci[off + t] = cidx[keys[t]];
@@ -1516,7 +1601,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     const int g = ceil_div(n, TPB);
     DCsr &P = L.P;
     if (prm.interp == AMG_INTERP_EXT) {
-      Buf<int> mx(m, 2), eflag(m, 1), pcnt(m, n);
+      Buf<int> mx(m, 2), eflag(m, 2), pcnt(m, n);  // eflag[0]: at = 0; eflag[1]: largest |Chat_i|
       AMG_CUDA(cudaMemsetAsync(mx.p, 0, 2 * sizeof(int), s));
       AMG_CUDA(cudaMemsetAsync(eflag.p, 0, sizeof(int), s));
       {
@@ -1529,21 +1614,30 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       int hmx[2];
       AMG_CUDA(cudaMemcpyAsync(hmx, mx.p, sizeof(hmx), cudaMemcpyDeviceToHost, s));
       AMG_CUDA(cudaStreamSynchronize(s));
+      // the count pass sizes its set by the candidate bound (repeats counted),
+      // the fill pass by the largest distinct count the count pass found
+      auto geometry = [&](int T, bool fill, int *wpb_out) {
+        const size_t per = ext_warp_bytes(T, std::max(hmx[1], 1), fill);
+        const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kExtWarps, (size_t)(200 * 1024) / per));
+        if (per * wpb > 200 * 1024)
+          fail(AMG_ERR_UNSUPPORTED, "extended+i: a row's interpolatory candidates exceed the shared-memory set");
+        *wpb_out = wpb;
+        return per * wpb;
+      };
       int T = 32;
       while (T <= hmx[0]) T <<= 1;  // a free slot always remains
-      const size_t per = ext_warp_bytes(T, std::max(hmx[1], 1));
-      const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kExtWarps, (size_t)(200 * 1024) / per));
-      const size_t smem = per * wpb;
-      if (smem > 200 * 1024) fail(AMG_ERR_UNSUPPORTED, "extended+i: a row's interpolatory candidates exceed the shared-memory set");
       static std::atomic<unsigned long long> attr_c{0}, attr_f{0};
       ensure_smem_attr(k_ext_interp<false>, 200 * 1024, attr_c);
       ensure_smem_attr(k_ext_interp<true>, 200 * 1024, attr_f);
-      const int grid = std::max(1, std::min(ceil_div(n, wpb), kNumSMs * 16));
+      AMG_CUDA(cudaMemsetAsync(eflag.p, 0, 2 * sizeof(int), s));
       {
+        int wpb = 1;
+        const size_t smem = geometry(T, false, &wpb);
+        const int grid = std::max(1, std::min(ceil_div(n, wpb), kNumSMs * 16));
         ProfScope ps(s, AMG_K_INTERP, 4.0 * (n + 1) + 5.0 * A.nnz + 5.0 * n, k);
         k_ext_interp<false><<<grid, wpb * 32, smem, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, T,
-                                                                std::max(hmx[1], 1), pcnt.p, nullptr, nullptr,
-                                                                nullptr, eflag.p);
+                                                          std::max(hmx[1], 1), pcnt.p, nullptr, nullptr,
+                                                          nullptr, eflag.p);
         AMG_CHECK_LAUNCH();
       }
       P.n = n;
@@ -1552,11 +1646,19 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
       P.nnz = scan_counts(m, pcnt.p, P.rp, n);
       P.ci = m.get_n<int>(std::max<int64_t>(P.nnz, 1));
       P.v = m.get_n<double>(std::max<int64_t>(P.nnz, 1));
+      int hm2[2];
+      AMG_CUDA(cudaMemcpyAsync(hm2, eflag.p, sizeof(hm2), cudaMemcpyDeviceToHost, s));
+      AMG_CUDA(cudaStreamSynchronize(s));
+      int T2 = 32;
+      while (T2 <= 2 * hm2[1]) T2 <<= 1;  // the set at most half full
+      T2 = std::min(T2, T);
       {
+        int wpb = 1;
+        const size_t smem = geometry(T2, true, &wpb);
+        const int grid = std::max(1, std::min(ceil_div(n, wpb), kNumSMs * 16));
         ProfScope ps(s, AMG_K_INTERP, 8.0 * (n + 1) + 13.0 * A.nnz + 5.0 * n + 12.0 * P.nnz, k);
-        k_ext_interp<true><<<grid, wpb * 32, smem, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, T,
-                                                               std::max(hmx[1], 1), nullptr, P.rp, P.ci, P.v,
-                                                               eflag.p);
+        k_ext_interp<true><<<grid, wpb * 32, smem, s>>>(n, A.rp, A.ci, A.v, S.p, L.cf, cidx.p, T2,
+                                                         std::max(hmx[1], 1), nullptr, P.rp, P.ci, P.v, eflag.p);
         AMG_CHECK_LAUNCH();
       }
       int he = 0;

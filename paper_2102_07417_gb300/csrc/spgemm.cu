@@ -24,7 +24,9 @@
 //   tier 6    ub <= 4096   a block per row, 8192-slot table in shared memory;
 //   tier 7    larger       a block per row, table in a global scratch slice;
 //   tier 8    X row <= 8 entries and ub <= 64 (taken first): a thread per
-//                          row merging the row's sorted Y rows.
+//                          row merging the row's sorted Y rows.  (Splitting it
+//                          into lists by ub, for similar step counts per warp,
+//                          measured slower: 1.52 against 1.35 ms at level 0.)
 // (A thread-per-row variant with a private accumulator in shared memory for
 // every short row was bit-exact but twice as slow over a 128^3 set-up: its
 // lanes gather Y entries of 32 different rows at once, uncoalesced.)
@@ -661,10 +663,11 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, const SlotRows *ys
   const double xy_bytes = 4.0 * (rows + 1) + 12.0 * (double)X.nnz + ybytes + (yslot ? ybytes : 0.0);
   {
     ProfScope ps(s, AMG_K_SPGEMM, xy_bytes, level);
-    if (hm[T_THREAD] > 0) {
-      const int grid = std::max(1, std::min(ceil_div(hm[T_THREAD], TPB), kNumSMs * 16));
-      k_spgemm_merge<<<grid, TPB, 0, s>>>(list(T_THREAD), hm[T_THREAD], X.rp, X.ci, X.v, y, Y.ci, Y.v, off.p,
-                                          tci.p, tcv.p, cnt.p);
+    for (int t = T_THREAD; t <= T_THREAD; ++t) {
+      if (hm[t] == 0) continue;
+      const int grid = std::max(1, std::min(ceil_div(hm[t], TPB), kNumSMs * 16));
+      k_spgemm_merge<<<grid, TPB, 0, s>>>(list(t), hm[t], X.rp, X.ci, X.v, y, Y.ci, Y.v, off.p, tci.p, tcv.p,
+                                          cnt.p);
       AMG_CHECK_LAUNCH();
     }
     if (hm[0] > 0) {
