@@ -283,18 +283,9 @@ void build_fsai(amg_hierarchy *h, int k);
 // R = P^T with rows sorted (setup.cu)
 void csr_transpose(Mem &m, const DCsr &P, int ncols, DCsr &R);
 
-// A product left in slot form: row i at [rp[i], rp[i] + cnt[i]) of its arrays;
-// nnz (device) = sum of the counts, filled in stream order.
-struct SlotRows {
-  Buf<int> cnt;
-  Buf<long long> nnz;
-};
 // C = X Y with the canonical summation order (spgemm.cu); flags: device error
-// flags.  yslot: Y is in slot form (its arrays in Y, its counts here).  cslot:
-// leave C in slot form (C.rp = row offsets, C.nnz = slot capacity) instead of
-// compacting it into CSR.  level: hierarchy level for the profiler.
-void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, const SlotRows *yslot, int ncols, DCsr &C, int level,
-            SlotRows *cslot);
+// flags; level: hierarchy level for the profiler.
+void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C, int level);
 
 // device-wide exclusive scan of n int32 counts into out[0..n] (out[n] = total); returns total
 int64_t scan_counts(Mem &mem, const int *in, int *out, int n);

@@ -1692,12 +1692,9 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
     ST.reset();
     cidx.reset();
     transpose(m, P, nc, L.R);
-    DCsr AP;  // A P stays in the product's slot form; R (A P) reads it so
-    {
-      SlotRows ap;
-      spgemm(m, fl.d, A, P, nullptr, nc, AP, k, &ap);
-      spgemm(m, fl.d, L.R, AP, &ap, nc, h->lev[k + 1].A, k, nullptr);
-    }
+    DCsr AP;
+    spgemm(m, fl.d, A, P, nc, AP, k);
+    spgemm(m, fl.d, L.R, AP, nc, h->lev[k + 1].A, k);
     free_csr(m, AP);
     // the SpGEMM's overflow flag is read with the next level's first flag
     // read (every level reads its flags at least once), not with a sync here

@@ -9,10 +9,12 @@
 //
 // One numeric pass.  Each row i gets ub_i = sum_{p in X_i} nnz(Y_{k_p})
 // slots of scratch (an upper bound on its distinct columns); the row's sorted
-// columns and sums are written there with their count.  A P stays in that
-// slot form (row i at off[i], cnt[i] entries) and is read so by R (A P); the
-// coarse operator is compacted into CSR.  Rows are binned by ub_i into tiers
-// (lists filled tile by tile, so neighbouring warps work on neighbouring rows):
+// columns and sums are written there with their count, and a compaction
+// copies the rows into CSR.  (Leaving A P in that slot form for R (A P) to
+// read skips its compaction but doubles its footprint; at the 128^3 level 0
+// R (A P) then read 2.8 GB from DRAM and ran 1.5x longer.)  Rows are binned by
+// ub_i into tiers (lists filled tile by tile, so neighbouring warps work on
+// neighbouring rows):
 //   tier 0    ub <= 32     a warp per row, one candidate product per lane in
 //                          registers; duplicates found with __match_any_sync,
 //                          each group summed by its lowest lane in lane order
@@ -85,12 +87,11 @@ __device__ __forceinline__ int next_pow2(int v) {
 }
 
 
-// Rows of the right operand Y: [rp[k], rp[k] + cnt[k]) in slot form (cnt set),
-// else [rp[k], rp[k + 1]).
+// Rows of the right operand Y: [rp[k], rp[k + 1]).
 struct YRows {
-  const int *rp, *cnt;
+  const int *rp;
   __device__ __forceinline__ int b(int k) const { return rp[k]; }
-  __device__ __forceinline__ int e(int k) const { return cnt ? rp[k] + cnt[k] : rp[k + 1]; }
+  __device__ __forceinline__ int e(int k) const { return rp[k + 1]; }
 };
 
 // ------------------------------------------------------------- binning ----
@@ -561,15 +562,6 @@ __global__ void __launch_bounds__(TPB) k_compact(int m, const int *__restrict__ 
   }
 }
 
-// Sum of the per-row counts (the entries of a product left in slot form).
-__global__ void k_sum_counts(int m, const int *__restrict__ cnt, long long *total) {
-  long long s = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) s += cnt[i];
-#pragma unroll
-  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-  if ((threadIdx.x & 31) == 0 && s) atomicAdd(reinterpret_cast<unsigned long long *>(total), (unsigned long long)s);
-}
-
 template <int TAB>
 constexpr size_t hash_smem() {
   return (size_t)WARPS * 3 * TAB * sizeof(int);
@@ -600,12 +592,11 @@ void launch_hash(int nr, const int *list, const Args &a) {
 
 }  // namespace
 
-void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, const SlotRows *yslot, int ncols, DCsr &C, int level,
-            SlotRows *cslot) {
+void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C, int level) {
   cudaStream_t s = m.stream;
   const int rows = X.n;
   const int ntiles = ceil_div(rows, TILE);
-  const YRows y{Y.rp, yslot ? yslot->cnt.p : nullptr};
+  const YRows y{Y.rp};
   Buf<int> ub(m, (size_t)rows + 1), off(m, (size_t)rows + 1), lists(m, (size_t)std::max(rows, 1));
   Buf<int8_t> tier(m, (size_t)std::max(rows, 1));
   Buf<int> meta(m, 2 * NTIER + 1);  // per-tier row counts, max ub of the global tier, list cursors
@@ -620,14 +611,13 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, const SlotRows *ys
     else k_row_ub<32><<<grid, TPB, 0, s>>>(rows, X.rp, X.ci, y, ub.p, tier.p, meta.p, flags);
     AMG_CHECK_LAUNCH();
   }
-  // the scan's total, the tier counts and Y's entry count come back in one synchronisation
+  // the scan's total and the tier counts come back in one synchronisation
   Buf<long long> ub_tot(m, 1);
   scan_counts_async(m, ub.p, off.p, rows, ub_tot.p);
   int hm[NTIER + 1];
-  long long total_ub = 0, ynnz = Y.nnz;
+  long long total_ub = 0;
   AMG_CUDA(cudaMemcpyAsync(hm, meta.p, sizeof(hm), cudaMemcpyDeviceToHost, s));
   AMG_CUDA(cudaMemcpyAsync(&total_ub, ub_tot.p, sizeof(total_ub), cudaMemcpyDeviceToHost, s));
-  if (yslot) AMG_CUDA(cudaMemcpyAsync(&ynnz, yslot->nnz.p, sizeof(ynnz), cudaMemcpyDeviceToHost, s));
   AMG_CUDA(cudaStreamSynchronize(s));
   check_scan_total(total_ub);
   if (hm[NTIER] > (1 << 22)) {
@@ -656,11 +646,9 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, const SlotRows *ys
   Buf<int> cnt(m, (size_t)rows + 1);
   auto list = [&](int t) { return lists.p + start[t]; };
   const Args a{&X, y, Y.ci, Y.v, off.p, tci.p, tcv.p, cnt.p, flags, s};
-  // Algorithmic bytes (the byte model of A_c = R (A P)): X and Y read once; C
-  // written once -- charged here for a product left in slot form (A P) when it
-  // is read by the next product, and by the compaction for the coarse operator.
-  const double ybytes = 4.0 * (Y.n + 1) + (yslot ? 4.0 * Y.n : 0.0) + 12.0 * (double)ynnz;
-  const double xy_bytes = 4.0 * (rows + 1) + 12.0 * (double)X.nnz + ybytes + (yslot ? ybytes : 0.0);
+  // Algorithmic bytes (the byte model of A_c = R (A P)): X and Y read once
+  // here, C written once (charged to the compaction).
+  const double xy_bytes = 4.0 * (rows + 1) + 12.0 * (double)X.nnz + 4.0 * (Y.n + 1) + 12.0 * (double)Y.nnz;
   {
     ProfScope ps(s, AMG_K_SPGEMM, xy_bytes, level);
     for (int t = T_THREAD; t <= T_THREAD; ++t) {
@@ -694,20 +682,6 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, const SlotRows *ys
   }
   C.n = rows;
   C.ncols = ncols;
-  if (cslot) {  // leave C in slot form: row i at off[i], cnt[i] entries
-    C.rp = off.release();
-    C.ci = tci.release();
-    C.v = tcv.release();
-    C.nnz = total_ub;  // capacity of the slots
-    cslot->cnt = std::move(cnt);
-    cslot->nnz = Buf<long long>(m, 1);
-    AMG_CUDA(cudaMemsetAsync(cslot->nnz.p, 0, sizeof(long long), s));
-    ProfScope ps(s, AMG_K_SPGEMM, 0.0, level);
-    k_sum_counts<<<std::max(1, std::min(ceil_div(rows, TPB), kNumSMs * 4)), TPB, 0, s>>>(rows, cslot->cnt.p,
-                                                                                       cslot->nnz.p);
-    AMG_CHECK_LAUNCH();
-    return;
-  }
   C.rp = m.get_n<int>((size_t)rows + 1);
   C.nnz = scan_counts(m, cnt.p, C.rp, rows);
   C.ci = m.get_n<int>(std::max<int64_t>(C.nnz, 1));
