@@ -515,8 +515,10 @@ def run_gpu(args, rank, world, dist):
         "cop": info["cop"], "hierarchy_bytes": rec["bytes"], "x_rel_err": x_err,
         "solves_per_s_all_ranks": world * 1e3 / ms,
         "roofline": roof,
-        "vcycle_hbm": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s", "peak": peak,
-                       "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None},
+        "vcycle_hbm": vcycle_back_to_back(params, A_dev, stream, dev),
+        "vcycle_hbm_profiled": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s", "peak": peak,
+                                "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None,
+                                "note": "summed per-launch event times of the profiled step (gaps included)"},
         "profile_pass": {"note": "one extra step with events around every launch (not timed)",
                          "kernels_ms": kernels, "by_level_ms": by_level},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
@@ -524,6 +526,47 @@ def run_gpu(args, rank, world, dist):
         "config3": config3,
     }
     print(json.dumps(out), flush=True)
+
+
+def vcycle_back_to_back(params, A_dev, stream, dev, reps: int = 20):
+    """The V-cycle's HBM rate without per-launch events: one V-cycle applied with events around
+    every launch gives its algorithmic bytes, then `reps` V-cycles are applied back to back (after
+    3 untimed) with events only around the loop.  The profiled pass's per-launch events leave gaps
+    between the V-cycle's short launches, so its summed time overstates the V-cycle's.  The
+    level-0 matrix is larger than L2, as in the solve."""
+    import torch
+
+    from paper_2102_07417_gb300 import amg
+
+    h = amg.Hierarchy(A_dev, params, stream=stream)
+    try:
+        g = torch.Generator().manual_seed(7)
+        y = (torch.rand(A_dev.n, generator=g, dtype=torch.float64) * 2 - 1).to(dev)
+        z = torch.empty_like(y)
+        for _ in range(3):
+            h.vcycle(y, z, stream=stream)
+        torch.cuda.synchronize()
+        amg.profile(True)
+        h.vcycle(y, z, stream=stream)
+        torch.cuda.synchronize()
+        amg.profile(False)
+        prof = amg.profile_read()
+        by = sum(prof[k]["bytes"] for k in VCYCLE)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            h.vcycle(y, z, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+    finally:
+        h.close()
+    peak, peak_src = peaks()
+    gbs = by / (ms * 1e-3) / 1e9
+    return {"achieved": gbs, "unit": "GB/s", "peak": peak, "frac": gbs / peak, "peak_source": f"{peak_src} hbm_gbs",
+            "ms_per_vcycle": ms, "bytes_per_vcycle": by, "vcycles_timed": reps,
+            "method": "V-cycles applied back to back (amg_vcycle_apply), events around the loop only"}
 
 
 def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, prec_id=None, name=None, **kw):
@@ -578,8 +621,9 @@ def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, prec_id=None, name=No
     return {"precision": name, "t_setup_ms": tp, "t_solve_ms": ts,
             "t_total_ms": tp + ts, "iters": rec["iters"], "status": rec["status"], "x_rel_err": x_err,
             "steps": len(times), "cgd": rec["info"]["cgd"], "cop": rec["info"]["cop"],
-            "vcycle_hbm": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s", "peak": peak,
-                           "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None},
+            "vcycle_hbm": vcycle_back_to_back(params, A_dev, stream, dev),
+            "vcycle_hbm_profiled": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s",
+                                    "peak": peak, "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None},
             "profiled_kernels_ms": {k: round(v["ms"], 4) for k, v in prof.items() if v["launches"]}}
 
 
@@ -640,9 +684,10 @@ def run_config3(args, stream, dev, with_oracle):
            "rtol": args.rtol, "t_setup_ms": tp, "t_solve_ms": ts, "t_total_ms": tp + ts, "iters": rec["iters"],
            "status": rec["status"], "nlevels": rec["info"]["nlevels"], "cop": rec["info"]["cop"],
            "steps": len(times), "host_generation_s": t_gen, "clocks": clocks,
-           "vcycle_hbm": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s", "peak": peak,
-                          "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None,
-                          "peak_source": f"{peak_src} hbm_gbs"},
+           "vcycle_hbm": vcycle_back_to_back(params, A_dev, stream, dev),
+           "vcycle_hbm_profiled": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s",
+                                   "peak": peak, "frac": (vb / (vt * 1e-3) / 1e9) / peak if vt else None,
+                                   "peak_source": f"{peak_src} hbm_gbs"},
            "profile_pass_kernels_ms": kernels}
     if with_oracle:
         from oracle import oracle as O

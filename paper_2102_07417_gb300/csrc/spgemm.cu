@@ -20,15 +20,17 @@
 //                          each group summed by its lowest lane in lane order
 //                          (lane order = p order, so the sum is canonical);
 //   tier 1-5  ub <= 64 ... 1024   a warp per row, a shared-memory hash set of
-//                          2 ub_max slots (128 ... 2048), keys bitonic-sorted,
-//                          products staged in shared memory and summed 32 at a
-//                          time, equal columns grouped and added in p order;
+//                          2 ub_max slots (128 ... 2048) with a running sum
+//                          per slot; products fetched 32 at a time, equal
+//                          columns grouped and added in p order; the columns
+//                          bitonic-sorted at the end;
 //   tier 6    ub <= 4096   a block per row, 8192-slot table in shared memory;
 //   tier 7    larger       a block per row, table in a global scratch slice;
-//   tier 8    X row <= 8 entries and ub <= 64 (taken first): a thread per
-//                          row merging the row's sorted Y rows.  (Splitting it
-//                          into lists by ub, for similar step counts per warp,
-//                          measured slower: 1.52 against 1.35 ms at level 0.)
+//   tier 8    X row <= 8 entries and ub <= 64 (taken first when X has at least
+//                          2^16 rows): a thread per row merging the row's
+//                          sorted Y rows.  (Splitting it into lists by ub, for
+//                          similar step counts per warp, measured slower: 1.52
+//                          against 1.35 ms at level 0.)
 // (A thread-per-row variant with a private accumulator in shared memory for
 // every short row was bit-exact but twice as slow over a 128^3 set-up: its
 // lanes gather Y entries of 32 different rows at once, uncoalesced.)
@@ -53,32 +55,48 @@ constexpr int MERGE_L = 8;   // longest X row of the merge tier
 constexpr int BTAB = 8192;  // tier-6 table slots
 constexpr int TILE = 1024;  // rows per binning tile
 
-__device__ __forceinline__ int tier_of(int64_t ub, int xlen) {
-  if (xlen <= MERGE_L && ub <= 64) return T_THREAD;
+// The merge tier serialises a row's products in one thread: it is taken only
+// when X has enough rows to fill the GPU with threads (on the coarse levels'
+// few rows the warp tiers finish several times sooner).
+constexpr int MERGE_MIN_ROWS = 1 << 16;
+
+__device__ __forceinline__ int tier_of(int64_t ub, int xlen, bool merge_ok) {
+  if (merge_ok && xlen <= MERGE_L && ub <= 64) return T_THREAD;
   return ub <= 32 ? 0 : ub <= 64 ? 1 : ub <= 128 ? 2 : ub <= 256 ? 3 : ub <= 512 ? 4 : ub <= 1024 ? 5
          : ub <= 4096 ? 6 : T_GLOBAL;
 }
 
-// flags[3] is set on a full hash table (cannot happen while ub <= slots / 2).
-__device__ __forceinline__ void hash_insert(int *table, unsigned mask, int key, int *flags) {
+// Inserts key into an open-addressing set (linear probing) and returns its
+// slot; flags[3] is set, and -1 returned, on a full table (cannot happen while
+// ub <= slots / 2).
+__device__ __forceinline__ int hash_insert_slot(int *table, unsigned mask, int key, int *flags) {
   unsigned h = ((unsigned)key * 2654435761u) & mask;
   for (unsigned probe = 0; probe <= mask; ++probe) {
     const int prev = atomicCAS(&table[h], -1, key);
-    if (prev == -1 || prev == key) return;
+    if (prev == -1 || prev == key) return (int)h;
     h = (h + 1) & mask;
   }
   flags[3] = 1;
+  return -1;
 }
 
-__device__ __forceinline__ int lower_bound(const int *a, int len, int key) {
-  int lo = 0, hi = len;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (a[mid] < key) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
+// Slot of a key known to be in the table.
+__device__ __forceinline__ int hash_find(const int *table, unsigned mask, int key) {
+  unsigned h = ((unsigned)key * 2654435761u) & mask;
+  for (unsigned probe = 0; probe < mask && table[h] != key; ++probe) h = (h + 1) & mask;
+  return (int)h;
 }
+
+// Running sums start from -0.0 instead of the canonical +0.0: -0.0 + w == w
+// exactly for every w, so the first product of a column is assigned rather
+// than added (one FP64 add saved per output entry), and the two sequences
+// agree at every step except while every product so far was -0.0 (then the
+// canonical sum is +0.0: it never takes the value -0.0, since it starts at
+// +0.0 and rounding to nearest gives +0.0 for x + (-x)).  canon0() maps the
+// final -0.0 back to +0.0.
+constexpr long long NEG0_BITS = (long long)0x8000000000000000ull;
+__device__ __forceinline__ bool is_neg0(double a) { return __double_as_longlong(a) == NEG0_BITS; }
+__device__ __forceinline__ double canon0(double a) { return is_neg0(a) ? 0.0 : a; }
 
 __device__ __forceinline__ int next_pow2(int v) {
   int p = 1;
@@ -126,7 +144,7 @@ __global__ void __launch_bounds__(TPB) k_row_ub(int m, const int *__restrict__ x
         ub = 1 << 30;
       }
       ub_out[i] = (int)ub;
-      const int t = tier_of(ub, xrp[i + 1] - xrp[i]);
+      const int t = tier_of(ub, xrp[i + 1] - xrp[i], m >= MERGE_MIN_ROWS);
       tier[i] = (int8_t)t;
       atomicAdd(&cnt[t], 1);
       if (t == T_GLOBAL) atomicMax(&tcount[NTIER], (int)ub);
@@ -290,20 +308,21 @@ __global__ void __launch_bounds__(TPB) k_spgemm_merge(const int *__restrict__ ro
           hp[t] = q + 1;
           hc[t] = cn;
         }
-      if (bc != ccol) {
+      if (bc != ccol) {  // a new column: its sum starts as -0.0 + prod == prod
         if (ccol >= 0) {
           tci[base + count] = ccol;
-          tcv[base + count] = acc;
+          tcv[base + count] = canon0(acc);
           ++count;
         }
         ccol = bc;
-        acc = 0.0;
+        acc = prod;
+      } else {
+        acc = __dadd_rn(acc, prod);
       }
-      acc = __dadd_rn(acc, prod);
     }
     if (ccol >= 0) {
       tci[base + count] = ccol;
-      tcv[base + count] = acc;
+      tcv[base + count] = canon0(acc);
       ++count;
     }
     cnt[i] = count;
@@ -349,9 +368,10 @@ __global__ void __launch_bounds__(TPB) k_spgemm_reg(const int *__restrict__ rows
       rank += ((lmask >> j) & 1u) && kj < key;
     }
     const int maxg = (int)__reduce_max_sync(FULL, leader ? (unsigned)__popc(grp) : 0u);
-    double acc = 0.0;
-    unsigned mm = grp;
-    for (int it = 0; it < maxg; ++it) {
+    // the leader is its group's first member: the sum starts as -0.0 + val == val
+    double acc = val;
+    unsigned mm = grp & (grp - 1u);
+    for (int it = 1; it < maxg; ++it) {
       const int sl = mm ? __ffs(mm) - 1 : lane;
       const double v = __shfl_sync(FULL, val, sl);
       if (leader && mm) acc = __dadd_rn(acc, v);
@@ -360,21 +380,26 @@ __global__ void __launch_bounds__(TPB) k_spgemm_reg(const int *__restrict__ rows
     const int base = off[i];
     if (leader) {
       tci[base + rank] = key;
-      tcv[base + rank] = acc;
+      tcv[base + rank] = canon0(acc);
     }
     if (lane == 0) cnt[i] = __popc(lmask);
   }
 }
 
 // -------------------------------------------------------- tiers 1-5 ----
-// Shared memory per warp (TAB = 2 x the tier's largest ub):
-//   table[TAB] hash set (then TAB/2 double accumulators), keys[TAB/2] the
-//   row's distinct columns (then sorted), pk[TAB/2] / pv[TAB/2] the row's
-//   products in (p, q) order: column and rounded product x_ip * y_qJ.
-// The products are fetched in one flattened pass (all lanes busy), then summed
-// into the accumulators 32 at a time: lanes holding the same column form a
-// group (__match_any_sync) whose lowest lane adds the members in lane order,
-// which is p order -- the canonical order.
+// Shared memory per warp (TAB = 2 x the tier's largest ub): acc[TAB] the
+// running sum of each slot's column (doubles), table[TAB] the hash set of the
+// row's columns, keys[TAB/2] the distinct columns (then sorted).
+// The products are fetched 32 at a time in (p, q) order over the whole row
+// (all lanes busy), each inserted into the set and added into its slot's sum
+// at once: lanes holding the same column form a group (__match_any_sync)
+// whose lowest lane adds the members in lane order, which is p order -- the
+// canonical order.  The sorted columns then find their sums by their slots.
+template <int TAB>
+constexpr size_t hash_smem_warp() {
+  return (size_t)TAB * sizeof(double) + (size_t)(TAB + TAB / 2) * sizeof(int);
+}
+
 template <int TAB>
 __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ rows, int nrows,
                                                      const int *__restrict__ xrp, const int *__restrict__ xci,
@@ -382,21 +407,20 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
                                                      const int *__restrict__ yci, const double *__restrict__ yv,
                                                      const int *__restrict__ off, int *__restrict__ tci,
                                                      double *__restrict__ tcv, int *__restrict__ cnt, int *flags) {
-  constexpr int HALF = TAB / 2;
   extern __shared__ __align__(16) int smem_i[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int *table = smem_i + warp * (3 * TAB);
+  double *acc = reinterpret_cast<double *>(smem_i) + (size_t)warp * TAB;
+  int *table = smem_i + 2 * WARPS * TAB + warp * (TAB + TAB / 2);
   int *keys = table + TAB;
-  int *pk = keys + HALF;
-  double *pv = reinterpret_cast<double *>(pk + HALF);
-  double *acc = reinterpret_cast<double *>(table);
   const int gw = blockIdx.x * WARPS + warp, nw = gridDim.x * WARPS;
   for (int r = gw; r < nrows; r += nw) {
     const int i = rows[r];
-    for (int t = lane; t < TAB; t += 32) table[t] = -1;
+    for (int t = lane; t < TAB; t += 32) {
+      table[t] = -1;
+      acc[t] = -0.0;
+    }
     __syncwarp();
     const int xb = xrp[i], xe = xrp[i + 1];
-    int nprod = 0;
     for (int c0 = xb; c0 < xe; c0 += 32) {
       int total;
       const XChunk c = x_chunk(c0, xe, xci, xv, y, lane, &total);
@@ -405,15 +429,35 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
         const int src = x_source(c, u);
         const int ys = __shfl_sync(FULL, c.ys, src), ex = __shfl_sync(FULL, c.excl, src);
         const double xs = __shfl_sync(FULL, c.xv, src);
+        int slot = -1;
+        double v = 0.0;
         if (u < total) {
           const int q = ys + u - ex;
-          const int key = yci[q];
-          pk[nprod + u] = key;
-          pv[nprod + u] = __dmul_rn(xs, yv[q]);
-          hash_insert(table, TAB - 1, key, flags);
+          v = __dmul_rn(xs, yv[q]);
+          slot = hash_insert_slot(table, TAB - 1, yci[q], flags);
         }
+        const bool valid = slot >= 0;
+        if (!valid) slot = -1 - lane;  // a group of its own
+        const unsigned grp = __match_any_sync(FULL, slot);
+        const bool leader = valid && (__ffs(grp) - 1) == lane;
+        const int maxg = (int)__reduce_max_sync(FULL, leader ? (unsigned)__popc(grp) : 0u);
+        double a = leader ? acc[slot] : 0.0;
+        unsigned mm = grp;
+        for (int it = 0; it < maxg; ++it) {
+          const int sl = mm ? __ffs(mm) - 1 : lane;
+          const double w = __shfl_sync(FULL, v, sl);
+          const bool add = leader && mm != 0u;
+          // a sum still at -0.0 takes w without an add (-0.0 + w == w)
+          if (__any_sync(FULL, add && !is_neg0(a))) {
+            if (add) a = is_neg0(a) ? w : __dadd_rn(a, w);
+          } else if (add) {
+            a = w;
+          }
+          mm &= mm - 1u;
+        }
+        if (leader) acc[slot] = a;
+        __syncwarp();
       }
-      nprod += total;
     }
     __syncwarp();
     int count = 0;
@@ -440,31 +484,11 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
         }
         __syncwarp();
       }
-    for (int e = lane; e < count; e += 32) acc[e] = 0.0;
-    __syncwarp();
-    for (int t0 = 0; t0 < nprod; t0 += 32) {
-      const int t = t0 + lane;
-      const bool valid = t < nprod;
-      const int pos = valid ? lower_bound(keys, count, pk[t]) : -1 - lane;
-      const double v = valid ? pv[t] : 0.0;
-      const unsigned grp = __match_any_sync(FULL, pos);
-      const bool leader = valid && (__ffs(grp) - 1) == lane;
-      const int maxg = (int)__reduce_max_sync(FULL, leader ? (unsigned)__popc(grp) : 0u);
-      double a = leader ? acc[pos] : 0.0;
-      unsigned mm = grp;
-      for (int it = 0; it < maxg; ++it) {
-        const int sl = mm ? __ffs(mm) - 1 : lane;
-        const double w = __shfl_sync(FULL, v, sl);
-        if (leader && mm) a = __dadd_rn(a, w);
-        mm &= mm - 1u;
-      }
-      if (leader) acc[pos] = a;
-      __syncwarp();
-    }
     const int base = off[i];
     for (int e = lane; e < count; e += 32) {
-      tci[base + e] = keys[e];
-      tcv[base + e] = acc[e];
+      const int key = keys[e];
+      tci[base + e] = key;
+      tcv[base + e] = canon0(acc[hash_find(table, TAB - 1, key)]);
     }
     if (lane == 0) cnt[i] = count;
     __syncwarp();
@@ -472,9 +496,13 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
 }
 
 // -------------------------------------------------------- tiers 6-7 ----
-// A block per row; table of `cap` slots (then cap/2 double accumulators) and
-// cap/2 keys, in shared memory (GLOBAL = false, cap = BTAB) or in this block's
-// slice of global scratch (GLOBAL = true).
+// A block per row: acc[cap] running sums (doubles) indexed by the hash slot,
+// table[cap] the hash set and keys[cap/2] the distinct columns, in shared
+// memory (GLOBAL = false, cap = BTAB) or in this block's slices of global
+// scratch (GLOBAL = true).  One pass over the row's X entries in order: the
+// threads split Y row k_p (distinct columns, so no two threads meet on a
+// slot), insert each column and add the product into its slot's sum; a
+// barrier between X entries keeps every column's sum in p order.
 template <bool GLOBAL>
 __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ rows, int nrows,
                                                       const int *__restrict__ xrp, const int *__restrict__ xci,
@@ -482,24 +510,35 @@ __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ ro
                                                       const int *__restrict__ yci, const double *__restrict__ yv,
                                                       const int *__restrict__ off, int *__restrict__ tci,
                                                       double *__restrict__ tcv, int *__restrict__ cnt, int *flags,
-                                                      int *gscratch, int gcap) {
+                                                      int *gscratch, double *gacc, int gcap) {
   extern __shared__ __align__(16) int smem_b[];
   __shared__ int s_count;
   const int cap = GLOBAL ? gcap : BTAB;
-  int *table = GLOBAL ? gscratch + (size_t)blockIdx.x * ((size_t)cap + cap / 2) : smem_b;
+  double *acc = GLOBAL ? gacc + (size_t)blockIdx.x * cap : reinterpret_cast<double *>(smem_b);
+  int *table = GLOBAL ? gscratch + (size_t)blockIdx.x * ((size_t)cap + cap / 2) : smem_b + 2 * BTAB;
   int *keys = table + cap;
-  double *acc = reinterpret_cast<double *>(table);
   for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int i = rows[r];
-    for (int t = threadIdx.x; t < cap; t += blockDim.x) table[t] = -1;
+    for (int t = threadIdx.x; t < cap; t += blockDim.x) {
+      table[t] = -1;
+      acc[t] = -0.0;
+    }
     if (threadIdx.x == 0) s_count = 0;
     __syncthreads();
     const int xb = xrp[i], xe = xrp[i + 1];
     for (int p = xb; p < xe; ++p) {
       const int k = xci[p];
-      for (int q = y.b(k) + threadIdx.x; q < y.e(k); q += blockDim.x) hash_insert(table, cap - 1, yci[q], flags);
+      const double x = xv[p];
+      for (int q = y.b(k) + threadIdx.x; q < y.e(k); q += blockDim.x) {
+        const int slot = hash_insert_slot(table, cap - 1, yci[q], flags);
+        if (slot >= 0) {
+          const double w = __dmul_rn(x, yv[q]);
+          const double a = acc[slot];
+          acc[slot] = is_neg0(a) ? w : __dadd_rn(a, w);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
     for (int t = threadIdx.x; t < cap; t += blockDim.x) {
       const int key = table[t];
       if (key >= 0) keys[atomicAdd(&s_count, 1)] = key;
@@ -523,21 +562,11 @@ __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ ro
         }
         __syncthreads();
       }
-    for (int e = threadIdx.x; e < count; e += blockDim.x) acc[e] = 0.0;
-    __syncthreads();
-    for (int p = xb; p < xe; ++p) {
-      const int k = xci[p];
-      const double x = xv[p];
-      for (int q = y.b(k) + threadIdx.x; q < y.e(k); q += blockDim.x) {
-        const int pos = lower_bound(keys, count, yci[q]);
-        acc[pos] = __dadd_rn(acc[pos], __dmul_rn(x, yv[q]));
-      }
-      __syncthreads();
-    }
     const int base = off[i];
     for (int e = threadIdx.x; e < count; e += blockDim.x) {
-      tci[base + e] = keys[e];
-      tcv[base + e] = acc[e];
+      const int key = keys[e];
+      tci[base + e] = key;
+      tcv[base + e] = canon0(acc[hash_find(table, cap - 1, key)]);
     }
     if (threadIdx.x == 0) cnt[i] = count;
     __syncthreads();
@@ -564,9 +593,10 @@ __global__ void __launch_bounds__(TPB) k_compact(int m, const int *__restrict__ 
 
 template <int TAB>
 constexpr size_t hash_smem() {
-  return (size_t)WARPS * 3 * TAB * sizeof(int);
+  return (size_t)WARPS * hash_smem_warp<TAB>();
 }
-constexpr size_t block_smem = (size_t)(BTAB + BTAB / 2) * sizeof(int);
+static_assert(hash_smem<2048>() <= 232448, "tier-5 shared memory above the per-block limit");
+constexpr size_t block_smem = (size_t)BTAB * sizeof(double) + (size_t)(BTAB + BTAB / 2) * sizeof(int);
 
 struct Args {
   const DCsr *X;
@@ -638,7 +668,11 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
   while (gcap < 2 * std::max(hm[NTIER], 1)) gcap <<= 1;
   const int gblocks = std::min(hm[T_GLOBAL], kNumSMs * 2);
   Buf<int> gscr;
-  if (hm[T_GLOBAL] > 0) gscr = Buf<int>(m, (size_t)gblocks * ((size_t)gcap + gcap / 2));
+  Buf<double> gacc;
+  if (hm[T_GLOBAL] > 0) {
+    gscr = Buf<int>(m, (size_t)gblocks * ((size_t)gcap + gcap / 2));
+    gacc = Buf<double>(m, (size_t)gblocks * gcap);
+  }
   static std::atomic<unsigned long long> attr{0};
   ensure_smem_attr(k_spgemm_block<false>, (int)block_smem, attr);
   Buf<int> tci(m, (size_t)std::max<int64_t>(total_ub, 1));
@@ -671,12 +705,12 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
     if (hm[6] > 0) {
       const int grid = std::max(1, std::min(hm[6], kNumSMs * 4));
       k_spgemm_block<false><<<grid, TPB, block_smem, s>>>(list(6), hm[6], X.rp, X.ci, X.v, y, Y.ci, Y.v, off.p,
-                                                          tci.p, tcv.p, cnt.p, flags, nullptr, 0);
+                                                          tci.p, tcv.p, cnt.p, flags, nullptr, nullptr, 0);
       AMG_CHECK_LAUNCH();
     }
     if (hm[T_GLOBAL] > 0) {
       k_spgemm_block<true><<<gblocks, TPB, 0, s>>>(list(T_GLOBAL), hm[T_GLOBAL], X.rp, X.ci, X.v, y, Y.ci, Y.v, off.p,
-                                                   tci.p, tcv.p, cnt.p, flags, gscr.p, gcap);
+                                                   tci.p, tcv.p, cnt.p, flags, gscr.p, gacc.p, gcap);
       AMG_CHECK_LAUNCH();
     }
   }
