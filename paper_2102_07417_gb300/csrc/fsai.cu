@@ -9,12 +9,16 @@
 // A[P_i, P_i] g = e_last scaled to (G A G^T)_ii = 1.  With the Cholesky
 // factor A[P_i, P_i] = L L^T that scaled solution is g = L^-T e_last, so each
 // row costs one dense Cholesky of its principal submatrix and one triangular
-// solve:
-//   rows of at most 4 or 8 lower entries: a thread per row, the submatrix in
-//   registers (the 7-point operators' finest levels: 4 entries);
-//   longer rows: a warp per row, the submatrix in a per-warp slice of shared
-//   memory (global scratch when a slice does not fit), factored right-looking
-//   by the lanes.
+// solve; rows are binned by m:
+//   m <= 8: a thread per row, the submatrix in registers (the 7-point
+//   operators' finest levels: 4 entries);
+//   m <= 16 / m <= 32: 8 / 16 lanes per row, the submatrix in a per-row slice
+//   of shared memory, factored right-looking by the row's lanes;
+//   longer: a warp per row, the submatrix in a per-warp slice of shared
+//   memory (global scratch when a slice does not fit).
+// Each pivot takes one reciprocal square root, kept on the diagonal of the
+// factor, in place of a square root and a division (FP64 square roots and
+// divisions are instruction sequences on GB300's narrow FP64 pipe).
 // G^T is stored too (a CSR transpose), its values scaled by omega, so that a
 // smoothing step is u = G w, s += (omega G^T) u.
 #include <cuda_runtime.h>
@@ -28,7 +32,6 @@ namespace amg {
 namespace {
 
 constexpr int TPB = 256;
-constexpr int kThreadRows = 16;  // longest lower row taken by the thread-per-row kernel
 
 // cnt[i] = number of stored entries of row i with column <= i; flags[0] when
 // the last of them is not the diagonal.  *mmax receives the largest count.
@@ -49,13 +52,17 @@ __global__ void k_fsai_count(int n, const int *__restrict__ rp, const int *__res
   atomicMax(mmax, m);
 }
 
-// Thread per row, rows of at most MM lower entries.  flags[1]: a non-positive pivot.
+// Thread per row, rows of at most MM lower entries, the submatrix in
+// registers; rows (may be null: rows 0..nrows-1) lists the rows to take.
+// flags[1]: a non-positive pivot.
 template <int MM>
-__global__ void __launch_bounds__(TPB) k_fsai_rows(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+__global__ void __launch_bounds__(TPB) k_fsai_rows(int nrows, const int *__restrict__ rows,
+                                                   const int *__restrict__ rp, const int *__restrict__ ci,
                                                    const double *__restrict__ a, const int *__restrict__ grp,
                                                    int *__restrict__ gci, double *__restrict__ gv, int *flags) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int r0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r0 >= nrows) return;
+  const int i = rows ? rows[r0] : r0;
   const int b = rp[i], o = grp[i], m = grp[i + 1] - o;
   int P[MM];
   double M[MM][MM];
@@ -82,15 +89,15 @@ __global__ void __launch_bounds__(TPB) k_fsai_rows(int n, const int *__restrict_
 #pragma unroll
     for (int k = 0; k < j; ++k) d -= M[j][k] * M[j][k];
     ok = ok && d > 0.0;
-    const double l = sqrt(d > 0.0 ? d : 1.0);
-    M[j][j] = l;
+    const double inv = rsqrt(d > 0.0 ? d : 1.0);  // 1 / l_jj, kept on the diagonal
+    M[j][j] = inv;
 #pragma unroll
     for (int r = j + 1; r < MM; ++r) {
       if (r >= m) break;
       double s = M[r][j];
 #pragma unroll
       for (int k = 0; k < j; ++k) s -= M[r][k] * M[j][k];
-      M[r][j] = s / l;
+      M[r][j] = s * inv;
     }
   }
   if (!ok) flags[1] = 1;
@@ -102,7 +109,7 @@ __global__ void __launch_bounds__(TPB) k_fsai_rows(int n, const int *__restrict_
 #pragma unroll
     for (int l = k + 1; l < MM; ++l)
       if (l < m) s -= M[l][k] * g[l];
-    g[k] = s / M[k][k];
+    g[k] = s * M[k][k];
   }
 #pragma unroll
   for (int r = 0; r < MM; ++r)
@@ -128,8 +135,12 @@ __device__ __forceinline__ double warp_sum(double v) {
 //     prefix of the parts' lengths); an entry of column l lands at
 //     M[r][c] with P_i[c] = l (binary search in P_i);
 //   factor: right-looking Cholesky, column j scaled by the lanes, then the
-//     trailing lower triangle updated with independent multiply-adds;
-//   solve: L^T g = e_last backwards, one warp sum per component.
+//     trailing lower triangle updated with independent multiply-adds, its
+//     (r, c) pairs spread over the lanes as one flat list; each pivot takes
+//     one reciprocal square root (kept on the diagonal), not a square root
+//     and a division: FP64 square roots and divisions are instruction
+//     sequences on GB300's narrow FP64 pipe, and all lanes compute the pivot;
+//   solve: L^T g = e_last backwards by columns (no warp sums).
 template <bool SMEM>
 __global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict__ rows, const int *__restrict__ rp,
                                                    const int *__restrict__ ci,
@@ -201,15 +212,28 @@ __global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict_
       for (int j = 0; j < m; ++j) {
         const double d = M[(size_t)j * ld + j];
         ok = ok && d > 0.0;
-        const double l = sqrt(d > 0.0 ? d : 1.0), inv = 1.0 / l;
+        const double inv = rsqrt(d > 0.0 ? d : 1.0);  // 1 / l_jj, kept on the diagonal
         __syncwarp();
         for (int r = j + 1 + lane; r < m; r += 32) M[(size_t)r * ld + j] *= inv;
-        if (lane == 0) M[(size_t)j * ld + j] = l;
+        if (lane == 0) M[(size_t)j * ld + j] = inv;
         __syncwarp();
-        for (int r = j + 1 + lane; r < m; r += 32) {  // trailing update of row r: columns j+1..r
-          double *Mr = M + (size_t)r * ld;
-          const double lrj = Mr[j];
-          for (int c = j + 1; c <= r; ++c) Mr[c] -= lrj * M[(size_t)c * ld + j];
+        // trailing lower triangle (rows and columns j+1..m-1) as one flat list
+        // of (r, c) pairs, t = r'(r'+1)/2 + c' with r' = r - j - 1, c' = c - j - 1,
+        // so every lane has work while any pair is left
+        const int sz = m - j - 1, npair = sz * (sz + 1) / 2;
+        int rr = 0, cc = lane;
+        while (cc > rr) {
+          cc -= rr + 1;
+          ++rr;
+        }
+        for (int t = lane; t < npair; t += 32) {
+          const int r = j + 1 + rr, c = j + 1 + cc;
+          M[(size_t)r * ld + c] -= M[(size_t)r * ld + j] * M[(size_t)c * ld + j];
+          cc += 32;
+          while (cc > rr) {
+            cc -= rr + 1;
+            ++rr;
+          }
         }
         __syncwarp();
       }
@@ -220,7 +244,7 @@ __global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict_
         for (int k = lane; k < j; k += 32) d += Mj[k] * Mj[k];
         d = Mj[j] - warp_sum(d);
         ok = ok && d > 0.0;
-        const double l = sqrt(d > 0.0 ? d : 1.0), inv = 1.0 / l;
+        const double inv = rsqrt(d > 0.0 ? d : 1.0);
         for (int r = j + 1 + lane; r < m; r += 32) {
           double *Mr = M + (size_t)r * ld;
           double sum = Mr[j];
@@ -228,17 +252,21 @@ __global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict_
           Mr[j] = sum * inv;
         }
         __syncwarp();
-        if (lane == 0) M[(size_t)j * ld + j] = l;
+        if (lane == 0) M[(size_t)j * ld + j] = inv;
         __syncwarp();
       }
     }
     if (!ok && lane == 0) flags[1] = 1;
-    // L^T g = e_last, backwards: g_k = (e_k - sum_{l > k} L_lk g_l) / L_kk
+    // L^T g = e_last, backwards by columns: once g_k = rhs_k / l_kk is known,
+    // rhs_l -= l_kl g_k for every l < k (the lanes split the l)
+    for (int t = lane; t < m; t += 32) g[t] = t == m - 1 ? 1.0 : 0.0;
+    __syncwarp();
     for (int k = m - 1; k >= 0; --k) {
-      double s = 0.0;
-      for (int l = k + 1 + lane; l < m; l += 32) s += M[(size_t)l * ld + k] * g[l];
-      s = warp_sum(s);
-      if (lane == 0) g[k] = ((k == m - 1 ? 1.0 : 0.0) - s) / M[(size_t)k * ld + k];
+      const double gk = g[k] * M[(size_t)k * ld + k];
+      __syncwarp();
+      const double *Mk = M + (size_t)k * ld;
+      for (int l = lane; l < k; l += 32) g[l] -= Mk[l] * gk;
+      if (lane == 0) g[k] = gk;
       __syncwarp();
     }
     for (int r = lane; r < m; r += 32) {
@@ -249,98 +277,155 @@ __global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict_
   }
 }
 
-// Thread per row for rows of at most ld lower entries: the submatrix in the
-// thread's slice of shared memory, interleaved across the block's threads
-// (element e of thread t at e * NT + t, so a warp's accesses hit distinct
-// banks).  Every FP64 operation of the factor and the solve is then done by
-// all lanes of a warp at once: GB300 issues FP64 per warp at a small fraction
-// of the FP32 rate, so a factor spread over the lanes of one row (the warp
-// kernel) spends most of its FP64 issue slots on idle lanes.  rows (may be
-// null: all rows) lists the rows to take.
-__global__ void k_fsai_thread(int n, const int *__restrict__ rows, int nrows, const int *__restrict__ rp,
-                              const int *__restrict__ ci, const double *__restrict__ a, const int *__restrict__ grp,
-                              int *__restrict__ gci, double *__restrict__ gv, int ld, int *flags) {
-  extern __shared__ __align__(16) double fsai_tsmem[];
-  const int NT = blockDim.x, t = threadIdx.x;
-  double *M = fsai_tsmem;              // M[(r * ld + c) * NT + t]
-  double *g = fsai_tsmem + (size_t)ld * ld * NT;  // g[k * NT + t]
-  for (int r0 = blockIdx.x * NT + t; r0 < nrows; r0 += gridDim.x * NT) {
-    const int i = rows ? rows[r0] : r0;
-    const int b = rp[i], o = grp[i], m = grp[i + 1] - o;
-    const int *P = ci + b;  // the row's lower part, ascending, ending at i
-    for (int r = 0; r < m; ++r) {
-      // row P[r] and P[0..r] are both ascending: one merge walk
+// G lanes per row (32 / G rows per warp) for rows of at most LD lower
+// entries.  Each row has a slice of LD * LD + 2 LD + 1 doubles in shared
+// memory (the submatrix, g, P_i as ints; the odd length staggers the slices'
+// banks): the lanes gather the rows of A[P_i, P_i] (each lane walks rows r,
+// r + G, ... of P_i), factor it right-looking with the trailing triangle's
+// (r, c) pairs spread over the row's lanes, one reciprocal square root per
+// pivot, and solve L^T g = e_last by columns.  Several short rows per warp
+// keep its lanes busy (a warp per row leaves most idle on rows of ~10
+// entries) while the per-row slices stay small enough for many warps per SM.
+// The rows of a warp step through the factor together (up to the warp's
+// longest row), so its __syncwarp()s are reached by every lane.
+template <int G, int LD>
+__global__ void __launch_bounds__(TPB) k_fsai_group(int nrows, const int *__restrict__ rows,
+                                                    const int *__restrict__ rp, const int *__restrict__ ci,
+                                                    const double *__restrict__ a, const int *__restrict__ grp,
+                                                    int *__restrict__ gci, double *__restrict__ gv, int *flags) {
+  constexpr int RPW = 32 / G;
+  constexpr int SLICE = LD * LD + 2 * LD + 1;
+  extern __shared__ __align__(16) double fsai_gsmem[];
+  const int lane = threadIdx.x & 31, sub = lane & (G - 1);
+  double *M = fsai_gsmem + (size_t)(threadIdx.x / G) * SLICE;
+  double *g = M + LD * LD;
+  int *P = reinterpret_cast<int *>(g + LD);
+  const int wg = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+  bool ok = true;
+  for (int base = wg * RPW; base < nrows; base += nwarps * RPW) {  // warp-uniform
+    const int r0 = base + lane / G;
+    int b = 0, o = 0, m = 0;
+    if (r0 < nrows) {
+      const int i = rows[r0];
+      b = rp[i];
+      o = grp[i];
+      m = grp[i + 1] - o;
+    }
+    const int mw = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
+    for (int t = sub; t < m; t += G) P[t] = ci[b + t];
+    for (int t = sub; t < m * LD; t += G) M[t] = 0.0;
+    __syncwarp();
+    for (int r = sub; r < m; r += G) {  // row P[r]: its columns P[c] (c <= r) are <= P[r]
       const int row = P[r];
-      int q = rp[row], c = 0;
-      while (c <= r) {
-        const int col = ci[q];
-        if (col == P[c]) {
-          M[(size_t)(r * ld + c) * NT + t] = a[q];
-          ++c;
-          ++q;
-        } else if (col < P[c]) {
-          ++q;
-        } else {
-          M[(size_t)(r * ld + c) * NT + t] = 0.0;
-          ++c;
+      for (int q = rp[row], qe = rp[row + 1]; q < qe; ++q) {
+        const int l = ci[q];
+        if (l > row) break;
+        int lo = 0, hi = r;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (P[mid] < l) lo = mid + 1;
+          else hi = mid;
+        }
+        if (P[lo] == l) M[r * LD + lo] = a[q];
+      }
+    }
+    __syncwarp();
+    for (int j = 0; j < mw; ++j) {
+      const bool act = j < m;
+      double inv = 0.0;
+      if (act) {
+        const double d = M[j * LD + j];
+        ok = ok && d > 0.0;
+        inv = rsqrt(d > 0.0 ? d : 1.0);  // 1 / l_jj, kept on the diagonal
+      }
+      __syncwarp();
+      if (act) {
+        for (int r = j + 1 + sub; r < m; r += G) M[r * LD + j] *= inv;
+        if (sub == 0) M[j * LD + j] = inv;
+      }
+      __syncwarp();
+      if (act) {  // pair t = r'(r'+1)/2 + c' of the trailing triangle, r' = r - j - 1
+        const int sz = m - j - 1, npair = sz * (sz + 1) / 2;
+        int rr = 0, cc = sub;
+        while (cc > rr) {
+          cc -= rr + 1;
+          ++rr;
+        }
+        for (int t = sub; t < npair; t += G) {
+          const int r = j + 1 + rr, c = j + 1 + cc;
+          M[r * LD + c] -= M[r * LD + j] * M[c * LD + j];
+          cc += G;
+          while (cc > rr) {
+            cc -= rr + 1;
+            ++rr;
+          }
         }
       }
+      __syncwarp();
     }
-    bool ok = true;
-    for (int j = 0; j < m; ++j) {  // left-looking Cholesky, one multiply by 1/l_jj per entry
-      double d = M[(size_t)(j * ld + j) * NT + t];
-      for (int k = 0; k < j; ++k) {
-        const double v = M[(size_t)(j * ld + k) * NT + t];
-        d -= v * v;
+    for (int t = sub; t < m; t += G) g[t] = t == m - 1 ? 1.0 : 0.0;
+    __syncwarp();
+    for (int k = mw - 1; k >= 0; --k) {  // L^T g = e_last by columns
+      const bool act = k < m;
+      const double gk = act ? g[k] * M[k * LD + k] : 0.0;
+      __syncwarp();
+      if (act) {
+        for (int l = sub; l < k; l += G) g[l] -= M[k * LD + l] * gk;
+        if (sub == 0) g[k] = gk;
       }
-      ok = ok && d > 0.0;
-      const double l = sqrt(d > 0.0 ? d : 1.0), inv = 1.0 / l;
-      M[(size_t)(j * ld + j) * NT + t] = l;
-      for (int r = j + 1; r < m; ++r) {
-        double s = M[(size_t)(r * ld + j) * NT + t];
-        for (int k = 0; k < j; ++k) s -= M[(size_t)(r * ld + k) * NT + t] * M[(size_t)(j * ld + k) * NT + t];
-        M[(size_t)(r * ld + j) * NT + t] = s * inv;
-      }
+      __syncwarp();
     }
-    if (!ok) flags[1] = 1;
-    for (int k = m - 1; k >= 0; --k) {  // L^T g = e_last
-      double s = k == m - 1 ? 1.0 : 0.0;
-      for (int l = k + 1; l < m; ++l) s -= M[(size_t)(l * ld + k) * NT + t] * g[(size_t)l * NT + t];
-      g[(size_t)k * NT + t] = s / M[(size_t)(k * ld + k) * NT + t];
-    }
-    for (int r = 0; r < m; ++r) {
+    for (int r = sub; r < m; r += G) {
       gci[o + r] = P[r];
-      gv[o + r] = g[(size_t)r * NT + t];
+      gv[o + r] = g[r];
     }
+    __syncwarp();
   }
+  if (!ok) flags[1] = 1;
 }
 
-// Rows of at most lim lower entries to list s, the others to list l (counts in
-// ns, nl); tiles of the block append with one atomic each.
-__global__ void k_fsai_split(int n, const int *__restrict__ grp, int lim, int *__restrict__ ls, int *ns,
-                             int *__restrict__ ll, int *nl) {
-  __shared__ int cs, cl, bs, bl;
-  if (threadIdx.x == 0) cs = cl = 0;
+template <int G, int LD>
+constexpr size_t group_slice_bytes() {
+  return (size_t)(LD * LD + 2 * LD + 1) * sizeof(double);
+}
+
+// Rows binned by their lower-entry count m: bin 0 m <= 8, 1 m <= 16,
+// 2 m <= 32, 3 longer; list b at lists + b * n, its count in counts[b].
+// Tiles of the block append with one atomic per bin.
+__global__ void k_fsai_bin(int n, const int *__restrict__ grp, int *__restrict__ lists, int *counts) {
+  __shared__ int c[4], base[4];
+  if (threadIdx.x < 4) c[threadIdx.x] = 0;
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = i < n;
-  const bool small = live && grp[i + 1] - grp[i] <= lim;
-  int ps = -1, pl = -1;
-  if (live && small) ps = atomicAdd(&cs, 1);
-  if (live && !small) pl = atomicAdd(&cl, 1);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    bs = cs ? atomicAdd(ns, cs) : 0;
-    bl = cl ? atomicAdd(nl, cl) : 0;
+  int bin = -1, pos = 0;
+  if (i < n) {
+    const int m = grp[i + 1] - grp[i];
+    bin = m <= 8 ? 0 : m <= 16 ? 1 : m <= 32 ? 2 : 3;
+    pos = atomicAdd(&c[bin], 1);
   }
   __syncthreads();
-  if (ps >= 0) ls[bs + ps] = i;
-  if (pl >= 0) ll[bl + pl] = i;
+  if (threadIdx.x < 4) base[threadIdx.x] = c[threadIdx.x] ? atomicAdd(&counts[threadIdx.x], c[threadIdx.x]) : 0;
+  __syncthreads();
+  if (bin >= 0) lists[(size_t)bin * n + base[bin] + pos] = i;
 }
 
 __global__ void k_scale(int64_t n, double f, double *__restrict__ v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     v[i] *= f;
+}
+
+// Rows of a list with at most LD lower entries, G lanes each, blocks of tpb
+// threads (tpb / G row slices of shared memory per block).
+template <int G, int LD>
+void launch_group(const int *rows, int nrows, int tpb, const DCsr &A, DCsr &G_, int *flags, cudaStream_t s) {
+  const size_t smem = (size_t)(tpb / G) * group_slice_bytes<G, LD>();
+  static std::atomic<unsigned long long> attr{0};
+  ensure_smem_attr(k_fsai_group<G, LD>, (int)smem, attr);
+  const int rows_per_block = tpb / G;
+  const int blocks = std::max(1, std::min(ceil_div(nrows, rows_per_block), kNumSMs * 16));
+  k_fsai_group<G, LD><<<blocks, tpb, smem, s>>>(nrows, rows, A.rp, A.ci, A.v, G_.rp, G_.ci, G_.v, flags);
+  AMG_CHECK_LAUNCH();
 }
 
 }  // namespace
@@ -375,49 +460,47 @@ void build_fsai(amg_hierarchy *h, int k) {
   {
     // bytes: A's lower rows gathered (once per use, ~m per row), G written
     ProfScope ps(s, AMG_K_FSAI, 4.0 * (n + 1) + 12.0 * (double)A.nnz + 4.0 * (n + 1) + 12.0 * (double)G.nnz, k);
-    auto launch_thread = [&](const int *rows, int nrows, int ld) {
-      const size_t per = ((size_t)ld * ld + ld) * sizeof(double);  // per thread
-      const int nt = (int)std::max<size_t>(32, std::min<size_t>(256, (200 * 1024 / per) / 32 * 32));
-      static std::atomic<unsigned long long> attr{0};
-      ensure_smem_attr(k_fsai_thread, 200 * 1024, attr);
-      const int blocks = std::max(1, std::min(ceil_div(nrows, nt), kNumSMs * 8));
-      k_fsai_thread<<<blocks, nt, per * nt, s>>>(n, rows, nrows, A.rp, A.ci, A.v, G.rp, G.ci, G.v, ld, meta.p);
-      AMG_CHECK_LAUNCH();
-    };
     if (mmax <= 4) {
-      k_fsai_rows<4><<<ceil_div(n, TPB), TPB, 0, s>>>(n, A.rp, A.ci, A.v, G.rp, G.ci, G.v, meta.p);
+      k_fsai_rows<4><<<ceil_div(n, TPB), TPB, 0, s>>>(n, nullptr, A.rp, A.ci, A.v, G.rp, G.ci, G.v, meta.p);
     } else if (mmax <= 8) {
-      k_fsai_rows<8><<<ceil_div(n, TPB), TPB, 0, s>>>(n, A.rp, A.ci, A.v, G.rp, G.ci, G.v, meta.p);
-    } else if (mmax <= kThreadRows) {
-      launch_thread(nullptr, n, mmax);
+      k_fsai_rows<8><<<ceil_div(n, TPB), TPB, 0, s>>>(n, nullptr, A.rp, A.ci, A.v, G.rp, G.ci, G.v, meta.p);
     } else {
-      // rows of at most kThreadRows lower entries by the thread kernel, the
-      // others by the warp kernel
-      Buf<int> lsmall(m, n), llarge(m, n), nsl(m, 2);
-      AMG_CUDA(cudaMemsetAsync(nsl.p, 0, 2 * sizeof(int), s));
-      k_fsai_split<<<ceil_div(n, TPB), TPB, 0, s>>>(n, G.rp, kThreadRows, lsmall.p, nsl.p, llarge.p, nsl.p + 1);
+      // rows binned by m: registers (m <= 8), 8 lanes per row (m <= 16),
+      // 16 lanes per row (m <= 32), a warp per row (longer)
+      Buf<int> lists(m, 4 * (size_t)n), cnts(m, 4);
+      AMG_CUDA(cudaMemsetAsync(cnts.p, 0, 4 * sizeof(int), s));
+      k_fsai_bin<<<ceil_div(n, TPB), TPB, 0, s>>>(n, G.rp, lists.p, cnts.p);
       AMG_CHECK_LAUNCH();
-      int hn[2];
-      AMG_CUDA(cudaMemcpyAsync(hn, nsl.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
+      int hn[4];
+      AMG_CUDA(cudaMemcpyAsync(hn, cnts.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
       AMG_CUDA(cudaStreamSynchronize(s));
-      if (hn[0] > 0) launch_thread(lsmall.p, hn[0], kThreadRows);
-      const int nbig = hn[1];
-      // slice per warp: ld * ld + 2 ld doubles (P_i's ints fit in the last ld)
-      const size_t slice = ((size_t)mmax * mmax + 2 * (size_t)mmax) * sizeof(double);
-      const int wpb = (int)std::min<size_t>(8, (size_t)(200 * 1024) / slice);
-      if (wpb >= 1) {  // shared memory
-        static std::atomic<unsigned long long> attr{0};
-        ensure_smem_attr(k_fsai_warp<true>, 200 * 1024, attr);
-        const int blocks = std::max(1, std::min(ceil_div(nbig, wpb), kNumSMs * 32));
-        k_fsai_warp<true><<<blocks, wpb * 32, slice * wpb, s>>>(nbig, llarge.p, A.rp, A.ci, A.v, G.rp, G.ci, G.v,
-                                                                 nullptr, mmax, blocks * wpb, meta.p);
-      } else {  // global scratch
-        const int64_t cap_warps = std::max<int64_t>(1, ((int64_t)256 << 20) / (int64_t)slice);
-        const int warps = (int)std::min<int64_t>({(int64_t)std::max(nbig, 1), (int64_t)kNumSMs * 16, cap_warps});
-        Buf<double> scr(m, slice / sizeof(double) * (size_t)warps);
-        k_fsai_warp<false><<<ceil_div((int64_t)warps * 32, TPB), TPB, 0, s>>>(nbig, llarge.p, A.rp, A.ci, A.v,
-                                                                             G.rp, G.ci, G.v, scr.p, mmax, warps,
-                                                                             meta.p);
+      if (hn[0] > 0) {
+        k_fsai_rows<8><<<ceil_div(hn[0], TPB), TPB, 0, s>>>(hn[0], lists.p, A.rp, A.ci, A.v, G.rp, G.ci, G.v,
+                                                            meta.p);
+        AMG_CHECK_LAUNCH();
+      }
+      if (hn[1] > 0) launch_group<8, 16>(lists.p + n, hn[1], TPB, A, G, meta.p, s);
+      if (hn[2] > 0) launch_group<16, 32>(lists.p + 2 * (size_t)n, hn[2], TPB / 2, A, G, meta.p, s);
+      const int nbig = hn[3];
+      const int *llarge = lists.p + 3 * (size_t)n;
+      if (nbig > 0) {
+        // slice per warp: ld * ld + 2 ld doubles (P_i's ints fit in the last ld)
+        const size_t slice = ((size_t)mmax * mmax + 2 * (size_t)mmax) * sizeof(double);
+        const int wpb = (int)std::min<size_t>(8, (size_t)(200 * 1024) / slice);
+        if (wpb >= 1) {  // shared memory
+          static std::atomic<unsigned long long> attr{0};
+          ensure_smem_attr(k_fsai_warp<true>, 200 * 1024, attr);
+          const int blocks = std::max(1, std::min(ceil_div(nbig, wpb), kNumSMs * 32));
+          k_fsai_warp<true><<<blocks, wpb * 32, slice * wpb, s>>>(nbig, llarge, A.rp, A.ci, A.v, G.rp, G.ci, G.v,
+                                                                   nullptr, mmax, blocks * wpb, meta.p);
+        } else {  // global scratch
+          const int64_t cap_warps = std::max<int64_t>(1, ((int64_t)256 << 20) / (int64_t)slice);
+          const int warps = (int)std::min<int64_t>({(int64_t)nbig, (int64_t)kNumSMs * 16, cap_warps});
+          Buf<double> scr(m, slice / sizeof(double) * (size_t)warps);
+          k_fsai_warp<false><<<ceil_div((int64_t)warps * 32, TPB), TPB, 0, s>>>(nbig, llarge, A.rp, A.ci, A.v,
+                                                                               G.rp, G.ci, G.v, scr.p, mmax, warps,
+                                                                               meta.p);
+        }
       }
     }
     AMG_CHECK_LAUNCH();
