@@ -231,6 +231,10 @@ struct amg_hierarchy {
   cudaGraphExec_t iter_exec = nullptr;
   const void *iter_x = nullptr, *iter_hist = nullptr;
   long long iter_launches = 0;
+  // amg_vcycle_apply's kernels, captured for one (y, z) pair and replayed
+  cudaGraphExec_t vc_exec = nullptr;
+  const void *vc_y = nullptr, *vc_z = nullptr;
+  long long vc_launches = 0;
   // dense operator of the V-cycle from level dense_level down (solve.cu), n x n
   // FP64 row-major with n = lev[dense_level].A.n; dense_level = -1: none
   int dense_level = -1;

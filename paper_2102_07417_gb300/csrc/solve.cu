@@ -1541,6 +1541,8 @@ void prepare_solve(amg_hierarchy *h) {
 void release_solve(amg_hierarchy *h) {
   if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
   h->iter_exec = nullptr;
+  if (h->vc_exec) cudaGraphExecDestroy(h->vc_exec);
+  h->vc_exec = nullptr;
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   h->cap_stream = nullptr;
   if (h->h_done) cudaFreeHost(h->h_done);
@@ -1560,13 +1562,54 @@ int pcg_solve(amg_hierarchy *h, const double *b, double *x, double rtol, int max
   }
 }
 
+// One V-cycle z = M^-1 y.  Unless its kernels are being event-timed, the
+// launches are captured once per (y, z) pair (on the hierarchy's capture
+// stream, which does not run them) and replayed as one graph launch: a
+// V-cycle's ~40 launches one by one are host-bound on the small levels (the
+// PCG iteration is replayed the same way).
 void vcycle_apply(amg_hierarchy *h, const double *y, double *z) {
-  switch (h->prm.precision) {
-    case AMG_PREC_FP64: vcycle_apply_impl<double, double>(h, y, z); break;
-    case AMG_PREC_FP32: vcycle_apply_impl<float, float>(h, y, z); break;
-    default: vcycle_apply_impl<float, __nv_bfloat16>(h, y, z); break;
+  auto run = [&]() {
+    switch (h->prm.precision) {
+      case AMG_PREC_FP64: vcycle_apply_impl<double, double>(h, y, z); break;
+      case AMG_PREC_FP32: vcycle_apply_impl<float, float>(h, y, z); break;
+      default: vcycle_apply_impl<float, __nv_bfloat16>(h, y, z); break;
+    }
+  };
+  cudaStream_t s = h->mem.stream;
+  if (prof_records_solve()) {
+    run();
+    prof_collect(s);
+    return;
   }
-  prof_collect(h->mem.stream);
+  if (h->vc_exec == nullptr || h->vc_y != y || h->vc_z != z) {
+    if (h->vc_exec) AMG_CUDA(cudaGraphExecDestroy(h->vc_exec));
+    h->vc_exec = nullptr;
+    if (!h->cap_stream) AMG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    const long long before = g_launches.load();
+    h->mem.stream = h->cap_stream;
+    AMG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      run();
+    } catch (...) {
+      cudaStreamEndCapture(h->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      h->mem.stream = s;
+      throw;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &g);
+    h->mem.stream = s;
+    AMG_CUDA(ec);
+    h->vc_launches = g_launches.load() - before;
+    g_launches.fetch_sub(h->vc_launches);
+    const cudaError_t ei = cudaGraphInstantiate(&h->vc_exec, g, 0);
+    cudaGraphDestroy(g);
+    AMG_CUDA(ei);
+    h->vc_y = y;
+    h->vc_z = z;
+  }
+  AMG_CUDA(cudaGraphLaunch(h->vc_exec, s));
+  g_launches.fetch_add(h->vc_launches);
 }
 
 void spmv_level(amg_hierarchy *h, int level, const double *x, double *y) {
