@@ -19,14 +19,22 @@
 //                          registers; duplicates found with __match_any_sync,
 //                          each group summed by its lowest lane in lane order
 //                          (lane order = p order, so the sum is canonical);
-//   tier 1-5  ub <= 64 ... 1024   a warp per row, a shared-memory hash set of
-//                          2 ub_max slots (128 ... 2048) with a running sum
-//                          per slot; products fetched 32 at a time, equal
-//                          columns grouped and added in p order; the columns
+//   tier 1-2  ub <= 64, 128   a warp per row, a shared-memory hash set of
+//                          2 ub_max slots (128, 256) with a running sum per
+//                          slot; products fetched 32 at a time, equal columns
+//                          grouped and added in p order; the columns
 //                          bitonic-sorted at the end;
-//   tier 6    ub <= 4096   a block per row, 8192-slot table in shared memory;
-//   tier 7    larger       a block per row, table in a global scratch slice;
-//   tier 8    X row <= 8 entries and ub <= 64 (taken first when X has at least
+//   tier 3    ub > 128     the same with 256 slots, sized for the columns a
+//                          row has rather than its product bound (Galerkin
+//                          rows have far fewer: at most 122 distinct columns
+//                          among the 128^3 Poisson rows with ub <= 4096); a
+//                          row that finds more than 128 is retried with 1024
+//                          slots, then with an exact table (2 ub slots) and
+//                          a block per row -- in shared memory for ub <=
+//                          4096, else in a global scratch slice.  (Tables of
+//                          2 ub slots for every row had left 16 warps per SM
+//                          at ub <= 512.)
+//   merge     X row <= 8 entries and ub <= 64 (taken first when X has at least
 //                          2^16 rows): a thread per row merging the row's
 //                          sorted Y rows.  (Splitting it into lists by ub, for
 //                          similar step counts per warp, measured slower: 1.52
@@ -48,11 +56,11 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int TPB = 256;
 constexpr int WARPS = TPB / 32;
-constexpr int NTIER = 9;
-constexpr int T_GLOBAL = 7;  // block per row, table in global scratch
-constexpr int T_THREAD = 8;  // thread per row, k-way merge
+constexpr int NTIER = 5;
+constexpr int T_OPT = 3;     // ub > 128: warp tables sized for the row's distinct columns, retried on overflow
+constexpr int T_THREAD = 4;  // thread per row, k-way merge
 constexpr int MERGE_L = 8;   // longest X row of the merge tier
-constexpr int BTAB = 8192;  // tier-6 table slots
+constexpr int BTAB = 8192;  // shared-memory table slots of the exact block tier (ub <= 4096)
 constexpr int TILE = 1024;  // rows per binning tile
 
 // The merge tier serialises a row's products in one thread: it is taken only
@@ -62,21 +70,25 @@ constexpr int MERGE_MIN_ROWS = 1 << 16;
 
 __device__ __forceinline__ int tier_of(int64_t ub, int xlen, bool merge_ok) {
   if (merge_ok && xlen <= MERGE_L && ub <= 64) return T_THREAD;
-  return ub <= 32 ? 0 : ub <= 64 ? 1 : ub <= 128 ? 2 : ub <= 256 ? 3 : ub <= 512 ? 4 : ub <= 1024 ? 5
-         : ub <= 4096 ? 6 : T_GLOBAL;
+  return ub <= 32 ? 0 : ub <= 64 ? 1 : ub <= 128 ? 2 : T_OPT;
 }
 
 // Inserts key into an open-addressing set (linear probing) and returns its
 // slot; flags[3] is set, and -1 returned, on a full table (cannot happen while
 // ub <= slots / 2).
-__device__ __forceinline__ int hash_insert_slot(int *table, unsigned mask, int key, int *flags) {
+// *added tells whether the key was new to the set.
+__device__ __forceinline__ int hash_insert_slot(int *table, unsigned mask, int key, int *flags, bool *added) {
   unsigned h = ((unsigned)key * 2654435761u) & mask;
   for (unsigned probe = 0; probe <= mask; ++probe) {
     const int prev = atomicCAS(&table[h], -1, key);
-    if (prev == -1 || prev == key) return (int)h;
+    if (prev == -1 || prev == key) {
+      *added = prev == -1;
+      return (int)h;
+    }
     h = (h + 1) & mask;
   }
   flags[3] = 1;
+  *added = false;
   return -1;
 }
 
@@ -117,7 +129,8 @@ struct YRows {
 // (G = 1 for short X rows, up to 32 for long ones: the coarse levels' rows are
 // long and few, and a thread walking a whole row left most SMs idle); the
 // row's tier; per-tier row counts (block-aggregated) and the largest ub of
-// the global tier in tcount[NTIER].
+// the T_OPT rows in tcount[NTIER].  ub_out receives the row's scratch slice
+// length, ub_i rounded up to 8.
 template <int G>
 __global__ void __launch_bounds__(TPB) k_row_ub(int m, const int *__restrict__ xrp, const int *__restrict__ xci,
                                                 YRows y, int *__restrict__ ub_out, int8_t *__restrict__ tier,
@@ -143,11 +156,15 @@ __global__ void __launch_bounds__(TPB) k_row_ub(int m, const int *__restrict__ x
         flags[3] = 1;
         ub = 1 << 30;
       }
-      ub_out[i] = (int)ub;
+      // the row's scratch slice, rounded up to 8 entries: every slice starts
+      // on a 32-byte sector of column indices (two of values), so no sector
+      // is shared by two rows written at different times (a partly written
+      // sector costs DRAM a read-modify-write when it leaves L2)
+      ub_out[i] = (int)((ub + 7) & ~(int64_t)7);
       const int t = tier_of(ub, xrp[i + 1] - xrp[i], m >= MERGE_MIN_ROWS);
       tier[i] = (int8_t)t;
       atomicAdd(&cnt[t], 1);
-      if (t == T_GLOBAL) atomicMax(&tcount[NTIER], (int)ub);
+      if (t == T_OPT) atomicMax(&tcount[NTIER], (int)ub);
     }
   }
   __syncthreads();
@@ -386,15 +403,22 @@ __global__ void __launch_bounds__(TPB) k_spgemm_reg(const int *__restrict__ rows
   }
 }
 
-// -------------------------------------------------------- tiers 1-5 ----
-// Shared memory per warp (TAB = 2 x the tier's largest ub): acc[TAB] the
-// running sum of each slot's column (doubles), table[TAB] the hash set of the
-// row's columns, keys[TAB/2] the distinct columns (then sorted).
+// ------------------------------------------------- hash tiers 1-3 ----
+// Shared memory per warp: acc[TAB] the running sum of each slot's column
+// (doubles), table[TAB] the hash set of the row's columns, keys[TAB/2] the
+// distinct columns (then sorted).
 // The products are fetched 32 at a time in (p, q) order over the whole row
 // (all lanes busy), each inserted into the set and added into its slot's sum
 // at once: lanes holding the same column form a group (__match_any_sync)
 // whose lowest lane adds the members in lane order, which is p order -- the
 // canonical order.  The sorted columns then find their sums by their slots.
+// A row may hold at most TAB/2 distinct columns.  The exact tiers (ub <=
+// TAB/2) never reach that.  With a retry list (the optimistic tier, tables
+// sized for the columns a row has rather than its product bound) a row that
+// passes the limit is dropped after that chunk -- at most TAB/2 + 31 keys are
+// then in the table, so probes always end -- and appended to the list for a
+// larger table.  nrows_dev (if set) holds the length of the row list, filled
+// by the previous kernel of the stream.
 template <int TAB>
 constexpr size_t hash_smem_warp() {
   return (size_t)TAB * sizeof(double) + (size_t)(TAB + TAB / 2) * sizeof(int);
@@ -402,16 +426,19 @@ constexpr size_t hash_smem_warp() {
 
 template <int TAB>
 __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ rows, int nrows,
+                                                     const int *__restrict__ nrows_dev,
                                                      const int *__restrict__ xrp, const int *__restrict__ xci,
                                                      const double *__restrict__ xv, YRows y,
                                                      const int *__restrict__ yci, const double *__restrict__ yv,
                                                      const int *__restrict__ off, int *__restrict__ tci,
-                                                     double *__restrict__ tcv, int *__restrict__ cnt, int *flags) {
+                                                     double *__restrict__ tcv, int *__restrict__ cnt, int *flags,
+                                                     int *__restrict__ retry, int *retry_n) {
   extern __shared__ __align__(16) int smem_i[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double *acc = reinterpret_cast<double *>(smem_i) + (size_t)warp * TAB;
   int *table = smem_i + 2 * WARPS * TAB + warp * (TAB + TAB / 2);
   int *keys = table + TAB;
+  if (nrows_dev) nrows = *nrows_dev;
   const int gw = blockIdx.x * WARPS + warp, nw = gridDim.x * WARPS;
   for (int r = gw; r < nrows; r += nw) {
     const int i = rows[r];
@@ -421,7 +448,9 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
     }
     __syncwarp();
     const int xb = xrp[i], xe = xrp[i + 1];
-    for (int c0 = xb; c0 < xe; c0 += 32) {
+    int ndist = 0;
+    bool over = false;
+    for (int c0 = xb; c0 < xe && !over; c0 += 32) {
       int total;
       const XChunk c = x_chunk(c0, xe, xci, xv, y, lane, &total);
       for (int u0 = 0; u0 < total; u0 += 32) {
@@ -430,12 +459,14 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
         const int ys = __shfl_sync(FULL, c.ys, src), ex = __shfl_sync(FULL, c.excl, src);
         const double xs = __shfl_sync(FULL, c.xv, src);
         int slot = -1;
+        bool added = false;
         double v = 0.0;
         if (u < total) {
           const int q = ys + u - ex;
           v = __dmul_rn(xs, yv[q]);
-          slot = hash_insert_slot(table, TAB - 1, yci[q], flags);
+          slot = hash_insert_slot(table, TAB - 1, yci[q], flags, &added);
         }
+        ndist += __popc(__ballot_sync(FULL, added));
         const bool valid = slot >= 0;
         if (!valid) slot = -1 - lane;  // a group of its own
         const unsigned grp = __match_any_sync(FULL, slot);
@@ -457,7 +488,19 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
         }
         if (leader) acc[slot] = a;
         __syncwarp();
+        if (ndist > TAB / 2) {
+          over = true;
+          break;
+        }
       }
+    }
+    if (over) {
+      if (lane == 0) {
+        if (retry) retry[atomicAdd(retry_n, 1)] = i;
+        else flags[3] = 1;
+      }
+      __syncwarp();
+      continue;
     }
     __syncwarp();
     int count = 0;
@@ -495,7 +538,7 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
   }
 }
 
-// -------------------------------------------------------- tiers 6-7 ----
+// ------------------------------------------- exact block-per-row retry ----
 // A block per row: acc[cap] running sums (doubles) indexed by the hash slot,
 // table[cap] the hash set and keys[cap/2] the distinct columns, in shared
 // memory (GLOBAL = false, cap = BTAB) or in this block's slices of global
@@ -505,6 +548,7 @@ __global__ void __launch_bounds__(TPB) k_spgemm_hash(const int *__restrict__ row
 // barrier between X entries keeps every column's sum in p order.
 template <bool GLOBAL>
 __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ rows, int nrows,
+                                                      const int *__restrict__ nrows_dev,
                                                       const int *__restrict__ xrp, const int *__restrict__ xci,
                                                       const double *__restrict__ xv, YRows y,
                                                       const int *__restrict__ yci, const double *__restrict__ yv,
@@ -517,6 +561,7 @@ __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ ro
   double *acc = GLOBAL ? gacc + (size_t)blockIdx.x * cap : reinterpret_cast<double *>(smem_b);
   int *table = GLOBAL ? gscratch + (size_t)blockIdx.x * ((size_t)cap + cap / 2) : smem_b + 2 * BTAB;
   int *keys = table + cap;
+  if (nrows_dev) nrows = *nrows_dev;
   for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int i = rows[r];
     for (int t = threadIdx.x; t < cap; t += blockDim.x) {
@@ -530,7 +575,8 @@ __global__ void __launch_bounds__(TPB) k_spgemm_block(const int *__restrict__ ro
       const int k = xci[p];
       const double x = xv[p];
       for (int q = y.b(k) + threadIdx.x; q < y.e(k); q += blockDim.x) {
-        const int slot = hash_insert_slot(table, cap - 1, yci[q], flags);
+        bool added;
+        const int slot = hash_insert_slot(table, cap - 1, yci[q], flags, &added);
         if (slot >= 0) {
           const double w = __dmul_rn(x, yv[q]);
           const double a = acc[slot];
@@ -595,7 +641,7 @@ template <int TAB>
 constexpr size_t hash_smem() {
   return (size_t)WARPS * hash_smem_warp<TAB>();
 }
-static_assert(hash_smem<2048>() <= 232448, "tier-5 shared memory above the per-block limit");
+static_assert(hash_smem<1024>() <= 232448, "hash-tier shared memory above the per-block limit");
 constexpr size_t block_smem = (size_t)BTAB * sizeof(double) + (size_t)(BTAB + BTAB / 2) * sizeof(int);
 
 struct Args {
@@ -610,13 +656,16 @@ struct Args {
   cudaStream_t s;
 };
 
+// nr: the list's length, or (with nr_dev) a bound on the length held at
+// nr_dev; retry / retry_n: where rows beyond TAB/2 distinct columns go.
 template <int TAB>
-void launch_hash(int nr, const int *list, const Args &a) {
+void launch_hash(int nr, const int *list, const int *nr_dev, int *retry, int *retry_n, int max_blocks,
+                 const Args &a) {
   static std::atomic<unsigned long long> attr{0};
   ensure_smem_attr(k_spgemm_hash<TAB>, (int)hash_smem<TAB>(), attr);
-  const int grid = std::max(1, std::min(ceil_div(nr, WARPS), kNumSMs * 32));
-  k_spgemm_hash<TAB><<<grid, TPB, hash_smem<TAB>(), a.s>>>(list, nr, a.X->rp, a.X->ci, a.X->v, a.y, a.yci, a.yv,
-                                                           a.off, a.tci, a.tcv, a.cnt, a.flags);
+  const int grid = std::max(1, std::min(ceil_div(nr, WARPS), max_blocks));
+  k_spgemm_hash<TAB><<<grid, TPB, hash_smem<TAB>(), a.s>>>(list, nr, nr_dev, a.X->rp, a.X->ci, a.X->v, a.y, a.yci,
+                                                           a.yv, a.off, a.tci, a.tcv, a.cnt, a.flags, retry, retry_n);
   AMG_CHECK_LAUNCH();
 }
 
@@ -629,7 +678,7 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
   const YRows y{Y.rp};
   Buf<int> ub(m, (size_t)rows + 1), off(m, (size_t)rows + 1), lists(m, (size_t)std::max(rows, 1));
   Buf<int8_t> tier(m, (size_t)std::max(rows, 1));
-  Buf<int> meta(m, 2 * NTIER + 1);  // per-tier row counts, max ub of the global tier, list cursors
+  Buf<int> meta(m, 2 * NTIER + 1);  // per-tier row counts, max ub of the T_OPT rows, list cursors
   AMG_CUDA(cudaMemsetAsync(meta.p, 0, sizeof(int) * (2 * NTIER + 1), s));
   {
     ProfScope ps(s, AMG_K_SPGEMM, 0.0, level);  // bookkeeping: no algorithmic bytes
@@ -664,14 +713,24 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
     k_tier_scatter<<<std::max(1, ntiles), TPB, 0, s>>>(rows, tier.p, startd.p, meta.p + NTIER + 1, lists.p);
     AMG_CHECK_LAUNCH();
   }
+  // rows of the optimistic tier that overflow a 256-slot table are retried
+  // with 1024 slots, then with an exact table (a block per row: shared memory
+  // for ub <= BTAB / 2, else a global scratch slice of gcap >= 2 ub slots)
+  const int nopt = hm[T_OPT];
+  const bool gtab = hm[NTIER] > BTAB / 2;
   int gcap = 2;
   while (gcap < 2 * std::max(hm[NTIER], 1)) gcap <<= 1;
-  const int gblocks = std::min(hm[T_GLOBAL], kNumSMs * 2);
-  Buf<int> gscr;
+  const int gblocks = std::max(1, std::min(nopt, kNumSMs * 2));
+  Buf<int> retry, rn, gscr;
   Buf<double> gacc;
-  if (hm[T_GLOBAL] > 0) {
-    gscr = Buf<int>(m, (size_t)gblocks * ((size_t)gcap + gcap / 2));
-    gacc = Buf<double>(m, (size_t)gblocks * gcap);
+  if (nopt > 0) {
+    retry = Buf<int>(m, 2 * (size_t)nopt);
+    rn = Buf<int>(m, 2);
+    AMG_CUDA(cudaMemsetAsync(rn.p, 0, 2 * sizeof(int), s));
+    if (gtab) {
+      gscr = Buf<int>(m, (size_t)gblocks * ((size_t)gcap + gcap / 2));
+      gacc = Buf<double>(m, (size_t)gblocks * gcap);
+    }
   }
   static std::atomic<unsigned long long> attr{0};
   ensure_smem_attr(k_spgemm_block<false>, (int)block_smem, attr);
@@ -697,20 +756,19 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
       k_spgemm_reg<<<grid, TPB, 0, s>>>(list(0), hm[0], X.rp, X.ci, X.v, y, Y.ci, Y.v, off.p, tci.p, tcv.p, cnt.p);
       AMG_CHECK_LAUNCH();
     }
-    if (hm[1] > 0) launch_hash<128>(hm[1], list(1), a);
-    if (hm[2] > 0) launch_hash<256>(hm[2], list(2), a);
-    if (hm[3] > 0) launch_hash<512>(hm[3], list(3), a);
-    if (hm[4] > 0) launch_hash<1024>(hm[4], list(4), a);
-    if (hm[5] > 0) launch_hash<2048>(hm[5], list(5), a);
-    if (hm[6] > 0) {
-      const int grid = std::max(1, std::min(hm[6], kNumSMs * 4));
-      k_spgemm_block<false><<<grid, TPB, block_smem, s>>>(list(6), hm[6], X.rp, X.ci, X.v, y, Y.ci, Y.v, off.p,
-                                                          tci.p, tcv.p, cnt.p, flags, nullptr, nullptr, 0);
-      AMG_CHECK_LAUNCH();
-    }
-    if (hm[T_GLOBAL] > 0) {
-      k_spgemm_block<true><<<gblocks, TPB, 0, s>>>(list(T_GLOBAL), hm[T_GLOBAL], X.rp, X.ci, X.v, y, Y.ci, Y.v, off.p,
-                                                   tci.p, tcv.p, cnt.p, flags, gscr.p, gacc.p, gcap);
+    if (hm[1] > 0) launch_hash<128>(hm[1], list(1), nullptr, nullptr, nullptr, kNumSMs * 32, a);
+    if (hm[2] > 0) launch_hash<256>(hm[2], list(2), nullptr, nullptr, nullptr, kNumSMs * 32, a);
+    if (nopt > 0) {
+      launch_hash<256>(nopt, list(T_OPT), nullptr, retry.p, rn.p, kNumSMs * 32, a);
+      launch_hash<1024>(nopt, retry.p, rn.p, retry.p + nopt, rn.p + 1, kNumSMs * 2, a);
+      if (!gtab) {
+        k_spgemm_block<false><<<gblocks, TPB, block_smem, s>>>(retry.p + nopt, nopt, rn.p + 1, X.rp, X.ci, X.v, y,
+                                                               Y.ci, Y.v, off.p, tci.p, tcv.p, cnt.p, flags, nullptr,
+                                                               nullptr, 0);
+      } else {
+        k_spgemm_block<true><<<gblocks, TPB, 0, s>>>(retry.p + nopt, nopt, rn.p + 1, X.rp, X.ci, X.v, y, Y.ci, Y.v,
+                                                     off.p, tci.p, tcv.p, cnt.p, flags, gscr.p, gacc.p, gcap);
+      }
       AMG_CHECK_LAUNCH();
     }
   }
