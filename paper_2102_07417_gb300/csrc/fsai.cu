@@ -14,8 +14,9 @@
 //   operators' finest levels: 4 entries);
 //   m <= 16 / m <= 32: 8 / 16 lanes per row, the submatrix in a per-row slice
 //   of shared memory, factored right-looking by the row's lanes;
-//   longer: a warp per row, the submatrix in a per-warp slice of shared
-//   memory (global scratch when a slice does not fit).
+//   m <= 64 / longer: a block of 64 / 256 threads per row, the submatrix a
+//   packed lower triangle in shared memory (a warp per row in global scratch
+//   when it does not fit).
 // Each pivot takes one reciprocal square root, kept on the diagonal of the
 // factor, in place of a square root and a division (FP64 square roots and
 // divisions are instruction sequences on GB300's narrow FP64 pipe).
@@ -125,35 +126,27 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Warp per row.  Each warp has a slice of ld * ld + 2 ld doubles (the
-// submatrix, g, and P_i as ints) -- in shared memory when SMEM (the block's
-// dynamic shared memory, warp w at w * slice), else in global scratch (warp w
-// at w * slice; warps beyond nw have no slice and return).  Rows are visited
-// with stride nw.
+// Warp per row, for rows too long for k_fsai_block's shared memory.  Each
+// warp has a slice of ld * ld + 2 ld doubles (the submatrix, g, and P_i as
+// ints) in global scratch (warp w at w * slice; warps beyond nw have no slice
+// and return).  Rows are visited with stride nw.
 //   gather: the lower parts of the rows P_i[r] are walked as one flattened
 //     sequence (lane u takes entry u, found by a shuffle search over the
 //     prefix of the parts' lengths); an entry of column l lands at
 //     M[r][c] with P_i[c] = l (binary search in P_i);
-//   factor: right-looking Cholesky, column j scaled by the lanes, then the
-//     trailing lower triangle updated with independent multiply-adds, its
-//     (r, c) pairs spread over the lanes as one flat list; each pivot takes
-//     one reciprocal square root (kept on the diagonal), not a square root
-//     and a division: FP64 square roots and divisions are instruction
-//     sequences on GB300's narrow FP64 pipe, and all lanes compute the pivot;
+//   factor: left-looking Cholesky (global scratch is read far more than
+//     written), one reciprocal square root per pivot;
 //   solve: L^T g = e_last backwards by columns (no warp sums).
-template <bool SMEM>
 __global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict__ rows, const int *__restrict__ rp,
                                                    const int *__restrict__ ci,
                                                    const double *__restrict__ a, const int *__restrict__ grp,
                                                    int *__restrict__ gci, double *__restrict__ gv, double *scratch,
                                                    int ld, int nw, int *flags) {
-  extern __shared__ __align__(16) double fsai_smem[];
   const int lane = threadIdx.x & 31;
-  const int wb = threadIdx.x >> 5;
   const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (w >= nw) return;
   const size_t slice = (size_t)ld * ld + 2 * (size_t)ld;
-  double *M = SMEM ? fsai_smem + slice * wb : scratch + slice * w;
+  double *M = scratch + slice * w;
   double *g = M + (size_t)ld * ld;
   int *P = reinterpret_cast<int *>(g + ld);
   for (int r0 = w; r0 < n; r0 += nw) {
@@ -208,36 +201,7 @@ __global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict_
     }
     __syncwarp();
     bool ok = true;
-    if (SMEM) {  // right-looking: independent updates of the trailing triangle
-      for (int j = 0; j < m; ++j) {
-        const double d = M[(size_t)j * ld + j];
-        ok = ok && d > 0.0;
-        const double inv = rsqrt(d > 0.0 ? d : 1.0);  // 1 / l_jj, kept on the diagonal
-        __syncwarp();
-        for (int r = j + 1 + lane; r < m; r += 32) M[(size_t)r * ld + j] *= inv;
-        if (lane == 0) M[(size_t)j * ld + j] = inv;
-        __syncwarp();
-        // trailing lower triangle (rows and columns j+1..m-1) as one flat list
-        // of (r, c) pairs, t = r'(r'+1)/2 + c' with r' = r - j - 1, c' = c - j - 1,
-        // so every lane has work while any pair is left
-        const int sz = m - j - 1, npair = sz * (sz + 1) / 2;
-        int rr = 0, cc = lane;
-        while (cc > rr) {
-          cc -= rr + 1;
-          ++rr;
-        }
-        for (int t = lane; t < npair; t += 32) {
-          const int r = j + 1 + rr, c = j + 1 + cc;
-          M[(size_t)r * ld + c] -= M[(size_t)r * ld + j] * M[(size_t)c * ld + j];
-          cc += 32;
-          while (cc > rr) {
-            cc -= rr + 1;
-            ++rr;
-          }
-        }
-        __syncwarp();
-      }
-    } else {  // left-looking: global scratch is read far more than written
+    {  // left-looking
       for (int j = 0; j < m; ++j) {
         const double *Mj = M + (size_t)j * ld;
         double d = 0.0;
@@ -277,13 +241,21 @@ __global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict_
   }
 }
 
+// Doubles per row slice of k_fsai_group: the submatrix (LD x LD), g (LD),
+// then P_i as ints; an odd count, so that the slices of one warp start on
+// different banks.
+template <int LD>
+__host__ __device__ constexpr int group_slice() {
+  return (LD * LD + LD + (LD + 1) / 2) | 1;
+}
+
 // G lanes per row (32 / G rows per warp) for rows of at most LD lower
-// entries.  Each row has a slice of LD * LD + 2 LD + 1 doubles in shared
-// memory (the submatrix, g, P_i as ints; the odd length staggers the slices'
-// banks): the lanes gather the rows of A[P_i, P_i] (each lane walks rows r,
-// r + G, ... of P_i), factor it right-looking with the trailing triangle's
-// (r, c) pairs spread over the row's lanes, one reciprocal square root per
-// pivot, and solve L^T g = e_last by columns.  Several short rows per warp
+// entries.  Each row has a slice of group_slice<LD>() doubles in shared
+// memory: the lanes gather the rows of A[P_i, P_i] (each lane walks rows r,
+// r + G, ... of P_i; gathering the rows as one flat list of entries over the
+// lanes measured slower), factor it right-looking with the trailing
+// triangle's (r, c) pairs spread over the row's lanes, one reciprocal square
+// root per pivot, and solve L^T g = e_last by columns.  Several short rows per warp
 // keep its lanes busy (a warp per row leaves most idle on rows of ~10
 // entries) while the per-row slices stay small enough for many warps per SM.
 // The rows of a warp step through the factor together (up to the warp's
@@ -294,7 +266,7 @@ __global__ void __launch_bounds__(TPB) k_fsai_group(int nrows, const int *__rest
                                                     const double *__restrict__ a, const int *__restrict__ grp,
                                                     int *__restrict__ gci, double *__restrict__ gv, int *flags) {
   constexpr int RPW = 32 / G;
-  constexpr int SLICE = LD * LD + 2 * LD + 1;
+  constexpr int SLICE = group_slice<LD>();
   extern __shared__ __align__(16) double fsai_gsmem[];
   const int lane = threadIdx.x & 31, sub = lane & (G - 1);
   double *M = fsai_gsmem + (size_t)(threadIdx.x / G) * SLICE;
@@ -385,27 +357,121 @@ __global__ void __launch_bounds__(TPB) k_fsai_group(int nrows, const int *__rest
   if (!ok) flags[1] = 1;
 }
 
+// A block per row for rows of more than 32 lower entries (ld = the longest
+// such row of the level).  The submatrix is kept as a packed lower triangle,
+// M(r, c) at r (r + 1) / 2 + c, followed by g (ld doubles) and P_i (ld ints),
+// in shared memory: ld = 123 then takes 62 KB, three rows per SM, where an
+// ld x ld slice per warp left one warp per SM.  The block's threads gather
+// the rows of A[P_i, P_i] (a thread per row of P_i), factor it right-looking
+// -- each column's pivot as
+// one reciprocal square root, the trailing triangle's (r, c) pairs spread over
+// all threads -- and solve L^T g = e_last by columns.
+__device__ __forceinline__ int tri(int r, int c) { return r * (r + 1) / 2 + c; }
+
+__global__ void __launch_bounds__(TPB) k_fsai_block(int nrows, const int *__restrict__ rows,
+                                                    const int *__restrict__ rp, const int *__restrict__ ci,
+                                                    const double *__restrict__ a, const int *__restrict__ grp,
+                                                    int *__restrict__ gci, double *__restrict__ gv, int ld,
+                                                    int *flags) {
+  extern __shared__ __align__(16) double fsai_bsmem[];
+  double *M = fsai_bsmem;
+  double *g = M + (size_t)ld * (ld + 1) / 2;
+  int *P = reinterpret_cast<int *>(g + ld);
+  const int t = threadIdx.x, nt = blockDim.x;
+  bool ok = true;
+  for (int r0 = blockIdx.x; r0 < nrows; r0 += gridDim.x) {
+    const int i = rows[r0];
+    const int b = rp[i], o = grp[i], m = grp[i + 1] - o;
+    for (int e = t; e < m; e += nt) P[e] = ci[b + e];
+    for (int e = t; e < m * (m + 1) / 2; e += nt) M[e] = 0.0;
+    __syncthreads();
+    for (int r = t; r < m; r += nt) {  // row P[r]: its columns P[c] (c <= r) are <= P[r]
+      const int row = P[r];
+      for (int q = rp[row], qe = rp[row + 1]; q < qe; ++q) {
+        const int l = ci[q];
+        if (l > row) break;
+        int lo = 0, hi = r;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (P[mid] < l) lo = mid + 1;
+          else hi = mid;
+        }
+        if (P[lo] == l) M[tri(r, lo)] = a[q];
+      }
+    }
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+      const double d = M[tri(j, j)];
+      ok = ok && d > 0.0;
+      const double inv = rsqrt(d > 0.0 ? d : 1.0);  // 1 / l_jj
+      for (int r = j + 1 + t; r < m; r += nt) M[tri(r, j)] *= inv;
+      __syncthreads();
+      // trailing triangle rows and columns j+1..m-1: pair u = r'(r'+1)/2 + c'
+      const int sz = m - j - 1, npair = sz * (sz + 1) / 2;
+      int rr = 0, cc = t;
+      while (cc > rr) {
+        cc -= rr + 1;
+        ++rr;
+      }
+      for (int u = t; u < npair; u += nt) {
+        const int r = j + 1 + rr, c = j + 1 + cc;
+        M[tri(r, c)] -= M[tri(r, j)] * M[tri(c, j)];
+        cc += nt;
+        while (cc > rr) {
+          cc -= rr + 1;
+          ++rr;
+        }
+      }
+      if (t == 0) M[tri(j, j)] = inv;  // no thread reads the pivot in this phase
+      __syncthreads();
+    }
+    for (int e = t; e < m; e += nt) g[e] = e == m - 1 ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = m - 1; k >= 0; --k) {  // L^T g = e_last by columns
+      const double gk = g[k] * M[tri(k, k)];
+      __syncthreads();
+      for (int l = t; l < k; l += nt) g[l] -= M[tri(k, l)] * gk;
+      if (t == 0) g[k] = gk;
+      __syncthreads();
+    }
+    for (int e = t; e < m; e += nt) {
+      gci[o + e] = P[e];
+      gv[o + e] = g[e];
+    }
+    __syncthreads();
+  }
+  if (!ok) flags[1] = 1;
+}
+
+// shared memory of k_fsai_block for rows of at most ld entries, and the
+// most a block may take (the opt-in limit per block)
+constexpr int kBlockSmemMax = 227 * 1024;
+size_t block_smem_bytes(int ld) {
+  return ((size_t)ld * (ld + 1) / 2 + (size_t)ld) * sizeof(double) + (size_t)ld * sizeof(int);
+}
+
 template <int G, int LD>
 constexpr size_t group_slice_bytes() {
-  return (size_t)(LD * LD + 2 * LD + 1) * sizeof(double);
+  return (size_t)group_slice<LD>() * sizeof(double);
 }
 
 // Rows binned by their lower-entry count m: bin 0 m <= 8, 1 m <= 16,
-// 2 m <= 32, 3 longer; list b at lists + b * n, its count in counts[b].
-// Tiles of the block append with one atomic per bin.
+// 2 m <= 32, 3 m <= 64, 4 longer; list b at lists + b * n, its count in
+// counts[b].  Tiles of the block append with one atomic per bin.
+constexpr int kFsaiBins = 5;
 __global__ void k_fsai_bin(int n, const int *__restrict__ grp, int *__restrict__ lists, int *counts) {
-  __shared__ int c[4], base[4];
-  if (threadIdx.x < 4) c[threadIdx.x] = 0;
+  __shared__ int c[kFsaiBins], base[kFsaiBins];
+  if (threadIdx.x < kFsaiBins) c[threadIdx.x] = 0;
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   int bin = -1, pos = 0;
   if (i < n) {
     const int m = grp[i + 1] - grp[i];
-    bin = m <= 8 ? 0 : m <= 16 ? 1 : m <= 32 ? 2 : 3;
+    bin = m <= 8 ? 0 : m <= 16 ? 1 : m <= 32 ? 2 : m <= 64 ? 3 : 4;
     pos = atomicAdd(&c[bin], 1);
   }
   __syncthreads();
-  if (threadIdx.x < 4) base[threadIdx.x] = c[threadIdx.x] ? atomicAdd(&counts[threadIdx.x], c[threadIdx.x]) : 0;
+  if (threadIdx.x < kFsaiBins) base[threadIdx.x] = c[threadIdx.x] ? atomicAdd(&counts[threadIdx.x], c[threadIdx.x]) : 0;
   __syncthreads();
   if (bin >= 0) lists[(size_t)bin * n + base[bin] + pos] = i;
 }
@@ -466,40 +532,48 @@ void build_fsai(amg_hierarchy *h, int k) {
       k_fsai_rows<8><<<ceil_div(n, TPB), TPB, 0, s>>>(n, nullptr, A.rp, A.ci, A.v, G.rp, G.ci, G.v, meta.p);
     } else {
       // rows binned by m: registers (m <= 8), 8 lanes per row (m <= 16),
-      // 16 lanes per row (m <= 32), a warp per row (longer)
-      Buf<int> lists(m, 4 * (size_t)n), cnts(m, 4);
-      AMG_CUDA(cudaMemsetAsync(cnts.p, 0, 4 * sizeof(int), s));
+      // 16 lanes per row (m <= 32), a block of 64 threads per row (m <= 64),
+      // a block of 256 (longer; a warp per row in global scratch when the
+      // packed triangle does not fit in shared memory)
+      Buf<int> lists(m, kFsaiBins * (size_t)n), cnts(m, kFsaiBins);
+      AMG_CUDA(cudaMemsetAsync(cnts.p, 0, kFsaiBins * sizeof(int), s));
       k_fsai_bin<<<ceil_div(n, TPB), TPB, 0, s>>>(n, G.rp, lists.p, cnts.p);
       AMG_CHECK_LAUNCH();
-      int hn[4];
+      int hn[kFsaiBins];
       AMG_CUDA(cudaMemcpyAsync(hn, cnts.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
       AMG_CUDA(cudaStreamSynchronize(s));
+      auto list = [&](int b) { return lists.p + (size_t)b * n; };
       if (hn[0] > 0) {
-        k_fsai_rows<8><<<ceil_div(hn[0], TPB), TPB, 0, s>>>(hn[0], lists.p, A.rp, A.ci, A.v, G.rp, G.ci, G.v,
+        k_fsai_rows<8><<<ceil_div(hn[0], TPB), TPB, 0, s>>>(hn[0], list(0), A.rp, A.ci, A.v, G.rp, G.ci, G.v,
                                                             meta.p);
         AMG_CHECK_LAUNCH();
       }
-      if (hn[1] > 0) launch_group<8, 16>(lists.p + n, hn[1], TPB, A, G, meta.p, s);
-      if (hn[2] > 0) launch_group<16, 32>(lists.p + 2 * (size_t)n, hn[2], TPB / 2, A, G, meta.p, s);
-      const int nbig = hn[3];
-      const int *llarge = lists.p + 3 * (size_t)n;
+      if (hn[1] > 0) launch_group<8, 16>(list(1), hn[1], TPB, A, G, meta.p, s);
+      if (hn[2] > 0) launch_group<16, 32>(list(2), hn[2], TPB / 2, A, G, meta.p, s);
+      static std::atomic<unsigned long long> attr{0};
+      ensure_smem_attr(k_fsai_block, kBlockSmemMax, attr);
+      if (hn[3] > 0) {
+        const int ld = std::min(mmax, 64);
+        const int blocks = std::max(1, std::min(hn[3], kNumSMs * 32));
+        k_fsai_block<<<blocks, 64, block_smem_bytes(ld), s>>>(hn[3], list(3), A.rp, A.ci, A.v, G.rp, G.ci, G.v, ld,
+                                                              meta.p);
+        AMG_CHECK_LAUNCH();
+      }
+      const int nbig = hn[4];
+      const int *llarge = list(4);
       if (nbig > 0) {
-        // slice per warp: ld * ld + 2 ld doubles (P_i's ints fit in the last ld)
-        const size_t slice = ((size_t)mmax * mmax + 2 * (size_t)mmax) * sizeof(double);
-        const int wpb = (int)std::min<size_t>(8, (size_t)(200 * 1024) / slice);
-        if (wpb >= 1) {  // shared memory
-          static std::atomic<unsigned long long> attr{0};
-          ensure_smem_attr(k_fsai_warp<true>, 200 * 1024, attr);
-          const int blocks = std::max(1, std::min(ceil_div(nbig, wpb), kNumSMs * 32));
-          k_fsai_warp<true><<<blocks, wpb * 32, slice * wpb, s>>>(nbig, llarge, A.rp, A.ci, A.v, G.rp, G.ci, G.v,
-                                                                   nullptr, mmax, blocks * wpb, meta.p);
-        } else {  // global scratch
+        const size_t bsm = block_smem_bytes(mmax);
+        if (bsm <= (size_t)kBlockSmemMax) {  // a block per row, packed triangle in shared memory
+          const int blocks = std::max(1, std::min(nbig, kNumSMs * 8));
+          k_fsai_block<<<blocks, TPB, bsm, s>>>(nbig, llarge, A.rp, A.ci, A.v, G.rp, G.ci, G.v, mmax, meta.p);
+        } else {  // a warp per row, the submatrix in a global scratch slice
+          // slice per warp: ld * ld + 2 ld doubles (P_i's ints fit in the last ld)
+          const size_t slice = ((size_t)mmax * mmax + 2 * (size_t)mmax) * sizeof(double);
           const int64_t cap_warps = std::max<int64_t>(1, ((int64_t)256 << 20) / (int64_t)slice);
           const int warps = (int)std::min<int64_t>({(int64_t)nbig, (int64_t)kNumSMs * 16, cap_warps});
           Buf<double> scr(m, slice / sizeof(double) * (size_t)warps);
-          k_fsai_warp<false><<<ceil_div((int64_t)warps * 32, TPB), TPB, 0, s>>>(nbig, llarge, A.rp, A.ci, A.v,
-                                                                               G.rp, G.ci, G.v, scr.p, mmax, warps,
-                                                                               meta.p);
+          k_fsai_warp<<<ceil_div((int64_t)warps * 32, TPB), TPB, 0, s>>>(nbig, llarge, A.rp, A.ci, A.v, G.rp, G.ci,
+                                                                        G.v, scr.p, mmax, warps, meta.p);
         }
       }
     }
