@@ -760,12 +760,14 @@ void spgemm(Mem &m, int *flags, const DCsr &X, const DCsr &Y, int ncols, DCsr &C
     if (hm[2] > 0) launch_hash<256>(hm[2], list(2), nullptr, nullptr, nullptr, kNumSMs * 32, a);
     if (nopt > 0) {
       launch_hash<256>(nopt, list(T_OPT), nullptr, retry.p, rn.p, kNumSMs * 32, a);
-      launch_hash<1024>(nopt, retry.p, rn.p, retry.p + nopt, rn.p + 1, kNumSMs * 2, a);
-      if (!gtab) {
+      // a row with ub <= 512 has at most 512 columns: the 1024-slot set holds it
+      const bool exact = hm[NTIER] > 512;
+      launch_hash<1024>(nopt, retry.p, rn.p, exact ? retry.p + nopt : nullptr, rn.p + 1, kNumSMs * 2, a);
+      if (exact && !gtab) {
         k_spgemm_block<false><<<gblocks, TPB, block_smem, s>>>(retry.p + nopt, nopt, rn.p + 1, X.rp, X.ci, X.v, y,
                                                                Y.ci, Y.v, off.p, tci.p, tcv.p, cnt.p, flags, nullptr,
                                                                nullptr, 0);
-      } else {
+      } else if (exact) {
         k_spgemm_block<true><<<gblocks, TPB, 0, s>>>(retry.p + nopt, nopt, rn.p + 1, X.rp, X.ci, X.v, y, Y.ci, Y.v,
                                                      off.p, tci.p, tcv.p, cnt.p, flags, gscr.p, gacc.p, gcap);
       }
