@@ -304,7 +304,8 @@ __device__ __forceinline__ long long lam_key(const double *__restrict__ lam, int
 __global__ void k_pmis_select(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                               const uint8_t *__restrict__ S, const uint8_t *__restrict__ ST,
                               const double *__restrict__ lam, const int8_t *__restrict__ st_old,
-                              int8_t *__restrict__ st_new) {
+                              int8_t *__restrict__ st_new, const int *__restrict__ prev_undecided) {
+  if (prev_undecided && *prev_undecided == 0) return;  // the splitting is complete
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int8_t s = st_old[i];
@@ -328,7 +329,9 @@ __global__ void k_pmis_select(int n, const int *__restrict__ rp, const int *__re
 // F; new C points become C.  Counts the points still undecided.
 __global__ void k_pmis_update(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                               const uint8_t *__restrict__ S, const int8_t *__restrict__ st_new,
-                              int8_t *__restrict__ st_next, int *undecided) {
+                              int8_t *__restrict__ st_next, int *undecided,
+                              const int *__restrict__ prev_undecided) {
+  if (prev_undecided && *prev_undecided == 0) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool und = false;
   if (i < n) {
@@ -632,7 +635,8 @@ __global__ void k_pmis_init_w(int n, const int *__restrict__ rp, const int *__re
 __global__ void k_pmis_select_w(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                 const uint8_t *__restrict__ S, const uint8_t *__restrict__ ST,
                                 const double *__restrict__ lam, const int8_t *__restrict__ st_old,
-                                int8_t *__restrict__ st_new) {
+                                int8_t *__restrict__ st_new, const int *__restrict__ prev_undecided) {
+  if (prev_undecided && *prev_undecided == 0) return;
   WARP_ROW_BEGIN
   const int8_t s0 = st_old[i];
   if (s0 != ST_U) {
@@ -654,7 +658,9 @@ __global__ void k_pmis_select_w(int n, const int *__restrict__ rp, const int *__
 
 __global__ void k_pmis_update_w(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                 const uint8_t *__restrict__ S, const int8_t *__restrict__ st_new,
-                                int8_t *__restrict__ st_next, int *undecided) {
+                                int8_t *__restrict__ st_next, int *undecided,
+                                const int *__restrict__ prev_undecided) {
+  if (prev_undecided && *prev_undecided == 0) return;
   __shared__ int und_blk;
   if (threadIdx.x == 0) und_blk = 0;
   __syncthreads();
@@ -1533,30 +1539,36 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain) {
         else k_pmis_init<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, prm.seed, k, fl.d);
         AMG_CHECK_LAUNCH();
       }
-      // Rounds run two at a time between host checks: a round after the last
-      // undecided point is gone changes nothing, so the second one is free to
-      // run past the end.  flags[6] / flags[7] count the points each of the
-      // two rounds leaves undecided (read with the error flags, one sync).
-      for (int round = 0;; round += 2) {
+      // Rounds run kPmisBatch at a time between host checks.  Round r's
+      // kernels return at once when round r - 1 left no point undecided (a
+      // round after that would change nothing), so the batch may run past the
+      // end; und[r] counts the points round r leaves undecided, and the last
+      // one is read with the error flags (one synchronisation per batch).
+      constexpr int kPmisBatch = 8;
+      Buf<int> und(m, kPmisBatch);
+      for (int round = 0;; round += kPmisBatch) {
         if (round > gn + 1) fail(AMG_ERR_SETUP, "PMIS did not terminate");
-        AMG_CUDA(cudaMemsetAsync(fl.d + 6, 0, 2 * sizeof(int), s));
-        for (int sub = 0; sub < 2; ++sub) {
+        AMG_CUDA(cudaMemsetAsync(und.p, 0, kPmisBatch * sizeof(int), s));
+        for (int sub = 0; sub < kPmisBatch; ++sub) {
+          const int *prev = sub ? und.p + sub - 1 : nullptr;
           {
             ProfScope ps(s, AMG_K_PMIS, rows + 6.0 * nz + 10.0 * gn, k);
-            if (gwide) k_pmis_select_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, st1.p);
-            else k_pmis_select<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, st1.p);
+            if (gwide) k_pmis_select_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, st1.p, prev);
+            else k_pmis_select<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, ST.p, lam.p, st0.p, st1.p, prev);
             AMG_CHECK_LAUNCH();
           }
           {
             ProfScope ps(s, AMG_K_PMIS, rows + 5.0 * nz + 2.0 * gn, k);
-            if (gwide) k_pmis_update_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, st1.p, st0.p, fl.d + 6 + sub);
-            else k_pmis_update<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, st1.p, st0.p, fl.d + 6 + sub);
+            if (gwide) k_pmis_update_w<<<ggw, TPB, 0, s>>>(gn, grp, gci, gS, st1.p, st0.p, und.p + sub, prev);
+            else k_pmis_update<<<gg, TPB, 0, s>>>(gn, grp, gci, gS, st1.p, st0.p, und.p + sub, prev);
             AMG_CHECK_LAUNCH();
           }
         }
+        int left = 0;
+        AMG_CUDA(cudaMemcpyAsync(&left, und.p + kPmisBatch - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         sync_flags();
         if (fl.h[2]) fail(AMG_ERR_INVALID_ARG, "matrix pattern is not structurally symmetric");
-        if (fl.h[7] == 0) break;
+        if (left == 0) break;
       }
       L.cf = m.get_n<int8_t>(n);
       Buf<int> isC(m, n);
