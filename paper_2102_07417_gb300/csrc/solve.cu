@@ -853,14 +853,15 @@ void launch_rows(RowMap map, int n, const int *rp, const int *ci, const Op &op, 
   AMG_CHECK_LAUNCH();
 }
 
-// Matrices with at least kSellMinRows rows get a SELL copy (thread per row
-// needs enough rows to fill the GPU; smaller ones use the CSR vector form).
-// The single-vector kernels use it from kSellSolveRows rows up: between the
-// two, rows are few enough (and on coarse levels long enough) that the CSR
-// vector form with a few lanes per row keeps more loads in flight than a lane
-// per row (measured on the 128^3 Poisson hierarchy: level 2, 137K rows of 46
-// entries, smoothing 62 us in CSR against 79 us in SELL).  The batched kernels
-// use the SELL copy whenever it exists.
+// Matrices with at least kSellSolveRows rows get a SELL copy, used by the
+// single-vector kernels and (up to 16 columns) the batched ones; smaller ones
+// use the CSR vector form.  From kSellMinRows rows up the CSR form puts at
+// most a quarter of the mean row length of lanes on a row (see choose_map):
+// there rows are few enough (and on coarse levels long enough) that a few
+// lanes per row keep more loads in flight than a lane per row in SELL
+// (measured on the 128^3 Poisson hierarchy: level 2, 137K rows of 46
+// entries, smoothing 62 us in CSR against 79 us in SELL).  (Copies were once
+// built from kSellMinRows rows too, which no kernel read.)
 constexpr int kSellMinRows = 1 << 15;
 constexpr int kSellSolveRows = 1 << 18;
 inline bool on_sell(const DCsr &M) { return M.use_sell && M.n >= kSellSolveRows; }
@@ -1497,10 +1498,10 @@ void prepare_solve(amg_hierarchy *h) {
       }
     }
     // SELL copies for the large matrices (A also in FP64 on level 0 for the CG products)
-    if (n >= kSellMinRows) build_sell(m, L.A, fp64 || k == 0, !fp64, false);
+    if (n >= kSellSolveRows) build_sell(m, L.A, fp64 || k == 0, !fp64, false);
     if (!last) {
-      if (L.P.n >= kSellMinRows) build_sell(m, L.P, fp64, prec == AMG_PREC_FP32, prec == AMG_PREC_FP32_BF16PR);
-      if (L.R.n >= kSellMinRows) build_sell(m, L.R, fp64, prec == AMG_PREC_FP32, prec == AMG_PREC_FP32_BF16PR);
+      if (L.P.n >= kSellSolveRows) build_sell(m, L.P, fp64, prec == AMG_PREC_FP32, prec == AMG_PREC_FP32_BF16PR);
+      if (L.R.n >= kSellSolveRows) build_sell(m, L.R, fp64, prec == AMG_PREC_FP32, prec == AMG_PREC_FP32_BF16PR);
     }
     if (!last && h->prm.smoother == AMG_SMOOTH_FSAI) {  // G and omega G^T, stored like A
       build_fsai(h, k);
@@ -1513,7 +1514,7 @@ void prepare_solve(amg_hierarchy *h) {
           k_to_f32<<<grid_for(M->nnz), TPB, 0, s>>>(M->nnz, M->v, M->v32);
           AMG_CHECK_LAUNCH();
         }
-        if (n >= kSellMinRows) build_sell(m, *M, fp64, !fp64, false);
+        if (n >= kSellSolveRows) build_sell(m, *M, fp64, !fp64, false);
       }
     }
   }
