@@ -201,24 +201,22 @@ __global__ void __launch_bounds__(TPB) k_fsai_warp(int n, const int *__restrict_
     }
     __syncwarp();
     bool ok = true;
-    {  // left-looking
-      for (int j = 0; j < m; ++j) {
-        const double *Mj = M + (size_t)j * ld;
-        double d = 0.0;
-        for (int k = lane; k < j; k += 32) d += Mj[k] * Mj[k];
-        d = Mj[j] - warp_sum(d);
-        ok = ok && d > 0.0;
-        const double inv = rsqrt(d > 0.0 ? d : 1.0);
-        for (int r = j + 1 + lane; r < m; r += 32) {
-          double *Mr = M + (size_t)r * ld;
-          double sum = Mr[j];
-          for (int k = 0; k < j; ++k) sum -= Mr[k] * Mj[k];
-          Mr[j] = sum * inv;
-        }
-        __syncwarp();
-        if (lane == 0) M[(size_t)j * ld + j] = inv;
-        __syncwarp();
+    for (int j = 0; j < m; ++j) {  // left-looking; 1 / l_jj kept on the diagonal
+      const double *Mj = M + (size_t)j * ld;
+      double d = 0.0;
+      for (int k = lane; k < j; k += 32) d += Mj[k] * Mj[k];
+      d = Mj[j] - warp_sum(d);
+      ok = ok && d > 0.0;
+      const double inv = rsqrt(d > 0.0 ? d : 1.0);
+      for (int r = j + 1 + lane; r < m; r += 32) {
+        double *Mr = M + (size_t)r * ld;
+        double sum = Mr[j];
+        for (int k = 0; k < j; ++k) sum -= Mr[k] * Mj[k];
+        Mr[j] = sum * inv;
       }
+      __syncwarp();
+      if (lane == 0) M[(size_t)j * ld + j] = inv;
+      __syncwarp();
     }
     if (!ok && lane == 0) flags[1] = 1;
     // L^T g = e_last, backwards by columns: once g_k = rhs_k / l_kk is known,

@@ -71,6 +71,25 @@ def test_ext_pcg_fp64_parity(name, smoother):
     assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-9 * np.linalg.norm(xo)
 
 
+@pytest.mark.parametrize("name", ["poisson3d_20", "graph_hubs_4000"])
+def test_ext_fsai_factors_match_oracle(name):
+    """FSAI factors on the denser extended+i hierarchies: poisson3d_20's levels hold rows of every
+    size bin of the GPU factor kernels (up to ~100 lower entries, a block per row in shared
+    memory), the hub graph rows too long for shared memory (a warp per row in global scratch).
+    Pattern exact, values within 1e-12 of the row's largest entry."""
+    A = CASES[name]()
+    ho = O.Hierarchy(A, seed=0, interp="ext", smoother="fsai", omega=1.0)
+    hg = amg.Hierarchy(A, seed=0, interp=amg.INTERP_EXT, smoother=amg.SMOOTH_FSAI, omega=1.0)
+    assert_same_hierarchy(hg, ho)
+    for k in range(ho.nlevels - 1):
+        gr, gc, gv = hg.export_fsai(k)
+        orp, oci, ov = ho.G(k)
+        assert np.array_equal(gr, orp) and np.array_equal(gc, oci), f"G_{k} pattern"
+        scale = np.maximum.reduceat(np.abs(ov), orp[:-1])
+        rows = np.repeat(np.arange(len(orp) - 1), np.diff(orp))
+        assert np.all(np.abs(gv - ov) <= 1e-12 * scale[rows]), f"G_{k} values"
+
+
 def test_ext_large_sell_levels_and_fp32():
     """262,144 rows (the solve kernels on sliced-ELLPACK copies): FP64 with the oracle's count,
     FP32 V-cycle within 1e-6 of the oracle's x."""
