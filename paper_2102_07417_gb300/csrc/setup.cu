@@ -479,6 +479,36 @@ __device__ __forceinline__ int sign_class(double v) {
   return bits < 0 ? -1 : 1;
 }
 
+// RN(a / b) from y = RN(1 / b), by two FMA corrections:
+//   q0 = RN(a y) is within two ulps of a / b (y carries half an ulp of error
+//     and the product another half);
+//   q1 = RN(q0 + r0 y) with r0 = RN(a - b q0) is within one ulp (a faithful
+//     quotient): r0 y differs from a / b - q0 by about 2^-52 of |q0 - a/b|;
+//   q = RN(q1 + r1 y) with r1 = a - b q1, exact in one FMA since q1 is
+//     faithful, is RN(a / b) by Markstein's theorem (P. W. Markstein,
+//     "Computation of elementary functions on the IBM RISC System/6000
+//     processor", IBM J. Res. Develop. 34(1), 1990; the FMA division theorem
+//     in Muller et al., Handbook of Floating-Point Arithmetic).
+// So the result is the correctly rounded quotient a division gives, away
+// from overflow and underflow: operands whose exponents leave a safe range
+// (|x| in [2^-822, 2^776], where no remainder or product underflows) take
+// the division itself.  Quotients that share a divisor then cost one
+// correctly rounded reciprocal and a multiply and four FMAs each, where each
+// division is a longer instruction sequence on GB300's narrow FP64 pipe.
+__device__ __forceinline__ bool div_safe(double x) {
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  return e > 200 && e < 1800;
+}
+
+__device__ __forceinline__ double div_by(double a, double b, double y) {
+  const double q0 = __dmul_rn(a, y);
+  if (!(div_safe(a) && div_safe(b) && div_safe(q0))) return __ddiv_rn(a, b);
+  const double r0 = __fma_rn(-q0, b, a);
+  const double q1 = __fma_rn(r0, y, q0);
+  const double r1 = __fma_rn(-q1, b, a);
+  return __fma_rn(r1, y, q1);
+}
+
 __global__ void k_interp_count(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                const uint8_t *__restrict__ S, const int8_t *__restrict__ cf,
                                int *__restrict__ cnt) {
@@ -545,12 +575,13 @@ __global__ void k_interp_fill(int n, int bs, const int *__restrict__ rp, const i
   const double alpha = sp_neg != 0.0 ? __ddiv_rn(sn_neg, sp_neg) : 0.0;
   const double beta = sp_pos != 0.0 ? __ddiv_rn(sn_pos, sp_pos) : 0.0;
   const double at = sp_pos != 0.0 ? aii : __dadd_rn(aii, sn_pos);
+  const double yat = __drcp_rn(at);  // the row's weights share the divisor
   for (int p = b; p < e; ++p) {
     const int j = ci[p];
     if (j == i || !S[p] || !cf[j]) continue;
     const double v = a[p];
     const int sg = sign_class(v);
-    const double w = sg ? __ddiv_rn(-__dmul_rn(sg < 0 ? alpha : beta, v), at) : 0.0;
+    const double w = sg ? div_by(-__dmul_rn(sg < 0 ? alpha : beta, v), at, yat) : 0.0;
     pci[pos] = cidx[j];
     pv[pos] = w;
     ++pos;
@@ -811,6 +842,7 @@ __global__ void __launch_bounds__(256) k_interp_fill_w(int n, int bs, const int 
   alpha = __shfl_sync(0xffffffffu, alpha, 0);
   beta = __shfl_sync(0xffffffffu, beta, 0);
   at = __shfl_sync(0xffffffffu, at, 0);
+  const double yat = __drcp_rn(at);  // the row's weights share the divisor
   for (int c0 = b; c0 < e; c0 += 32) {
     const int p = c0 + lane;
     bool sel = false;
@@ -823,7 +855,7 @@ __global__ void __launch_bounds__(256) k_interp_fill_w(int n, int bs, const int 
     if (sel) {
       const double v = a[p];
       const int sg = sign_class(v);
-      const double wv = sg ? __ddiv_rn(-__dmul_rn(sg < 0 ? alpha : beta, v), at) : 0.0;
+      const double wv = sg ? div_by(-__dmul_rn(sg < 0 ? alpha : beta, v), at, yat) : 0.0;
       const int q = pos + __popc(bal & ((1u << lane) - 1u));
       pci[q] = cidx[j];
       pv[q] = wv;
