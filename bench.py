@@ -218,7 +218,9 @@ def default_precision(p, requested=None):
 
 
 # ------------------------------------------------------------------ oracle arm --
-def oracle_solve(p, rtol):
+def oracle_solve(p, rtol, out=None):
+    """One oracle set-up + PCG solve of p: (set-up s, solve s, iterations, status); the solution
+    goes to out["x"] when out is a dict (single right-hand side)."""
     from oracle import oracle as O
 
     kw = getattr(p, "params", {})
@@ -233,6 +235,8 @@ def oracle_solve(p, rtol):
         return t1 - t0, per_it * ELASTICITY64_FP64_ITERS * p.b.shape[1], ELASTICITY64_FP64_ITERS, 0
     st, x, it, _, _ = h.pcg(p.b, rtol=rtol, maxit=1000)
     t2 = time.perf_counter()
+    if out is not None:
+        out["x"] = x
     return t1 - t0, t2 - t1, it, st
 
 
@@ -458,8 +462,14 @@ def run_gpu(args, rank, world, dist):
                "d2h_bytes_per_step": 8 * n * k_ + (0 if batch else 8 + 8 * 10)}
 
     cpu = None
+    x_oracle = None  # the oracle's solution, to compare the GPU solutions against
+    x_diff = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and p.A.n <= 4_200_000:
-        tp_o, ts_o, it_o, st_o = oracle_solve(p, args.rtol)
+        got = {}
+        tp_o, ts_o, it_o, st_o = oracle_solve(p, args.rtol, got)
+        if not batch:
+            x_oracle = got["x"]
+            x_diff = float(np.linalg.norm(x_dev.cpu().numpy() - x_oracle) / np.linalg.norm(x_oracle))
         sample = f"one full oracle set-up ({tp_o:.2f} s) + PCG solve ({ts_o:.2f} s, {it_o} it) of the workload"
         if batch:
             sample = (f"oracle set-up ({tp_o:.2f} s) + 30 PCG iterations of one column, scaled to "
@@ -468,8 +478,9 @@ def run_gpu(args, rank, world, dist):
 
     mixed = None
     if prec == "fp64" and not batch and not args.no_mixed:
-        mixed = run_mixed(args, p, A_dev, b_dev, stream, dev, barrier)
-        mixed["bf16_pr_ablation"] = run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, amg.PREC_FP32_BF16PR)
+        mixed = run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, x_oracle=x_oracle)
+        mixed["bf16_pr_ablation"] = run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, amg.PREC_FP32_BF16PR,
+                                              x_oracle=x_oracle)
     fsai = None
     if not batch and not args.no_mixed:
         # the paper's default smoother family (Eq. smo), static FSAI on lower(A_k), omega = 1
@@ -514,6 +525,7 @@ def run_gpu(args, rank, world, dist):
         "host_ms_median": {k_: statistics.median(v_[-args.steps:]) for k_, v_ in host.items()},
         "iters": rec["iters"], "status": rec["status"], "nlevels": info["nlevels"], "cgd": info["cgd"],
         "cop": info["cop"], "hierarchy_bytes": rec["bytes"], "x_rel_err": x_err,
+        "x_rel_diff_vs_oracle": x_diff,
         "solves_per_s_all_ranks": world * 1e3 / ms,
         "roofline": roof,
         "vcycle_hbm": vcycle,
@@ -570,7 +582,7 @@ def vcycle_back_to_back(params, A_dev, stream, dev, reps: int = 20):
             "method": "V-cycles applied back to back (amg_vcycle_apply), events around the loop only"}
 
 
-def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, prec_id=None, name=None, **kw):
+def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, prec_id=None, name=None, x_oracle=None, **kw):
     """The same workload with the hierarchy stored and the V-cycle run in FP32 under the FP64
     flexible PCG (the mixed-precision form; with prec_id = PREC_FP32_BF16PR, P and R stored in
     BF16), or another variant of the method given by `kw` (e.g. the FSAI smoother): set-up +
@@ -619,8 +631,12 @@ def run_mixed(args, p, A_dev, b_dev, stream, dev, barrier, prec_id=None, name=No
     if name is None:
         name = ("fp32 hierarchy + V-cycle, fp64 flexible PCG" if prec_id == amg.PREC_FP32 else
                 "fp32 hierarchy + V-cycle with P and R in bf16, fp64 flexible PCG")
+    x_diff = None
+    if x_oracle is not None:  # against the oracle's FP64 solution of the same system (same method)
+        x_diff = float(np.linalg.norm(x_dev.cpu().numpy() - x_oracle) / np.linalg.norm(x_oracle))
     return {"precision": name, "t_setup_ms": tp, "t_solve_ms": ts,
             "t_total_ms": tp + ts, "iters": rec["iters"], "status": rec["status"], "x_rel_err": x_err,
+            "x_rel_diff_vs_oracle": x_diff,
             "steps": len(times), "cgd": rec["info"]["cgd"], "cop": rec["info"]["cop"],
             "vcycle_hbm": vcycle_back_to_back(params, A_dev, stream, dev),
             "vcycle_hbm_profiled": {"achieved": vb / (vt * 1e-3) / 1e9 if vt else None, "unit": "GB/s",
