@@ -244,6 +244,8 @@ int amg_spmv(amg_hierarchy *h, int32_t level, const double *x, double *y, void *
  * A as CSR (rowptr[n+1], colidx[nnz], val[nnz]) and p[n], q[n], pq[1] are
  * device pointers on the current device; q receives A p and *pq receives
  * (p, A p), both FP64, stream-ordered on `stream` (nothing is synchronised).
+ * q and pq must not overlap each other, p or A's arrays (the kernel reads p
+ * and A through the read-only path while it writes q).
  * Limit: n <= 16,777,216 rows (the scratch holds 2048 block partials of 8192
  * rows each); larger n returns AMG_ERR_UNSUPPORTED before any GPU work.
  * The first call on each device looks up the scratch array's device address
