@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
     L.amg_slots_free.argtypes = [vp]
     L.amg_slots_free.restype = None
     L.amg_spmv.argtypes = [vp, i32, vp, vp, vp]
+    L.amg_spmv_dot_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp]
     L.amg_solve.argtypes = [C.POINTER(Csr), vp, vp, C.POINTER(Params), dbl, i32, C.POINTER(Allocator), vp,
                             C.POINTER(Result)]
     L.amg_hierarchy_info.argtypes = [vp, C.POINTER(i32), i32, vp, vp, vp, C.POINTER(dbl), C.POINTER(dbl)]
@@ -453,6 +454,29 @@ def profile_read(level: int = -1) -> dict:
 def launch_count() -> int:
     """libamg kernel launches in this process so far."""
     return int(load().amg_launch_count())
+
+
+def spmv_dot_noalloc(rowptr, col, val, p, q, pq, stream=None):
+    """q = A p and pq[0] = (p, A p) in one launch that allocates no device memory
+    (amg_spmv_dot_noalloc).  A is CSR as contiguous CUDA tensors rowptr (int32, n + 1), col (int32)
+    and val (float64); p and q are float64 CUDA tensors of n entries and pq one of at least one,
+    all owned by the caller.  Stream-ordered on `stream`; nothing is synchronised.  Calls that
+    overlap on the GPU share the library's scratch and must be serialised.  Returns (q, pq)."""
+    import torch
+
+    for name, t, dt in (("rowptr", rowptr, torch.int32), ("col", col, torch.int32), ("val", val, torch.float64),
+                        ("p", p, torch.float64), ("q", q, torch.float64), ("pq", pq, torch.float64)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise ValueError(f"spmv_dot_noalloc: {name} must be a contiguous CUDA tensor of {dt}")
+    n = rowptr.numel() - 1
+    if col.numel() != val.numel() or p.numel() != n or q.numel() != n or pq.numel() < 1:
+        raise ValueError(f"spmv_dot_noalloc: sizes do not match n = {n} rows "
+                         f"(col {col.numel()}, val {val.numel()}, p {p.numel()}, q {q.numel()}, pq {pq.numel()})")
+    if col.numel() > 2**31 - 1:
+        raise ValueError(f"spmv_dot_noalloc: {col.numel()} nonzeros exceed the C ABI's int32 count")
+    check(load().amg_spmv_dot_noalloc(n, col.numel(), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(p), _ptr(q),
+                                      _ptr(pq), _stream_handle(stream)), "amg_spmv_dot_noalloc")
+    return q, pq
 
 
 def solve(A, b, x0=None, params: Params | None = None, rtol: float = 1e-8, maxit: int = 500, stream=None,

@@ -78,3 +78,26 @@ def test_bad_params_rejected_without_gpu(lib):
         p = amg.default_params(**kw)
         assert lib.amg_setup(C.byref(csr), C.byref(p), None, None, C.byref(h)) == code
         assert h.value is None
+
+
+def test_noalloc_arguments_refused_without_gpu(lib):
+    """amg_spmv_dot_noalloc checks its arguments before any CUDA call (the pointers below are
+    never dereferenced): NULL pointers and n < 1 are invalid, n above its scratch's 16,777,216 rows
+    unsupported.  The Python wrapper refuses host tensors before reaching the library."""
+    torch = pytest.importorskip("torch")
+    f = lib.amg_spmv_dot_noalloc
+    assert len(f.argtypes) == 9
+    fake = 256  # a non-NULL address that the refused calls never touch
+    assert f(4, 4, None, fake, fake, fake, fake, fake, None) == amg.AMG_ERR_INVALID_ARG
+    assert f(4, 4, fake, None, fake, fake, fake, fake, None) == amg.AMG_ERR_INVALID_ARG
+    assert f(4, 4, fake, fake, fake, fake, fake, None, None) == amg.AMG_ERR_INVALID_ARG
+    assert f(0, 0, fake, None, None, fake, fake, fake, None) == amg.AMG_ERR_INVALID_ARG
+    assert f(4, -1, fake, fake, fake, fake, fake, fake, None) == amg.AMG_ERR_INVALID_ARG
+    assert f(16_777_217, 0, fake, None, None, fake, fake, fake, None) == amg.AMG_ERR_UNSUPPORTED
+    assert b"exceeds the limit" in lib.amg_last_error()
+    rp = torch.tensor([0, 1], dtype=torch.int32)
+    ci = torch.tensor([0], dtype=torch.int32)
+    v = torch.ones(1, dtype=torch.float64)
+    x = torch.ones(1, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        amg.spmv_dot_noalloc(rp, ci, v, x, x.clone(), x.clone())

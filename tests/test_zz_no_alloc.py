@@ -67,3 +67,25 @@ def test_noalloc_refuses_sizes_beyond_its_scratch():
     st = f(MAX_ROWS + 1, 0, idx.data_ptr(), None, None, x.data_ptr(), x.data_ptr(), x.data_ptr(), None)
     assert st == amg.AMG_ERR_UNSUPPORTED
     assert b"exceeds the limit" in amg.load().amg_last_error()
+
+
+def test_noalloc_through_the_binding():
+    """The same product through the Python binding's spmv_dot_noalloc, on a 24^3 Poisson operator
+    (13,824 rows: one full block of 8192 rows and a partial one), against a host product in FP64
+    (1e-13 of max |q|; (p, q) to 1e-12 relative).  Mismatched sizes are refused on the host."""
+    A = pr.poisson3d(24)
+    dev = "cuda:0"
+    rp, ci, v = (torch.as_tensor(a, device=dev) for a in (A.rowptr, A.col, A.val))
+    ph = np.random.default_rng(3).standard_normal(A.n)
+    p = torch.as_tensor(ph, device=dev)
+    q = torch.full_like(p, float("nan"))
+    pq = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
+    q2, pq2 = amg.spmv_dot_noalloc(rp, ci, v, p, q, pq)
+    assert q2 is q and pq2 is pq
+    torch.cuda.synchronize()
+    qh = A.matvec(ph)
+    assert np.abs(q.cpu().numpy() - qh).max() <= 1e-13 * np.abs(qh).max()
+    dot = float(ph @ qh)
+    assert abs(pq.item() - dot) <= 1e-12 * abs(dot)
+    with pytest.raises(ValueError, match="sizes do not match"):
+        amg.spmv_dot_noalloc(rp, ci, v, p[:-1], q, pq)
